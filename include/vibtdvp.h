@@ -1,0 +1,187 @@
+/*
+ * vibtdvp — C ABI of the GB300 two-site TDVP (2TDVP) library for vibronic
+ * Hamiltonians (Xie et al., arXiv:1908.10588).
+ *
+ * The method: an MPS (Sec. 2.1.1, Eq. MPS tensor) is propagated in time by
+ * the two-site time-dependent variational principle (Sec. 2.1.2): at every
+ * bond the two-site tensor is evolved with the two-site effective Hamiltonian
+ * (Eq. two-site Hamiltonian) through a Krylov exponential (Eq. Krylov
+ * subspace), split and truncated (DBSS / fixed M, Sec. 2.1.1), and the new
+ * center site is evolved backward with the one-site effective Hamiltonian
+ * (Eq. one-site Hamiltonian 1). The Hamiltonian is the vibronic model of
+ * Sec. 2.2 (Eqs. Hel_2, Hvib_2, Helvib_2), given to mpo_build as its sum of
+ * terms and turned into an MPO (Eq. MPO).
+ *
+ * Conventions for every entry point:
+ *  - Units: energies in eV, times in fs, hbar = 0.6582119569 eV fs.
+ *  - Complex numbers are interleaved (re, im) pairs of double (or float
+ *    where stated); every tensor is dense and row-major in the index order
+ *    written next to it.
+ *  - Host pointers are borrowed for the duration of the call only. Device
+ *    pointers are owned by the caller unless a handle owns them.
+ *  - No C++ exception crosses this boundary. Every call returns a vb_status;
+ *    on an error outputs are left unspecified and vb_last_error() returns a
+ *    thread-local message. Handles are not thread-safe.
+ *  - All device work of a handle runs on the stream given at creation
+ *    (NULL = the legacy default stream); calls that return host data
+ *    synchronise that stream.
+ */
+#ifndef VIBTDVP_H
+#define VIBTDVP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VB_OK = 0,
+  VB_EINVAL = -1,    /* bad argument, size or layout */
+  VB_ENOMEM = -2,    /* device allocation failed */
+  VB_ECUDA = -3,     /* a CUDA call failed; message in vb_last_error() */
+  VB_ENOCONV = -4,   /* Krylov exponential not converged and policy = fail */
+  VB_ETIMEOUT = -5,  /* a device-side wait ran out of its iteration budget */
+  VB_ESTATE = -6     /* handle in the wrong state (e.g. center not at site 0) */
+} vb_status;
+
+enum { VB_FP64 = 0, VB_MIXED = 1 };
+
+/* Vibronic model, Sec. 2.2. Host memory, borrowed by mpo_build.
+ * H = sum_ij h_ij |i><j|  with h_ii = e0[i], h_ij = v0[i*n_el+j] (i != j)  (Eq. Hel_2)
+ *   + sum_I omega[I] (b_I^+ b_I + include_zpe/2)                          (Eq. Hvib_2)
+ *   + sum_{I,i,j} g1[(I*n_el+i)*n_el+j] q_I |i><j|
+ *   + sum_k g2_val[k] q_I q_J |i><j|, (I,J,i,j) = g2_idx[4k..4k+3], I <= J,
+ *     I == J meaning q_I^2                                                (Eq. Helvib_2)
+ * with q = (b + b^+)/sqrt(2) on the basis |0..levels[I]-1>.
+ * site_order[n_modes+1] gives the chain: -1 = electronic site, k = mode k;
+ * NULL = electronic site first, then the modes in index order. */
+typedef struct {
+  int n_el;
+  const double *e0;
+  const double *v0;
+  int n_modes;
+  const double *omega;
+  const int *levels;
+  const double *g1;
+  int n_g2;
+  const int *g2_idx;
+  const double *g2_val;
+  const int *site_order;
+  int include_zpe;
+} vb_model;
+
+/* Optional device allocator (e.g. a framework's caching allocator). */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, void *stream, void *ctx);
+  void *ctx;
+} vb_allocator;
+
+typedef struct {
+  int m_cap;          /* largest bond dimension the handle reserves memory for */
+  int dtype;          /* VB_FP64 or VB_MIXED (H_eff products in split-TF32) */
+  int pad_full;       /* mps_create: pad the product state to full bonds (<= m_cap) */
+  int krylov_cap;     /* largest Krylov dimension reserved (default 40) */
+  void *cuda_stream;  /* cudaStream_t */
+  const vb_allocator *alloc; /* NULL = cudaMalloc / cudaFree */
+} vb_mps_opts;
+
+/* Truncation (Sec. 2.1.1) and Krylov (Eq. Krylov subspace) parameters. */
+typedef struct {
+  int m_max;          /* fixed-M cap, <= m_cap */
+  double eps;         /* DBSS: discarded weight <= eps * trace (0 = off) */
+  double zero_floor;  /* always drop weights <= zero_floor * trace (0 = keep) */
+  int krylov_max;     /* <= krylov_cap */
+  double krylov_tol;  /* a-posteriori error bound of each local exponential */
+  int on_noconv;      /* 0 = continue with the last iterate, 1 = return VB_ENOCONV */
+} vb_tdvp_opts;
+
+typedef struct {
+  int max_bond;
+  double discarded_weight;  /* sum over the step's splits of the relative discarded weight */
+  int krylov_iters_max;
+  int krylov_iters_total;
+  int noconv;               /* number of local exponentials that hit krylov_max */
+} vb_sweep_stats;
+
+typedef struct vb_mpo vb_mpo;
+typedef struct vb_mps vb_mps;
+
+const char *vb_last_error(void);
+int vb_version(void);
+
+/* ---- MPO (Eq. MPO): finite-state-automaton construction from the terms.
+ * Host only until first use by an MPS (device upload is lazy), so these
+ * calls work without a GPU. */
+vb_status mpo_build(const vb_model *model, vb_mpo **out);
+vb_status mpo_destroy(vb_mpo *mpo);
+int mpo_n_sites(const vb_mpo *mpo);
+/* w_in, d, w_out of site p */
+vb_status mpo_site_dims(const vb_mpo *mpo, int site, int *w_in, int *d, int *w_out);
+/* dense real W[w_in][s_out][s_in][w_out] copied to host_out */
+vb_status mpo_site_tensor(const vb_mpo *mpo, int site, double *host_out);
+
+/* ---- MPS (Eq. MPS tensor), mixed-canonical with the center on site 0. */
+/* Product state |init_index[p]> on every site p (Sec. 3.1 initial state). */
+vb_status mps_create(const vb_mpo *mpo, const int *init_index, const vb_mps_opts *opts,
+                     vb_mps **out);
+/* Arbitrary right-canonical MPS: bond_dims[n-1]; host_tensors[p] is complex
+ * double [m_{p-1}][d_p][m_p] (m_{-1} = m_{n-1} = 1); sites 1..n-1 must be
+ * right-orthonormal (Eq. r orthonormal), site 0 carries the norm. */
+vb_status mps_create_from_tensors(const vb_mpo *mpo, const int *bond_dims,
+                                  const double *const *host_tensors,
+                                  const vb_mps_opts *opts, vb_mps **out);
+vb_status mps_destroy(vb_mps *mps);
+int mps_n_sites(const vb_mps *mps);
+vb_status mps_bond_dims(const vb_mps *mps, int *host_out /* [n-1] */);
+/* complex double [m_{p-1}][d_p][m_p] of site p copied to host_out */
+vb_status mps_get_site(const vb_mps *mps, int site, double *host_out);
+
+/* ---- one 2TDVP time step (Sec. 2.1.2): left-to-right half sweep with
+ * dt/2 then right-to-left half sweep with dt/2; the center returns to site 0. */
+vb_status tdvp2_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts,
+                      vb_sweep_stats *stats /* nullable */);
+
+/* Electronic populations P_k = <psi| |k><k| |psi> / <psi|psi> (Sec. 3.1).
+ * Needs the electronic site at chain position 0 and the center there. */
+vb_status measure_populations(const vb_mps *mps, double *pop_host /* [n_el] */);
+
+/* ---- single operations on caller-owned device buffers (complex double).
+ * These run the same kernels as tdvp2_sweep; `stream` is a cudaStream_t. */
+
+/* y[a',s',t',b'] = sum L[a',w0,a] W_i[w0,s',s,w1] W_{i+1}[w1,t',t,w2] R[b',w2,b] theta[a,s,t,b]
+ * (Eq. two-site Hamiltonian). L: [mL][w_in(i)][mL], R: [mR][w_out(i+1)][mR],
+ * theta, y: [mL][d_i][d_{i+1}][mR]. work: >= vb_heff_work_elems(...) complex. */
+vb_status vb_heff2_apply(const vb_mpo *mpo, int site_i, int mL, int mR, const double *L,
+                         const double *R, const double *theta, double *y, double *work,
+                         int dtype, void *stream);
+/* y[a',t',b'] = sum L[a',w0,a] W[w0,t',t,w1] R[b',w1,b] C[a,t,b] (Eq. one-site Hamiltonian 1) */
+vb_status vb_heff1_apply(const vb_mpo *mpo, int site, int mL, int mR, const double *L,
+                         const double *R, const double *C, double *y, double *work,
+                         int dtype, void *stream);
+/* complex elements of work needed by vb_heff2_apply (two_site=1) / vb_heff1_apply */
+size_t vb_heff_work_elems(const vb_mpo *mpo, int site, int mL, int mR, int two_site);
+/* L_new[y',v,y] = sum conj(A[x,s',y']) L[x,w,z] W[w,s',s,v] A[z,s,y] (left block of
+ * Eq. one-site Hamiltonian 1). A: [mL][d][mR], L: [mL][w_in][mL], L_new: [mR][w_out][mR]. */
+vb_status vb_env_left_update(const vb_mpo *mpo, int site, int mL, int mR, const double *L,
+                             const double *A, double *L_new, double *work, void *stream);
+/* R_new[a',w,a] = sum conj(B[a',t',y]) R[y,v,z] W[w,t',t,v] B[a,t,z].
+ * B: [mL][d][mR], R: [mR][w_out][mR], R_new: [mL][w_in][mL]. */
+vb_status vb_env_right_update(const vb_mpo *mpo, int site, int mL, int mR, const double *R,
+                              const double *B, double *R_new, double *work, void *stream);
+size_t vb_env_work_elems(const vb_mpo *mpo, int site, int mL, int mR);
+
+/* Leading eigenpairs of a Hermitian n x n matrix rho (complex double,
+ * row-major; destroyed). Householder reduction to tridiagonal form,
+ * bisection for the k_want largest eigenvalues, inverse iteration and back
+ * transformation. evals: [k_want] descending (device); evecs: [k_vec][n]
+ * (device, row j = eigenvector j); k_vec <= k_want. work: >= vb_eig_work_bytes(n, k_want). */
+vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *evals,
+                          double *evecs, void *work, void *stream);
+size_t vb_eig_work_bytes(int n, int k_want);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libvibtdvp (include/vibtdvp.h).
+
+Argument marshalling only: every step of the 2TDVP path runs in the
+library's CUDA kernels. The library is built in-tree by `build.py`; if it is
+missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvibtdvp.so")
+
+VB_OK, VB_EINVAL, VB_ENOMEM, VB_ECUDA, VB_ENOCONV, VB_ETIMEOUT, VB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+VB_FP64, VB_MIXED = 0, 1
+_NAMES = {0: "VB_OK", -1: "VB_EINVAL", -2: "VB_ENOMEM", -3: "VB_ECUDA", -4: "VB_ENOCONV",
+          -5: "VB_ETIMEOUT", -6: "VB_ESTATE"}
+
+EXPORTED = [
+    "vb_last_error", "vb_version", "mpo_build", "mpo_destroy", "mpo_n_sites", "mpo_site_dims",
+    "mpo_site_tensor", "mps_create", "mps_create_from_tensors", "mps_destroy", "mps_n_sites",
+    "mps_bond_dims", "mps_get_site", "tdvp2_sweep", "measure_populations", "vb_heff2_apply",
+    "vb_heff1_apply", "vb_heff_work_elems", "vb_env_left_update", "vb_env_right_update",
+    "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes",
+]
+
+
+class VbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class vb_model(C.Structure):
+    _fields_ = [("n_el", C.c_int), ("e0", C.POINTER(C.c_double)), ("v0", C.POINTER(C.c_double)),
+                ("n_modes", C.c_int), ("omega", C.POINTER(C.c_double)), ("levels", C.POINTER(C.c_int)),
+                ("g1", C.POINTER(C.c_double)), ("n_g2", C.c_int), ("g2_idx", C.POINTER(C.c_int)),
+                ("g2_val", C.POINTER(C.c_double)), ("site_order", C.POINTER(C.c_int)),
+                ("include_zpe", C.c_int)]
+
+
+class vb_allocator(C.Structure):
+    _fields_ = [("alloc", C.c_void_p), ("free", C.c_void_p), ("ctx", C.c_void_p)]
+
+
+class vb_mps_opts(C.Structure):
+    _fields_ = [("m_cap", C.c_int), ("dtype", C.c_int), ("pad_full", C.c_int), ("krylov_cap", C.c_int),
+                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(vb_allocator))]
+
+
+class vb_tdvp_opts(C.Structure):
+    _fields_ = [("m_max", C.c_int), ("eps", C.c_double), ("zero_floor", C.c_double),
+                ("krylov_max", C.c_int), ("krylov_tol", C.c_double), ("on_noconv", C.c_int)]
+
+
+class vb_sweep_stats(C.Structure):
+    _fields_ = [("max_bond", C.c_int), ("discarded_weight", C.c_double), ("krylov_iters_max", C.c_int),
+                ("krylov_iters_total", C.c_int), ("noconv", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1908_10588_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    sig = {
+        "vb_last_error": (C.c_char_p, []),
+        "vb_version": (i, []),
+        "mpo_build": (i, [C.POINTER(vb_model), C.POINTER(vp)]),
+        "mpo_destroy": (i, [vp]),
+        "mpo_n_sites": (i, [vp]),
+        "mpo_site_dims": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+        "mpo_site_tensor": (i, [vp, i, vp]),
+        "mps_create": (i, [vp, C.POINTER(i), C.POINTER(vb_mps_opts), C.POINTER(vp)]),
+        "mps_create_from_tensors": (i, [vp, C.POINTER(i), C.POINTER(vp), C.POINTER(vb_mps_opts), C.POINTER(vp)]),
+        "mps_destroy": (i, [vp]),
+        "mps_n_sites": (i, [vp]),
+        "mps_bond_dims": (i, [vp, C.POINTER(i)]),
+        "mps_get_site": (i, [vp, i, vp]),
+        "tdvp2_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
+        "measure_populations": (i, [vp, vp]),
+        "vb_heff2_apply": (i, [vp, i, i, i, vp, vp, vp, vp, vp, i, vp]),
+        "vb_heff1_apply": (i, [vp, i, i, i, vp, vp, vp, vp, vp, i, vp]),
+        "vb_heff_work_elems": (sz, [vp, i, i, i, i]),
+        "vb_env_left_update": (i, [vp, i, i, i, vp, vp, vp, vp, vp]),
+        "vb_env_right_update": (i, [vp, i, i, i, vp, vp, vp, vp, vp]),
+        "vb_env_work_elems": (sz, [vp, i, i, i]),
+        "vb_herm_eig_top": (i, [i, vp, i, i, vp, vp, vp, vp]),
+        "vb_eig_work_bytes": (sz, [i, i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(code):
+    if code != VB_OK:
+        msg = lib().vb_last_error()
+        raise VbError(code, msg.decode() if msg else "")
+
+
+def _dp(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------- MPO
+class Mpo:
+    """MPO of a vibronic model dict (see vibmodels); owns the C handle."""
+
+    def __init__(self, model: dict):
+        L = lib()
+        n_el = int(model["n_el"])
+        omega = np.ascontiguousarray(model["omega"], dtype=np.float64)
+        nm = omega.size
+        self._keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        e0 = arr(model["e0"], np.float64)
+        v0 = arr(model["v0"], np.float64).reshape(-1)
+        lev = arr(model["levels"], np.int32)
+        g1 = arr(model["g1"], np.float64).reshape(-1)
+        g2 = model["g2"]
+        g2i = arr(np.array([[I, J, i, j] for (I, J, i, j, _) in g2], dtype=np.int32).reshape(-1, 4), np.int32)
+        g2v = arr(np.array([v for (*_, v) in g2], dtype=np.float64), np.float64)
+        so = model.get("site_order")
+        m = vb_model()
+        m.n_el = n_el
+        m.e0 = _dp(e0, C.c_double)
+        m.v0 = _dp(v0, C.c_double)
+        m.n_modes = nm
+        om = arr(omega, np.float64)
+        m.omega = _dp(om, C.c_double)
+        m.levels = _dp(lev, C.c_int)
+        m.g1 = _dp(g1, C.c_double)
+        m.n_g2 = len(g2)
+        m.g2_idx = _dp(g2i, C.c_int) if len(g2) else None
+        m.g2_val = _dp(g2v, C.c_double) if len(g2) else None
+        if so is not None:
+            soa = arr(so, np.int32)
+            m.site_order = _dp(soa, C.c_int)
+        else:
+            m.site_order = None
+        m.include_zpe = int(model.get("include_zpe", 1))
+        h = C.c_void_p()
+        check(L.mpo_build(C.byref(m), C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    @property
+    def n_sites(self) -> int:
+        return lib().mpo_n_sites(self.h)
+
+    def site_dims(self, p: int):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        check(lib().mpo_site_dims(self.h, p, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def site_tensor(self, p: int) -> np.ndarray:
+        wl, d, wr = self.site_dims(p)
+        out = np.zeros((wl, d, d, wr))
+        check(lib().mpo_site_tensor(self.h, p, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.h:
+            lib().mpo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- MPS
+class Mps:
+    """MPS handle (center on site 0) with its device buffers."""
+
+    def __init__(self, mpo: Mpo, init_index=None, m_cap: int = 64, dtype: int = VB_FP64,
+                 pad_full: bool = False, krylov_cap: int = 40, stream=None, tensors=None):
+        L = lib()
+        self.mpo = mpo
+        o = vb_mps_opts()
+        o.m_cap = m_cap
+        o.dtype = dtype
+        o.pad_full = int(pad_full)
+        o.krylov_cap = krylov_cap
+        o.cuda_stream = _stream_ptr(stream)
+        o.alloc = None
+        h = C.c_void_p()
+        if tensors is None:
+            idx = (C.c_int * mpo.n_sites)(*[int(x) for x in init_index])
+            check(L.mps_create(mpo.h, idx, C.byref(o), C.byref(h)))
+        else:
+            ts = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+            bonds = (C.c_int * max(1, len(ts) - 1))(*[t.shape[2] for t in ts[:-1]])
+            ptrs = (C.c_void_p * len(ts))(*[t.ctypes.data for t in ts])
+            check(L.mps_create_from_tensors(mpo.h, bonds, ptrs, C.byref(o), C.byref(h)))
+        self.h = h
+
+    @property
+    def n_sites(self) -> int:
+        return lib().mps_n_sites(self.h)
+
+    def bond_dims(self):
+        n = self.n_sites
+        out = (C.c_int * max(1, n - 1))()
+        check(lib().mps_bond_dims(self.h, out))
+        return list(out)[: n - 1]
+
+    def site(self, p: int) -> np.ndarray:
+        dims = [self.mpo.site_dims(q)[1] for q in range(self.n_sites)]
+        b = [1] + self.bond_dims() + [1]
+        out = np.zeros((b[p], dims[p], b[p + 1]), dtype=np.complex128)
+        check(lib().mps_get_site(self.h, p, out.ctypes.data))
+        return out
+
+    def tensors(self):
+        return [self.site(p) for p in range(self.n_sites)]
+
+    def sweep(self, dt_fs: float, m_max: int, eps: float = 0.0, zero_floor: float = 1e-14,
+              krylov_max: int = 30, krylov_tol: float = 1e-13, on_noconv: int = 0):
+        o = vb_tdvp_opts(m_max, eps, zero_floor, krylov_max, krylov_tol, on_noconv)
+        st = vb_sweep_stats()
+        check(lib().tdvp2_sweep(self.h, self.mpo.h, float(dt_fs), C.byref(o), C.byref(st)))
+        return st
+
+    def populations(self) -> np.ndarray:
+        n_el = self.mpo.site_dims(0)[1]
+        out = np.zeros(n_el)
+        check(lib().measure_populations(self.h, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.h:
+            lib().mps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------- single operations (device ptrs)
+def vb_heff_work_elems(mpo: Mpo, site: int, mL: int, mR: int, two_site: bool) -> int:
+    return int(lib().vb_heff_work_elems(mpo.h, site, mL, mR, int(two_site)))
+
+
+def vb_heff2_apply(mpo: Mpo, i, mL, mR, L, R, theta, y, work, dtype=VB_FP64, stream=None):
+    check(lib().vb_heff2_apply(mpo.h, i, mL, mR, _ptr(L), _ptr(R), _ptr(theta), _ptr(y), _ptr(work),
+                               dtype, _stream_ptr(stream)))
+
+
+def vb_heff1_apply(mpo: Mpo, j, mL, mR, L, R, Cc, y, work, dtype=VB_FP64, stream=None):
+    check(lib().vb_heff1_apply(mpo.h, j, mL, mR, _ptr(L), _ptr(R), _ptr(Cc), _ptr(y), _ptr(work),
+                               dtype, _stream_ptr(stream)))
+
+
+def vb_env_work_elems(mpo: Mpo, site, mL, mR) -> int:
+    return int(lib().vb_env_work_elems(mpo.h, site, mL, mR))
+
+
+def vb_env_left_update(mpo: Mpo, p, mL, mR, L, A, Lnew, work, stream=None):
+    check(lib().vb_env_left_update(mpo.h, p, mL, mR, _ptr(L), _ptr(A), _ptr(Lnew), _ptr(work),
+                                   _stream_ptr(stream)))
+
+
+def vb_env_right_update(mpo: Mpo, p, mL, mR, R, B, Rnew, work, stream=None):
+    check(lib().vb_env_right_update(mpo.h, p, mL, mR, _ptr(R), _ptr(B), _ptr(Rnew), _ptr(work),
+                                    _stream_ptr(stream)))
+
+
+def vb_eig_work_bytes(n, k_want) -> int:
+    return int(lib().vb_eig_work_bytes(n, k_want))
+
+
+def vb_herm_eig_top(n, rho, k_want, k_vec, evals, evecs, work, stream=None):
+    check(lib().vb_herm_eig_top(n, _ptr(rho), k_want, k_vec, _ptr(evals), _ptr(evecs), _ptr(work),
+                                _stream_ptr(stream)))

@@ -1,0 +1,192 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vibtdvp.h"
+
+namespace vb {
+
+// ------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+const char *get_error();
+
+#define VB_TRY_CUDA(call)                                                        \
+  do {                                                                           \
+    cudaError_t _e = (call);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      ::vb::set_error(std::string(#call) + ": " + cudaGetErrorString(_e) + " (" + \
+                      __FILE__ + ":" + std::to_string(__LINE__) + ")");          \
+      return VB_ECUDA;                                                           \
+    }                                                                            \
+  } while (0)
+
+#define VB_TRY(call)               \
+  do {                             \
+    vb_status _s = (call);         \
+    if (_s != VB_OK) return _s;    \
+  } while (0)
+
+#define VB_CHECK_LAUNCH() VB_TRY_CUDA(cudaGetLastError())
+
+inline vb_status fail(vb_status s, const std::string &msg) {
+  set_error(msg);
+  return s;
+}
+
+// ------------------------------------------------------------ complex
+struct __align__(16) cd {
+  double x, y;
+};
+
+__host__ __device__ inline cd mkc(double a, double b) {
+  cd r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+__host__ __device__ inline cd cadd(cd a, cd b) { return mkc(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline cd csub(cd a, cd b) { return mkc(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline cd cmul(cd a, cd b) {
+  return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline cd cconj(cd a) { return mkc(a.x, -a.y); }
+__host__ __device__ inline cd cscale(cd a, double s) { return mkc(a.x * s, a.y * s); }
+// conj(a) * b
+__host__ __device__ inline cd cdotc(cd a, cd b) {
+  return mkc(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
+
+// ------------------------------------------------------------ memory
+struct Alloc {
+  const vb_allocator *user = nullptr;
+  cudaStream_t stream = nullptr;
+  vb_status get(void **p, size_t bytes);
+  void put(void *p);
+};
+
+// Device buffer owned by a handle.
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  template <class T>
+  T *as() const {
+    return reinterpret_cast<T *>(p);
+  }
+};
+
+// ------------------------------------------------------------ GEMM
+// op codes for the strided batched complex GEMM
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2 /* conj transpose */, OP_R = 3 /* conj, no transpose */ };
+
+struct GemmArgs {
+  int M, N, K, batch;
+  int opA, opB;
+  const cd *A;
+  long long lda, sA;
+  const cd *B;
+  long long ldb, sB;
+  cd *C;
+  long long ldc, sC;
+  cd alpha, beta;
+  // element counts of the three buffers (required); every address the
+  // kernel forms is checked against them on the host before the launch
+  long long a_size, b_size, c_size;
+};
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; op(A) is M x K, op(B) is K x N.
+vb_status zgemm(const GemmArgs &g, cudaStream_t st);
+
+// ------------------------------------------------------------ MPO
+struct MpoBlock {
+  int win, wout;
+  int ident;   // operator is the identity
+  int op_off;  // offset (in doubles) of the d x d operator [s_out][s_in]
+};
+
+struct MpoSite {
+  int wl = 0, d = 0, wr = 0;
+  std::vector<double> dense;  // [wl][d][d][wr]
+  std::vector<MpoBlock> blocks;
+  std::vector<double> ops;  // concatenated non-identity operators
+  // device copies: operators, and for each direction a CSR over the produced
+  // bond index: entries (consumed index, ident, op_off)
+  double *d_ops = nullptr;
+  int *d_fwd_ptr = nullptr, *d_fwd_ent = nullptr;  // produce w_out from w_in
+  int *d_bwd_ptr = nullptr, *d_bwd_ent = nullptr;  // produce w_in from w_out
+  long long nnz_ops = 0;                           // non-identity blocks
+  long long n_ident = 0;
+};
+
+}  // namespace vb
+
+struct vb_mpo {
+  int n = 0;
+  int n_el = 0;
+  int el_pos = 0;
+  std::vector<int> dims;
+  std::vector<vb::MpoSite> sites;
+  int max_w = 0;
+  int max_d = 0;
+  bool uploaded = false;
+  int device = -1;
+  std::vector<void *> dev_allocs;
+};
+
+namespace vb {
+vb_status mpo_upload(const vb_mpo *mpo);
+
+// Sparse MPO application, one site:
+//  dir 0: Y[p, s', wo, q] = sum_{blocks wi->wo} sum_s O[s', s] X[p, wi, s, q]
+//  dir 1: Y[p, s', wi, q] = sum_{blocks wi->wo} sum_s O[s', s] X[p, wo, s, q]
+struct WStrides {
+  long long p, w, s, q;
+};
+// strides named explicitly: WS(p=..., w=..., s=..., q=...)
+inline WStrides WS(long long p, long long w, long long s, long long q) { return WStrides{p, w, s, q}; }
+// x_size / y_size: element counts of X and Y; the largest offset the kernel
+// forms is checked against them before the launch
+vb_status wapply(const MpoSite &site, int dir, const cd *X, WStrides xs, long long x_size, cd *Y,
+                 WStrides ys, long long y_size, int P, int Q, cudaStream_t st);
+
+// ------------------------------------------------------------ vectors
+vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
+                        cd *partial, int n_part, cudaStream_t st);
+// w -= sum_j c[j] V[j] (sign = -1) or w += ... (sign = +1); c on device; cscale applied
+vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
+                         long long n, cudaStream_t st);
+vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
+                    cudaStream_t st);
+// x *= 1/ (*nrm)  (device scalar)
+vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st);
+// y = s * x with s = *num / *den (device scalars; den may be null -> 1)
+vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st);
+// combine: y = (*nrm) * sum_j u[j] V[j]
+vb_status vec_combine(const cd *V, long long ldv, int nv, const cd *u, const double *nrm, cd *y,
+                      long long n, cudaStream_t st);
+int reduce_parts(long long n);
+
+// ------------------------------------------------------------ eigen
+struct EigWork {
+  // layout inside one device buffer
+  static size_t bytes(int n, int k_want);
+};
+// phase 1: reduce rho (n x n, destroyed) to real tridiagonal form and compute
+// the k_want largest eigenvalues (descending) into evals (device)
+vb_status eig_values(int n, cd *rho, int k_want, double *evals, void *work, cudaStream_t st);
+// phase 2: eigenvectors for the first k_vec of those eigenvalues, written as
+// rows of evecs [k_vec][n] (device). Needs the same rho/work after phase 1.
+vb_status eig_vectors(int n, const cd *rho, int k_want, int k_vec, const double *evals,
+                      cd *evecs, void *work, cudaStream_t st);
+
+// Krylov tridiagonal exponential: from alpha[0..k], beta[0..k-1] (device),
+// u = exp(-i T tau) e_1 (k+1 complex) and err = bnext * |u_k| written to
+// out_err (device or mapped host).
+vb_status tridiag_expm(const double *alpha, const double *beta, int kdim, double tau,
+                       const double *bnext, cd *u, double *out_err, cudaStream_t st);
+
+}  // namespace vb

@@ -1,0 +1,422 @@
+// Leading eigenpairs of the Hermitian reduced density matrix used to split
+// and truncate the two-site tensor (Sec. 2.1.1: truncation by fixed M or by
+// DBSS, which both keep the largest Schmidt weights).
+//
+// Pipeline, all FP64 on the GPU:
+//  1. Householder reduction rho = Q T Q^+ (T Hermitian tridiagonal), one
+//     column per step: reflector, Hermitian matrix-vector product, the
+//     rank-2 update of the trailing block. Reflectors are kept row-wise in a
+//     separate n x n buffer for coalesced back-transformation.
+//  2. A diagonal unitary D makes T real: T' = D^+ T D with |e_j| off the
+//     diagonal.
+//  3. Bisection with Sturm counts gives the k_want largest eigenvalues.
+//  4. Inverse iteration (tridiagonal LU with partial pivoting), run for all
+//     requested vectors in parallel, alternated with an in-order block
+//     Gram-Schmidt (two passes) so that clustered eigenvalues get an
+//     orthonormal basis of their invariant subspace.
+//  5. Back-transformation z = Q D y.
+#include "common.h"
+
+namespace vb {
+namespace {
+
+constexpr int INVIT_ROUNDS = 3;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum, result broadcast to all threads
+__device__ double block_sum_all(double v, double *sh) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double r = lane < nw ? sh[lane] : 0.0;
+    r = warp_sum(r);
+    if (lane == 0) sh[32] = r;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+struct EigLayout {
+  size_t off_vref, off_tau, off_dg, off_ec, off_eabs, off_delta, off_p, off_y, off_lu, total;
+  EigLayout(int n, int k) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      size_t r = o;
+      o += (bytes + 255) / 256 * 256;
+      return r;
+    };
+    off_vref = take((size_t)n * n * sizeof(cd));
+    off_tau = take((size_t)n * sizeof(double));
+    off_dg = take((size_t)n * sizeof(double));
+    off_ec = take((size_t)n * sizeof(cd));
+    off_eabs = take((size_t)n * sizeof(double));
+    off_delta = take((size_t)n * sizeof(cd));
+    off_p = take((size_t)n * sizeof(cd));
+    off_y = take((size_t)k * n * sizeof(double));
+    off_lu = take((size_t)k * n * 5 * sizeof(double) + (size_t)k * n * sizeof(int));
+    total = o;
+  }
+};
+
+// ---- 1. Householder reduction, one column j (trailing size m = n - j - 1 >= 2)
+__global__ void hh_vector(cd *A, int n, int j, cd *vref, double *tau, double *dg, cd *ec) {
+  __shared__ double sh[33];
+  const int m = n - j - 1;
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += cabs2(A[(long long)(j + 1 + i) * n + j]);
+  const double sigma = block_sum_all(s, sh);
+  const cd alpha = A[(long long)(j + 1) * n + j];
+  cd *v = vref + (long long)j * n + j + 1;
+  if (sigma == 0.0) {
+    if (threadIdx.x == 0) {
+      tau[j] = 0.0;
+      ec[j] = alpha;
+      dg[j] = A[(long long)j * n + j].x;
+    }
+    return;
+  }
+  const double aa = sqrt(cabs2(alpha));
+  const double nx = sqrt(aa * aa + sigma);
+  const cd ph = aa > 0.0 ? mkc(alpha.x / aa, alpha.y / aa) : mkc(1.0, 0.0);
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    v[i] = (i == 0) ? cscale(ph, aa + nx) : A[(long long)(j + 1 + i) * n + j];
+  if (threadIdx.x == 0) {
+    tau[j] = 1.0 / (nx * (nx + aa));
+    ec[j] = cscale(ph, -nx);
+    dg[j] = A[(long long)j * n + j].x;
+  }
+}
+
+// p = tau A22 v (one warp per row of the trailing block)
+__global__ void hh_symv(const cd *A, int n, int j, const cd *vref, const double *tau, cd *p) {
+  const double t = tau[j];
+  const int m = n - j - 1;
+  const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= m || t == 0.0) return;
+  const cd *row = A + (long long)(j + 1 + r) * n + j + 1;
+  const cd *v = vref + (long long)j * n + j + 1;
+  double sx = 0.0, sy = 0.0;
+  for (int c = lane; c < m; c += 32) {
+    cd a = row[c], b = v[c];
+    sx = fma(a.x, b.x, fma(-a.y, b.y, sx));
+    sy = fma(a.x, b.y, fma(a.y, b.x, sy));
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  if (lane == 0) p[r] = mkc(t * sx, t * sy);
+}
+
+// w = p - (tau/2) (v^+ p) v, in place in p
+__global__ void hh_wvec(int n, int j, const cd *vref, const double *tau, cd *p) {
+  __shared__ double sh[33];
+  const double t = tau[j];
+  if (t == 0.0) return;
+  const int m = n - j - 1;
+  const cd *v = vref + (long long)j * n + j + 1;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    cd a = v[c], b = p[c];
+    s += a.x * b.x + a.y * b.y;  // Re(conj(v) p)
+  }
+  const double K = 0.5 * t * block_sum_all(s, sh);
+  for (int c = threadIdx.x; c < m; c += blockDim.x) p[c] = csub(p[c], cscale(v[c], K));
+}
+
+// A22 -= v w^+ + w v^+
+__global__ void hh_rank2(cd *A, int n, int j, const cd *vref, const double *tau, const cd *w) {
+  if (tau[j] == 0.0) return;
+  const int m = n - j - 1;
+  const int r = blockIdx.y;
+  const cd *v = vref + (long long)j * n + j + 1;
+  const cd vr = v[r], wr = w[r];
+  cd *row = A + (long long)(j + 1 + r) * n + j + 1;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    cd vc = v[c], wc = w[c];
+    cd x = cadd(cmul(vr, cconj(wc)), cmul(wr, cconj(vc)));
+    row[c] = csub(row[c], x);
+  }
+}
+
+// ---- 2. last diagonal / off-diagonal entries, |e| and the phases of D
+__global__ void tri_finish(const cd *A, int n, double *tau, double *dg, cd *ec, double *eabs,
+                           cd *delta) {
+  if (threadIdx.x != 0) return;
+  if (n >= 2) {
+    dg[n - 2] = A[(long long)(n - 2) * n + n - 2].x;
+    ec[n - 2] = A[(long long)(n - 1) * n + n - 2];
+    tau[n - 2] = 0.0;
+  }
+  dg[n - 1] = A[(long long)(n - 1) * n + n - 1].x;
+  tau[n - 1] = 0.0;
+  delta[0] = mkc(1.0, 0.0);
+  for (int j = 0; j + 1 < n; ++j) {
+    double a = sqrt(cabs2(ec[j]));
+    eabs[j] = a;
+    delta[j + 1] = a > 0.0 ? cmul(delta[j], mkc(ec[j].x / a, ec[j].y / a)) : delta[j];
+  }
+  eabs[n - 1] = 0.0;
+}
+
+// ---- 3. bisection: evals[t] = (t)-th largest eigenvalue of T'
+__device__ int sturm_count(const double *dg, const double *e, int n, double x, double pivmin) {
+  // number of eigenvalues < x
+  int cnt = 0;
+  double q = dg[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = dg[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void bisect_kernel(const double *dg, const double *e, int n, int k_want,
+                              double *evals) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k_want) return;
+  double lo = 1e300, hi = -1e300, emax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? e[i - 1] : 0.0) + (i + 1 < n ? e[i] : 0.0);
+    lo = fmin(lo, dg[i] - r);
+    hi = fmax(hi, dg[i] + r);
+    emax = fmax(emax, fabs(dg[i]) + r);
+  }
+  const double tnorm = fmax(emax, 1e-300);
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, tnorm * tnorm);
+  lo -= 2.0 * 2.220446049250313e-16 * tnorm * n + 1e-300;
+  hi += 2.0 * 2.220446049250313e-16 * tnorm * n + 1e-300;
+  const int target = n - 1 - t;  // ascending index
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (hi - lo <= 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + 1e-18 * tnorm) break;
+    int c = sturm_count(dg, e, n, mid, pivmin);
+    if (c > target)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  evals[t] = 0.5 * (lo + hi);
+}
+
+// ---- 4. inverse iteration, one thread per vector
+__device__ __forceinline__ double hash_unit(int t, int i) {
+  unsigned int h = (unsigned int)(t * 7919 + 17) * 2654435761u ^ (unsigned int)(i + 1) * 2246822519u;
+  h ^= h >> 15;
+  h *= 2654435761u;
+  h ^= h >> 13;
+  return (double)(h & 0xFFFFFF) / (double)0x1000000 * 2.0 - 1.0;
+}
+
+__global__ void invit_round(const double *dg, const double *e, int n, int k_vec,
+                            const double *evals, double *Y, double *lu, int *piv, int round) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k_vec) return;
+  double *y = Y + (long long)t * n;
+  double *dl = lu + (long long)t * n * 4;
+  double *dd = dl + n, *du = dd + n, *du2 = du + n;
+  int *pv = piv + (long long)t * n;
+  double tnorm = 0.0;
+  for (int i = 0; i < n; ++i)
+    tnorm = fmax(tnorm, fabs(dg[i]) + (i > 0 ? e[i - 1] : 0.0) + (i + 1 < n ? e[i] : 0.0));
+  const double pivmin = fmax(tnorm * 2.220446049250313e-16, 1e-300);
+  const double lam = evals[t];
+  if (round == 0) {
+    // factor T' - lam I = P L U once
+    for (int i = 0; i < n; ++i) {
+      dd[i] = dg[i] - lam;
+      if (i + 1 < n) {
+        dl[i] = e[i];
+        du[i] = e[i];
+      }
+      du2[i] = 0.0;
+      pv[i] = 0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        if (dd[i] == 0.0) dd[i] = pivmin;
+        double l = dl[i] / dd[i];
+        dl[i] = l;
+        dd[i + 1] -= l * du[i];
+        pv[i] = 0;
+      } else {
+        double l = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = l;
+        double tmp = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = tmp - l * dd[i + 1];
+        if (i + 2 < n) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -l * du[i + 1];
+        }
+        pv[i] = 1;
+      }
+    }
+    if (dd[n - 1] == 0.0) dd[n - 1] = pivmin;
+    for (int i = 0; i < n; ++i) y[i] = hash_unit(t, i);
+  }
+  // solve (T' - lam I) y_new = y
+  for (int i = 0; i + 1 < n; ++i) {
+    if (pv[i]) {
+      double tmp = y[i];
+      y[i] = y[i + 1];
+      y[i + 1] = tmp;
+    }
+    y[i + 1] -= dl[i] * y[i];
+  }
+  // back substitution; the system is linear, so the whole vector may be
+  // rescaled whenever a component grows large (near-singular shifts)
+  for (int i = n - 1; i >= 0; --i) {
+    double v = y[i];
+    if (i + 1 < n) v -= du[i] * y[i + 1];
+    if (i + 2 < n) v -= du2[i] * y[i + 2];
+    v /= dd[i];
+    y[i] = v;
+    if (fabs(v) > 1e150)
+      for (int q = 0; q < n; ++q) y[q] *= 1e-150;
+  }
+  // normalise (guard against overflow by scaling with the max first)
+  double mx = 0.0;
+  for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(y[i]));
+  if (mx == 0.0) mx = 1.0;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    y[i] /= mx;
+    s += y[i] * y[i];
+  }
+  s = 1.0 / sqrt(s);
+  for (int i = 0; i < n; ++i) y[i] *= s;
+}
+
+// in-order two-pass Gram-Schmidt of the rows of Y (descending eigenvalues)
+__global__ void cgs2_rows(double *Y, int n, int k) {
+  __shared__ double sh[33];
+  __shared__ double coef[128];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = 0; t < k; ++t) {
+    double *yt = Y + (long long)t * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int s = wid; s < t; s += nw) {
+        const double *ys = Y + (long long)s * n;
+        double d = 0.0;
+        for (int i = lane; i < n; i += 32) d += ys[i] * yt[i];
+        d = warp_sum(d);
+        if (lane == 0) coef[s] = d;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = yt[i];
+        for (int s = 0; s < t; ++s) v -= coef[s] * Y[(long long)s * n + i];
+        yt[i] = v;
+      }
+      __syncthreads();
+    }
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ss += yt[i] * yt[i];
+    ss = block_sum_all(ss, sh);
+    const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) yt[i] *= inv;
+    __syncthreads();
+  }
+}
+
+// ---- 5. z_t = Q D y_t, one block per vector
+__global__ void backtransform(const cd *vref, const double *tau, const cd *delta, const double *Y,
+                              int n, cd *Z) {
+  __shared__ double sh[33];
+  const int t = blockIdx.x;
+  const double *y = Y + (long long)t * n;
+  cd *z = Z + (long long)t * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = cscale(delta[i], y[i]);
+  __syncthreads();
+  for (int j = n - 3; j >= 0; --j) {
+    const double tj = tau[j];
+    if (tj == 0.0) continue;
+    const cd *v = vref + (long long)j * n;
+    double sx = 0.0, sy = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      cd a = v[i], b = z[i];
+      sx += a.x * b.x + a.y * b.y;
+      sy += a.x * b.y - a.y * b.x;
+    }
+    sx = block_sum_all(sx, sh);
+    sy = block_sum_all(sy, sh);
+    const cd f = mkc(tj * sx, tj * sy);
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) z[i] = csub(z[i], cmul(v[i], f));
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t EigWork::bytes(int n, int k_want) { return EigLayout(n, k_want).total; }
+
+vb_status eig_values(int n, cd *rho, int k_want, double *evals, void *work, cudaStream_t st) {
+  if (n < 1 || k_want < 1 || k_want > n) return fail(VB_EINVAL, "eig_values: bad n / k_want");
+  EigLayout lay(n, k_want);
+  char *w = static_cast<char *>(work);
+  cd *vref = reinterpret_cast<cd *>(w + lay.off_vref);
+  double *tau = reinterpret_cast<double *>(w + lay.off_tau);
+  double *dg = reinterpret_cast<double *>(w + lay.off_dg);
+  cd *ec = reinterpret_cast<cd *>(w + lay.off_ec);
+  double *eabs = reinterpret_cast<double *>(w + lay.off_eabs);
+  cd *delta = reinterpret_cast<cd *>(w + lay.off_delta);
+  cd *p = reinterpret_cast<cd *>(w + lay.off_p);
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    hh_vector<<<1, 256, 0, st>>>(rho, n, j, vref, tau, dg, ec);
+    VB_CHECK_LAUNCH();
+    hh_symv<<<(m + 7) / 8, 256, 0, st>>>(rho, n, j, vref, tau, p);
+    VB_CHECK_LAUNCH();
+    hh_wvec<<<1, 256, 0, st>>>(n, j, vref, tau, p);
+    VB_CHECK_LAUNCH();
+    dim3 g2((m + 255) / 256, m);
+    hh_rank2<<<g2, 256, 0, st>>>(rho, n, j, vref, tau, p);
+    VB_CHECK_LAUNCH();
+  }
+  tri_finish<<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
+  VB_CHECK_LAUNCH();
+  bisect_kernel<<<(k_want + 63) / 64, 64, 0, st>>>(dg, eabs, n, k_want, evals);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status eig_vectors(int n, const cd *rho, int k_want, int k_vec, const double *evals, cd *evecs,
+                      void *work, cudaStream_t st) {
+  (void)rho;
+  if (k_vec < 1 || k_vec > k_want) return fail(VB_EINVAL, "eig_vectors: bad k_vec");
+  if (k_vec > 128) return fail(VB_EINVAL, "eig_vectors: at most 128 vectors");
+  EigLayout lay(n, k_want);
+  char *w = static_cast<char *>(work);
+  cd *vref = reinterpret_cast<cd *>(w + lay.off_vref);
+  double *tau = reinterpret_cast<double *>(w + lay.off_tau);
+  double *dg = reinterpret_cast<double *>(w + lay.off_dg);
+  double *eabs = reinterpret_cast<double *>(w + lay.off_eabs);
+  cd *delta = reinterpret_cast<cd *>(w + lay.off_delta);
+  double *Y = reinterpret_cast<double *>(w + lay.off_y);
+  double *lu = reinterpret_cast<double *>(w + lay.off_lu);
+  int *piv = reinterpret_cast<int *>(lu + (size_t)k_want * n * 4);
+  for (int r = 0; r < INVIT_ROUNDS; ++r) {
+    invit_round<<<(k_vec + 31) / 32, 32, 0, st>>>(dg, eabs, n, k_vec, evals, Y, lu, piv, r);
+    VB_CHECK_LAUNCH();
+    cgs2_rows<<<1, 512, 0, st>>>(Y, n, k_vec);
+    VB_CHECK_LAUNCH();
+  }
+  backtransform<<<k_vec, 256, 0, st>>>(vref, tau, delta, Y, n, evecs);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+}  // namespace vb

@@ -1,0 +1,146 @@
+// Strided batched complex double GEMM on the CUDA cores (FP64 path).
+//
+// Every dense contraction of the FP64 2TDVP path (the L and R legs of
+// H_eff, the environment updates, the merge of two sites, the reduced
+// density matrix and the split) is one call of this kernel with the right
+// operand views. GB300 has no FP64 tensor-core MMA kind, so this path runs
+// on the FP64 FMA units; the mixed-precision path replaces the H_eff legs
+// with tensor-core products.
+#include "common.h"
+
+namespace vb {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
+
+__device__ __forceinline__ cd ldA(const cd *A, int op, long long lda, int i, int k) {
+  // op(A)[i,k]
+  cd v;
+  if (op == OP_N || op == OP_R)
+    v = A[(long long)i * lda + k];
+  else
+    v = A[(long long)k * lda + i];
+  if (op == OP_C || op == OP_R) v.y = -v.y;
+  return v;
+}
+
+__device__ __forceinline__ cd ldB(const cd *B, int op, long long ldb, int k, int j) {
+  // op(B)[k,j]
+  cd v;
+  if (op == OP_N || op == OP_R)
+    v = B[(long long)k * ldb + j];
+  else
+    v = B[(long long)j * ldb + k];
+  if (op == OP_C || op == OP_R) v.y = -v.y;
+  return v;
+}
+
+__global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
+  __shared__ cd As[BK][BM + 1];
+  __shared__ cd Bs[BK][BN + 1];
+  const int b = blockIdx.z;
+  const cd *A = g.A + (long long)b * g.sA;
+  const cd *B = g.B + (long long)b * g.sB;
+  cd *C = g.C + (long long)b * g.sC;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const bool a_kfast = (g.opA == OP_N || g.opA == OP_R);
+  const bool b_jfast = (g.opB == OP_N || g.opB == OP_R);
+  cd acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = mkc(0.0, 0.0);
+
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int l = tid + r * NT;
+      int ii, kk;
+      if (a_kfast) {
+        kk = l % BK;
+        ii = l / BK;
+      } else {
+        ii = l % BM;
+        kk = l / BM;
+      }
+      int gi = i0 + ii, gk = k0 + kk;
+      As[kk][ii] = (gi < g.M && gk < g.K) ? ldA(A, g.opA, g.lda, gi, gk) : mkc(0.0, 0.0);
+      int jj;
+      if (b_jfast) {
+        jj = l % BN;
+        kk = l / BN;
+      } else {
+        kk = l % BK;
+        jj = l / BK;
+      }
+      int gj = j0 + jj;
+      gk = k0 + kk;
+      Bs[kk][jj] = (gj < g.N && gk < g.K) ? ldB(B, g.opB, g.ldb, gk, gj) : mkc(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cd a[4], bb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bb[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[r][c].x = fma(a[r].x, bb[c].x, acc[r][c].x);
+          acc[r][c].x = fma(-a[r].y, bb[c].y, acc[r][c].x);
+          acc[r][c].y = fma(a[r].x, bb[c].y, acc[r][c].y);
+          acc[r][c].y = fma(a[r].y, bb[c].x, acc[r][c].y);
+        }
+    }
+    __syncthreads();
+  }
+  const bool beta0 = (g.beta.x == 0.0 && g.beta.y == 0.0);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int gi = i0 + ty + 16 * r;
+    if (gi >= g.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int gj = j0 + tx + 16 * c;
+      if (gj >= g.N) continue;
+      cd v = cmul(g.alpha, acc[r][c]);
+      long long o = (long long)gi * g.ldc + gj;
+      if (!beta0) v = cadd(v, cmul(g.beta, C[o]));
+      C[o] = v;
+    }
+  }
+}
+
+}  // namespace
+
+vb_status zgemm(const GemmArgs &g, cudaStream_t st) {
+  if (g.M < 0 || g.N < 0 || g.K < 0 || g.batch < 0)
+    return fail(VB_EINVAL, "zgemm: negative size");
+  if (g.M == 0 || g.N == 0 || g.batch == 0) return VB_OK;
+  if (g.batch > 65535) return fail(VB_EINVAL, "zgemm: batch > 65535");
+  if ((g.M + BM - 1) / BM > 65535) return fail(VB_EINVAL, "zgemm: M too large");
+  {
+    const bool at = !(g.opA == OP_N || g.opA == OP_R), bt = !(g.opB == OP_N || g.opB == OP_R);
+    const long long amax = (long long)(g.batch - 1) * g.sA +
+                           (at ? (long long)(g.K - 1) * g.lda + (g.M - 1) : (long long)(g.M - 1) * g.lda + (g.K - 1));
+    const long long bmax = (long long)(g.batch - 1) * g.sB +
+                           (bt ? (long long)(g.N - 1) * g.ldb + (g.K - 1) : (long long)(g.K - 1) * g.ldb + (g.N - 1));
+    const long long cmax = (long long)(g.batch - 1) * g.sC + (long long)(g.M - 1) * g.ldc + (g.N - 1);
+    if ((g.K > 0 && g.a_size > 0 && amax >= g.a_size) || (g.K > 0 && g.b_size > 0 && bmax >= g.b_size) ||
+        (g.c_size > 0 && cmax >= g.c_size))
+      return fail(VB_EINVAL, "zgemm: operand view exceeds its buffer");
+    if (g.a_size <= 0 || g.b_size <= 0 || g.c_size <= 0)
+      return fail(VB_EINVAL, "zgemm: buffer sizes must be given");
+  }
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+  zgemm_kernel<<<grid, NT, 0, st>>>(g);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+}  // namespace vb

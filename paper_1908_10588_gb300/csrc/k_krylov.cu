@@ -1,0 +1,302 @@
+// Krylov-space kernels of the local exponential (Eq. Krylov subspace):
+// block inner products against all basis vectors, the matching update, norms,
+// scaling, the final combination theta' = |theta| sum_k u_k v_k, and the
+// exponential of the small tridiagonal Lanczos matrix. All in FP64 with
+// deterministic (fixed-order) reductions.
+#include "common.h"
+
+namespace vb {
+namespace {
+
+constexpr int RT = 256;  // threads per reduction block
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of one double per thread; result valid in thread 0
+__device__ double block_sum(double v, double *sh) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// partial[b * nv + j] = sum over block b's chunk of conj(V_j[i]) w[i]
+__global__ void __launch_bounds__(RT) multi_dot_part(const cd *__restrict__ V, long long ldv, int nv,
+                                                     const cd *__restrict__ w, long long n,
+                                                     cd *__restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  for (int j = 0; j < nv; ++j) {
+    const cd *v = V + j * ldv;
+    double sx = 0.0, sy = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += RT) {
+      cd a = v[i], b = w[i];
+      sx = fma(a.x, b.x, fma(a.y, b.y, sx));
+      sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
+    }
+    double rx = block_sum(sx, sh);
+    double ry = block_sum(sy, sh);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.x * nv + j] = mkc(rx, ry);
+  }
+}
+
+__global__ void reduce_parts_cd(const cd *__restrict__ partial, int n_part, int nv, cd *out) {
+  // one warp per output j
+  int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (j >= nv) return;
+  double sx = 0.0, sy = 0.0;
+  for (int b = lane; b < n_part; b += 32) {
+    cd p = partial[(long long)b * nv + j];
+    sx += p.x;
+    sy += p.y;
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  if (lane == 0) out[j] = mkc(sx, sy);
+}
+
+__global__ void multi_axpy_kernel(const cd *__restrict__ V, long long ldv, int nv,
+                                  const cd *__restrict__ c, double sign, cd *__restrict__ w,
+                                  long long n) {
+  __shared__ cd cs[128];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = c[j];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double ax = 0.0, ay = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      cd v = V[j * ldv + i];
+      ax = fma(cs[j].x, v.x, fma(-cs[j].y, v.y, ax));
+      ay = fma(cs[j].x, v.y, fma(cs[j].y, v.x, ay));
+    }
+    cd o = w[i];
+    w[i] = mkc(o.x + sign * ax, o.y + sign * ay);
+  }
+}
+
+__global__ void __launch_bounds__(RT) norm2_part(const cd *__restrict__ x, long long n,
+                                                 double *__restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += RT) {
+    cd a = x[i];
+    s = fma(a.x, a.x, fma(a.y, a.y, s));
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void norm2_final(const double *__restrict__ partial, int n_part, double *out) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < n_part; b += 32) s += partial[b];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+
+__global__ void scale_inv_kernel(cd *x, long long n, const double *nrm) {
+  double s = 1.0 / nrm[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cd a = x[i];
+    x[i] = mkc(a.x * s, a.y * s);
+  }
+}
+
+__global__ void copy_kernel(const cd *x, cd *y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
+__global__ void combine_kernel(const cd *__restrict__ V, long long ldv, int nv,
+                               const cd *__restrict__ u, const double *nrm, cd *__restrict__ y,
+                               long long n) {
+  __shared__ cd cs[128];
+  double s = nrm[0];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = cscale(u[j], s);
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double ax = 0.0, ay = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      cd v = V[j * ldv + i];
+      ax = fma(cs[j].x, v.x, fma(-cs[j].y, v.y, ax));
+      ay = fma(cs[j].x, v.y, fma(cs[j].y, v.x, ay));
+    }
+    y[i] = mkc(ax, ay);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// u = exp(-i T tau) e_1 for the symmetric tridiagonal Lanczos matrix T
+// (alpha on the diagonal, beta off it), kdim <= 64, one warp. T is shifted by
+// the midpoint mu of its diagonal; exp(-i (T - mu) tau) e_1 is built from s
+// substeps, each the degree-18 Taylor polynomial of A = -i (T - mu) tau / s
+// applied to the current vector, with s chosen so that ||A||_inf <= 1/2
+// (Taylor remainder < 2^-19 / 19! per substep). Row r of the vector lives in
+// lane r % 32, slot r / 32.
+__global__ void tridiag_expm_kernel(const double *__restrict__ alpha,
+                                    const double *__restrict__ beta, int kdim, double tau,
+                                    const double *bnext, cd *u, double *out_err) {
+  const int lane = threadIdx.x;
+  double a[2], bl[2], br[2];  // diagonal, coupling to row-1, coupling to row+1
+  double amin = 1e300, amax = -1e300;
+  for (int r = 0; r < kdim; ++r) {
+    amin = fmin(amin, alpha[r]);
+    amax = fmax(amax, alpha[r]);
+  }
+  const double mu = 0.5 * (amin + amax);
+  double nrm = 0.0;
+  for (int r = 0; r < kdim; ++r) {
+    double s = fabs(alpha[r] - mu);
+    if (r > 0) s += fabs(beta[r - 1]);
+    if (r + 1 < kdim) s += fabs(beta[r]);
+    nrm = fmax(nrm, s);
+  }
+  nrm *= fabs(tau);
+  int steps = (int)ceil(nrm / 0.5);
+  if (steps < 1) steps = 1;
+  const double h = tau / steps;
+  cd x[2];
+  for (int sl = 0; sl < 2; ++sl) {
+    int r = lane + 32 * sl;
+    bool ok = r < kdim;
+    a[sl] = ok ? (alpha[r] - mu) * h : 0.0;
+    bl[sl] = (ok && r > 0) ? beta[r - 1] * h : 0.0;
+    br[sl] = (ok && r + 1 < kdim) ? beta[r] * h : 0.0;
+    x[sl] = mkc(r == 0 ? 1.0 : 0.0, 0.0);
+  }
+  for (int st = 0; st < steps; ++st) {
+    cd term[2] = {x[0], x[1]};
+    cd acc[2] = {x[0], x[1]};
+    for (int n = 1; n <= 18; ++n) {
+      // neighbours of each row: row-1 and row+1
+      cd up0, up1, dn0, dn1;  // up = row-1, dn = row+1
+      double t0x = term[0].x, t0y = term[0].y, t1x = term[1].x, t1y = term[1].y;
+      double p0x = __shfl_up_sync(0xffffffffu, t0x, 1), p0y = __shfl_up_sync(0xffffffffu, t0y, 1);
+      double p1x = __shfl_up_sync(0xffffffffu, t1x, 1), p1y = __shfl_up_sync(0xffffffffu, t1y, 1);
+      double q0x = __shfl_down_sync(0xffffffffu, t0x, 1), q0y = __shfl_down_sync(0xffffffffu, t0y, 1);
+      double q1x = __shfl_down_sync(0xffffffffu, t1x, 1), q1y = __shfl_down_sync(0xffffffffu, t1y, 1);
+      double w31x = __shfl_sync(0xffffffffu, t0x, 31), w31y = __shfl_sync(0xffffffffu, t0y, 31);
+      double l0x = __shfl_sync(0xffffffffu, t1x, 0), l0y = __shfl_sync(0xffffffffu, t1y, 0);
+      up0 = lane > 0 ? mkc(p0x, p0y) : mkc(0.0, 0.0);
+      up1 = lane > 0 ? mkc(p1x, p1y) : mkc(w31x, w31y);
+      dn0 = lane < 31 ? mkc(q0x, q0y) : mkc(l0x, l0y);
+      dn1 = lane < 31 ? mkc(q1x, q1y) : mkc(0.0, 0.0);
+      cd nb[2][2] = {{up0, dn0}, {up1, dn1}};
+      for (int sl = 0; sl < 2; ++sl) {
+        // y = (T - mu) h * term ; new term = -i y / n
+        double yx = a[sl] * term[sl].x + bl[sl] * nb[sl][0].x + br[sl] * nb[sl][1].x;
+        double yy = a[sl] * term[sl].y + bl[sl] * nb[sl][0].y + br[sl] * nb[sl][1].y;
+        term[sl] = mkc(yy / n, -yx / n);
+        acc[sl] = cadd(acc[sl], term[sl]);
+      }
+    }
+    x[0] = acc[0];
+    x[1] = acc[1];
+  }
+  // phase exp(-i mu tau)
+  double sn, cs;
+  sincos(-mu * tau, &sn, &cs);
+  cd ph = mkc(cs, sn);
+  for (int sl = 0; sl < 2; ++sl) {
+    int r = lane + 32 * sl;
+    if (r < kdim) u[r] = cmul(ph, x[sl]);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    cd last = u[kdim - 1];
+    out_err[0] = bnext[0] * sqrt(cabs2(last));
+  }
+}
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+int reduce_parts(long long n) {
+  long long p = (n + 4095) / 4096;
+  if (p > 304) p = 304;
+  if (p < 1) p = 1;
+  return (int)p;
+}
+
+vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
+                        cd *partial, int n_part, cudaStream_t st) {
+  if (nv <= 0) return VB_OK;
+  multi_dot_part<<<n_part, RT, 0, st>>>(V, ldv, nv, w, n, partial);
+  VB_CHECK_LAUNCH();
+  reduce_parts_cd<<<(nv + 7) / 8, 256, 0, st>>>(partial, n_part, nv, out);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
+                         long long n, cudaStream_t st) {
+  if (nv <= 0 || n == 0) return VB_OK;
+  if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
+  multi_axpy_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, ldv, nv, c, sign, w, n);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
+                    cudaStream_t st) {
+  norm2_part<<<n_part, RT, 0, st>>>(x, n, partial);
+  VB_CHECK_LAUNCH();
+  norm2_final<<<1, 32, 0, st>>>(partial, n_part, out);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st) {
+  if (n == 0) return VB_OK;
+  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st) {
+  if (n == 0) return VB_OK;
+  copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, y, n);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_combine(const cd *V, long long ldv, int nv, const cd *u, const double *nrm, cd *y,
+                      long long n, cudaStream_t st) {
+  if (nv > 128) return fail(VB_EINVAL, "combine: more than 128 vectors");
+  combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, ldv, nv, u, nrm, y, n);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status tridiag_expm(const double *alpha, const double *beta, int kdim, double tau,
+                       const double *bnext, cd *u, double *out_err, cudaStream_t st) {
+  if (kdim < 1 || kdim > 64) return fail(VB_EINVAL, "tridiag_expm: kdim must be in 1..64");
+  tridiag_expm_kernel<<<1, 32, 0, st>>>(alpha, beta, kdim, tau, bnext, u, out_err);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+}  // namespace vb

@@ -1,0 +1,847 @@
+// Two-site TDVP time stepping (Sec. 2.1.2) on the GPU: host orchestration
+// of the kernels and the C ABI declared in include/vibtdvp.h.
+//
+// Data layout in device memory (all complex double, row-major):
+//   site tensor A[p]      [m_{p-1}][d_p][m_p]          capacity bcap_{p} d_p bcap_{p+1}
+//   left block  L[p]      [m_{p-1}][w_in(p)][m_{p-1}]  sites 0..p-1, first index bra
+//   right block R[p]      [m_{p-1}][w_in(p)][m_{p-1}]  sites p..n-1, first index bra
+//   two-site tensor       [m_{i-1}][d_i][d_{i+1}][m_{i+1}]
+//   Krylov basis          (krylov_cap + 1) vectors of the largest two-site size
+// bcap_b = min(m_cap, full dimension of bond b) bounds every bond.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+using namespace vb;
+
+namespace vb {
+constexpr double HBAR_EV_FS = 0.6582119569;
+constexpr double MULTIPLET_RTOL = 1e-10;
+
+// H_eff products in split-TF32 on the tensor cores (k_mixed.cu)
+vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
+                           const cd *R, const cd *x, cd *y, void *work, size_t work_bytes,
+                           cudaStream_t st);
+size_t heff_mixed_work_bytes(const vb_mpo *mpo, int site, int two_site, int mL, int mR);
+
+namespace {
+
+__global__ void trace_kernel(const cd *rho, int n, double *out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += rho[(long long)i * n + i].x;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    out[0] = t;
+  }
+}
+
+// dst[i*k + a] = src[a*n + i]
+__global__ void transpose_kernel(const cd *src, int k, int n, cd *dst) {
+  long long tot = (long long)k * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), a = (int)(e % k);
+    dst[e] = src[(long long)a * n + i];
+  }
+}
+
+__global__ void conj_copy_kernel(const cd *src, long long n, cd *dst) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = cconj(src[e]);
+}
+
+__global__ void set_alpha_kernel(const cd *c, const cd *c2, int k, double *alpha) {
+  alpha[k] = c[k].x + c2[k].x;
+}
+
+__global__ void populations_kernel(const cd *C, int d, int mR, double *out) {
+  // C[0][s][b]: P_s = sum_b |C[s,b]|^2 / sum |C|^2 ; one warp per s, then normalise
+  __shared__ double ps[64];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int s = w; s < d; s += nw) {
+    double a = 0.0;
+    for (int b = lane; b < mR; b += 32) a += cabs2(C[(long long)s * mR + b]);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) ps[s] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int s = 0; s < d; ++s) t += ps[s];
+    for (int s = 0; s < d; ++s) out[s] = ps[s] / t;
+  }
+}
+
+inline int grid1(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (int)std::max(1LL, b);
+}
+
+long long full_dim(const std::vector<int> &dims, int lo, int hi, long long cap) {
+  // product of dims[lo..hi) saturated at cap
+  long long p = 1;
+  for (int i = lo; i < hi; ++i) {
+    p *= dims[i];
+    if (p >= cap) return cap;
+  }
+  return p;
+}
+
+}  // namespace
+}  // namespace vb
+
+struct vb_mps {
+  int n = 0;
+  int dtype = VB_FP64;
+  int m_cap = 0;
+  int kcap = 40;
+  int device = -1;
+  cudaStream_t st = nullptr;
+  vb::Alloc alloc;
+  const vb_mpo *mpo = nullptr;
+  std::vector<int> dims;
+  std::vector<int> bond;   // bond[p] = left bond of site p; bond[0] = bond[n] = 1
+  std::vector<int> bcap;   // capacity per bond
+  std::vector<cd *> A, L, R;
+  cd *theta = nullptr, *V = nullptr, *T1 = nullptr, *T2 = nullptr, *rho = nullptr, *Z = nullptr;
+  void *eigw = nullptr;
+  void *mixw = nullptr;
+  size_t mixw_bytes = 0;
+  long long theta_cap = 0, inter_cap = 0, nrho_cap = 0;
+  int kw_cap = 0;
+  // device scalars
+  double *d_nrm = nullptr, *d_alpha = nullptr, *d_beta = nullptr, *d_bnext = nullptr,
+         *d_evals = nullptr, *d_trace = nullptr, *d_part = nullptr, *d_pop = nullptr;
+  cd *d_c = nullptr, *d_c2 = nullptr, *d_u = nullptr, *d_partc = nullptr;
+  double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
+  std::vector<void *> owned;
+  int center = 0;
+};
+
+namespace vb {
+namespace {
+
+vb_status mps_alloc(vb_mps *s, void **p, size_t bytes) {
+  VB_TRY(s->alloc.get(p, bytes));
+  s->owned.push_back(*p);
+  return VB_OK;
+}
+
+struct Ctx {
+  vb_mps *s;
+  const vb_mpo *mpo;
+  cudaStream_t st;
+};
+
+// ---- H_eff,2 theta (Eq. two-site Hamiltonian), FP64 path
+// T1 and T2 each hold at least max(w_in(i), w_out(i), w_out(i+1)) * |theta| elements.
+vb_status heff2_fp64(const vb_mpo *mpo, int i, int mL, int mR, const cd *L, const cd *R,
+                     const cd *x, cd *y, cd *T1, cd *T2, long long t_cap, cudaStream_t st) {
+  const MpoSite &Si = mpo->sites[i], &Sj = mpo->sites[i + 1];
+  const long long d1 = Si.d, d2 = Sj.d, wL = Si.wl, wM = Si.wr, wR = Sj.wr;
+  const long long th = mL * d1 * d2 * mR, Q1 = d2 * mR;
+  // T1[(a' w0), (s t b)] = L[(a' w0), a] x[a, (s t b)]
+  GemmArgs g{};
+  g.M = (int)(mL * wL); g.N = (int)(d1 * Q1); g.K = mL; g.batch = 1;
+  g.opA = OP_N; g.opB = OP_N;
+  g.A = L; g.lda = mL; g.B = x; g.ldb = g.N; g.C = T1; g.ldc = g.N;
+  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.a_size = mL * wL * mL; g.b_size = th; g.c_size = t_cap;
+  VB_TRY(zgemm(g, st));
+  // T2[a'][s'][w1][(t b)] = W_i applied to T1[a'][w0][s][(t b)]
+  VB_TRY(wapply(Si, 0, T1, WS(/*p*/ wL * d1 * Q1, /*w*/ d1 * Q1, /*s*/ Q1, /*q*/ 1), t_cap, T2,
+                WS(/*p*/ d1 * wM * Q1, /*w*/ Q1, /*s*/ wM * Q1, /*q*/ 1), t_cap, mL, (int)Q1, st));
+  // T3[(a' s')][t'][w2][b] = W_{i+1} applied to T2[(a' s')][w1][t][b]   (T3 reuses T1)
+  VB_TRY(wapply(Sj, 0, T2, WS(/*p*/ wM * d2 * mR, /*w*/ d2 * mR, /*s*/ mR, /*q*/ 1), t_cap, T1,
+                WS(/*p*/ d2 * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, (int)(mL * d1), mR, st));
+  // y[(a' s' t'), b'] = T3[(a' s' t'), (w2 b)] R[b', (w2 b)]^T
+  GemmArgs h{};
+  h.M = (int)(mL * d1 * d2); h.N = mR; h.K = (int)(wR * mR); h.batch = 1;
+  h.opA = OP_N; h.opB = OP_T;
+  h.A = T1; h.lda = h.K; h.B = R; h.ldb = h.K; h.C = y; h.ldc = mR;
+  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.a_size = t_cap; h.b_size = (long long)mR * wR * mR; h.c_size = th;
+  return zgemm(h, st);
+}
+
+// ---- H_eff,1 C (Eq. one-site Hamiltonian 1), FP64 path
+vb_status heff1_fp64(const vb_mpo *mpo, int j, int mL, int mR, const cd *L, const cd *R,
+                     const cd *x, cd *y, cd *T1, cd *T2, long long t_cap, cudaStream_t st) {
+  const MpoSite &S = mpo->sites[j];
+  const long long d = S.d, wL = S.wl, wR = S.wr;
+  GemmArgs g{};
+  g.M = (int)(mL * wL); g.N = (int)(d * mR); g.K = mL; g.batch = 1;
+  g.opA = OP_N; g.opB = OP_N;
+  g.A = L; g.lda = mL; g.B = x; g.ldb = g.N; g.C = T1; g.ldc = g.N;
+  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.a_size = mL * wL * mL; g.b_size = mL * d * mR; g.c_size = t_cap;
+  VB_TRY(zgemm(g, st));
+  // T2[a'][t'][w1][b] = W applied to T1[a'][w0][t][b]
+  VB_TRY(wapply(S, 0, T1, WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), t_cap, T2,
+                WS(/*p*/ d * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, mL, mR, st));
+  GemmArgs h{};
+  h.M = (int)(mL * d); h.N = mR; h.K = (int)(wR * mR); h.batch = 1;
+  h.opA = OP_N; h.opB = OP_T;
+  h.A = T2; h.lda = h.K; h.B = R; h.ldb = h.K; h.C = y; h.ldc = mR;
+  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.a_size = t_cap; h.b_size = (long long)mR * wR * mR; h.c_size = mL * d * mR;
+  return zgemm(h, st);
+}
+
+// ---- environment updates (the blocks of Eq. one-site Hamiltonian 1)
+vb_status env_left(const vb_mpo *mpo, int p, int mL, int mR, const cd *L, const cd *A, cd *Lnew,
+                   cd *T1, cd *T2, long long t_cap, cudaStream_t st) {
+  const MpoSite &S = mpo->sites[p];
+  const long long d = S.d, wL = S.wl, wR = S.wr;
+  // T1[(x w), (s y)] = L[(x w), z] A[z, (s y)]
+  GemmArgs g{};
+  g.M = (int)(mL * wL); g.N = (int)(d * mR); g.K = mL; g.batch = 1;
+  g.opA = OP_N; g.opB = OP_N;
+  g.A = L; g.lda = mL; g.B = A; g.ldb = g.N; g.C = T1; g.ldc = g.N;
+  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.a_size = mL * wL * mL; g.b_size = mL * d * mR; g.c_size = t_cap;
+  VB_TRY(zgemm(g, st));
+  // T2[x][s'][v][y] = W applied to T1[x][w][s][y]
+  VB_TRY(wapply(S, 0, T1, WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), t_cap, T2,
+                WS(/*p*/ d * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, mL, mR, st));
+  // Lnew[y', (v y)] = sum_{(x s')} conj(A[(x s'), y']) T2[(x s'), (v y)]
+  GemmArgs h{};
+  h.M = mR; h.N = (int)(wR * mR); h.K = (int)(mL * d); h.batch = 1;
+  h.opA = OP_C; h.opB = OP_N;
+  h.A = A; h.lda = mR; h.B = T2; h.ldb = h.N; h.C = Lnew; h.ldc = h.N;
+  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.a_size = mL * d * mR; h.b_size = t_cap; h.c_size = (long long)mR * wR * mR;
+  return zgemm(h, st);
+}
+
+vb_status env_right(const vb_mpo *mpo, int p, int mL, int mR, const cd *R, const cd *B, cd *Rnew,
+                    cd *T1, cd *T2, long long t_cap, cudaStream_t st) {
+  const MpoSite &S = mpo->sites[p];
+  const long long d = S.d, wL = S.wl, wR = S.wr;
+  // T1[(a t)][v][y] = sum_z B[(a t), z] R[y, v, z]   (batched over v)
+  GemmArgs g{};
+  g.M = (int)(mL * d); g.N = mR; g.K = mR; g.batch = (int)wR;
+  g.opA = OP_N; g.opB = OP_T;
+  g.A = B; g.lda = mR; g.sA = 0;
+  g.B = R; g.ldb = wR * mR; g.sB = mR;
+  g.C = T1; g.ldc = wR * mR; g.sC = mR;
+  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.a_size = mL * d * mR; g.b_size = (long long)mR * wR * mR; g.c_size = t_cap;
+  VB_TRY(zgemm(g, st));
+  // T2[a][w][t'][y] = sum_{t, v} W[w, t', t, v] T1[a][t][v][y]
+  VB_TRY(wapply(S, 1, T1, WS(/*p*/ d * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, T2,
+                WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), t_cap, mL, mR, st));
+  // Rnew[a', w, a] = sum_k conj(B[a', k]) T2[a, w, k]   (batched over w)
+  GemmArgs h{};
+  h.M = mL; h.N = mL; h.K = (int)(d * mR); h.batch = (int)wL;
+  h.opA = OP_R; h.opB = OP_T;
+  h.A = B; h.lda = d * mR; h.sA = 0;
+  h.B = T2; h.ldb = wL * d * mR; h.sB = d * mR;
+  h.C = Rnew; h.ldc = wL * mL; h.sC = mL;
+  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.a_size = mL * d * mR; h.b_size = t_cap; h.c_size = (long long)mL * wL * mL;
+  return zgemm(h, st);
+}
+
+// ---- operator applied inside the Krylov loop
+struct HeffOp {
+  int two_site;
+  int site;
+  int mL, mR;
+  const cd *L, *R;
+};
+
+vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
+  if (s->dtype == VB_MIXED)
+    return heff_mixed_apply(s->mpo, op.site, op.two_site, op.mL, op.mR, op.L, op.R, x, y, s->mixw,
+                            s->mixw_bytes, s->st);
+  if (op.two_site)
+    return heff2_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
+  return heff1_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
+}
+
+// ---- x <- exp(-i H dt/hbar) x by Lanczos with full re-orthogonalisation
+vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt_fs, int kmax,
+                      double tol, int *iters, int *converged) {
+  cudaStream_t st = s->st;
+  const int np = reduce_parts(N);
+  const long long ldv = s->theta_cap;
+  cd *V = s->V;
+  kmax = (int)std::min<long long>(std::min(kmax, s->kcap), N);
+  const double tau = dt_fs / HBAR_EV_FS;
+  VB_TRY(vec_norm2(x, N, s->d_nrm, s->d_part, np, st));
+  VB_TRY(vec_copy_scaled(x, V, N, st));
+  VB_TRY(vec_scale_inv(V, N, s->d_nrm, st));
+  int kdim = 0;
+  *converged = 0;
+  for (int k = 0; k < kmax; ++k) {
+    cd *w = V + (k + 1) * ldv;
+    VB_TRY(apply_heff(s, op, V + k * ldv, w));
+    VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st));
+    VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
+    VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st));
+    VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c2, -1.0, w, N, st));
+    set_alpha_kernel<<<1, 1, 0, st>>>(s->d_c, s->d_c2, k, s->d_alpha);
+    VB_CHECK_LAUNCH();
+    VB_TRY(vec_norm2(w, N, s->d_bnext, s->d_part, np, st));
+    VB_TRY(tridiag_expm(s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
+    VB_TRY_CUDA(cudaMemcpyAsync(s->d_flag + 1, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    const double err = s->h_flag[0], b = s->h_flag[1];
+    kdim = k + 1;
+    if (!(err == err) || !(b == b)) return fail(VB_ECUDA, "krylov: NaN in the Lanczos recurrence");
+    if (err < tol || b <= 1e-300 || k + 1 == N) {
+      *converged = 1;
+      break;
+    }
+    VB_TRY_CUDA(cudaMemcpyAsync(s->d_beta + k, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st));
+  }
+  *iters = kdim;
+  VB_TRY(vec_combine(V, ldv, kdim, s->d_u, s->d_nrm, x, N, st));
+  return VB_OK;
+}
+
+struct TruncOpts {
+  int m_max;
+  double eps, floor;
+};
+
+// number of kept Schmidt directions (DBSS / fixed M, Sec. 2.1.1) from the
+// kw largest eigenvalues lam (descending) of an n x n reduced density matrix
+// with trace tot; rank_bound bounds the Schmidt rank. Sets *disc to the
+// relative discarded weight.
+int choose_rank(const std::vector<double> &lam, int n, double tot, int rank_bound,
+                const TruncOpts &o, double *disc) {
+  const int kw = (int)lam.size();
+  int k = std::min(n, rank_bound);
+  if (o.floor > 0.0) {
+    int c = 0;
+    while (c < kw && lam[c] > o.floor * tot) ++c;
+    if (c < kw || kw == n) k = std::min(k, c);
+  }
+  std::vector<double> prefix(kw + 1, 0.0);
+  for (int j = 0; j < kw; ++j) prefix[j + 1] = prefix[j] + lam[j];
+  if (o.eps > 0.0) {
+    int kk = n;
+    for (int j = 0; j <= kw; ++j)
+      if (tot - prefix[j] <= o.eps * tot) {
+        kk = j;
+        break;
+      }
+    k = std::min(k, kk);
+  }
+  k = std::min(k, o.m_max);
+  k = std::max(k, 1);
+  while (k > 1 && k < n && k < kw && (lam[k - 1] - lam[k]) < MULTIPLET_RTOL * lam[k - 1]) --k;
+  *disc = tot > 0.0 ? (tot - prefix[std::min(k, kw)]) / tot : 0.0;
+  if (*disc < 0.0) *disc = 0.0;
+  return k;
+}
+
+// theta (mL d1 x d2 mR) -> left-orthonormal A_i (into dstA) and C (into dstC),
+// or (right) C (dstA) and right-orthonormal B (dstC). Returns the new bond.
+vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o,
+                cd *dstA, cd *dstC, int *k_out, double *disc) {
+  cudaStream_t st = s->st;
+  const int n1 = mL * d1, n2 = d2 * mR;
+  const int n = left ? n1 : n2;
+  const cd *M = s->theta;
+  GemmArgs g{};
+  g.M = n; g.N = n; g.batch = 1;
+  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  if (left) {  // rho = M M^+
+    g.K = n2; g.opA = OP_N; g.opB = OP_C;
+    g.A = M; g.lda = n2; g.B = M; g.ldb = n2;
+  } else {  // rho = M^+ M
+    g.K = n1; g.opA = OP_C; g.opB = OP_N;
+    g.A = M; g.lda = n2; g.B = M; g.ldb = n2;
+  }
+  g.C = s->rho; g.ldc = n;
+  g.a_size = (long long)n1 * n2; g.b_size = (long long)n1 * n2; g.c_size = s->nrho_cap * s->nrho_cap;
+  VB_TRY(zgemm(g, st));
+  trace_kernel<<<1, 256, 0, st>>>(s->rho, n, s->d_trace);
+  VB_CHECK_LAUNCH();
+  const int kw = std::min(n, o.m_max + 1);
+  VB_TRY(eig_values(n, s->rho, kw, s->d_evals, s->eigw, st));
+  std::vector<double> lam(kw);
+  double tot = 0.0;
+  VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), s->d_evals, kw * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaMemcpyAsync(&tot, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  const int k = choose_rank(lam, n, tot, std::min(n1, n2), o, disc);
+  VB_TRY(eig_vectors(n, s->rho, kw, k, s->d_evals, s->Z, s->eigw, st));
+  if (left) {
+    transpose_kernel<<<grid1((long long)k * n1), 256, 0, st>>>(s->Z, k, n1, dstA);
+    VB_CHECK_LAUNCH();
+    GemmArgs h{};
+    h.M = k; h.N = n2; h.K = n1; h.batch = 1;
+    h.opA = OP_R; h.opB = OP_N;
+    h.A = s->Z; h.lda = n1; h.B = M; h.ldb = n2; h.C = dstC; h.ldc = n2;
+    h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+    h.a_size = (long long)k * n1; h.b_size = (long long)n1 * n2; h.c_size = (long long)k * n2;
+    VB_TRY(zgemm(h, st));
+    const long long nc = (long long)k * n2;
+    VB_TRY(vec_norm2(dstC, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
+    VB_TRY(vec_scale_inv(dstC, nc, s->d_nrm, st));
+  } else {
+    conj_copy_kernel<<<grid1((long long)k * n2), 256, 0, st>>>(s->Z, (long long)k * n2, dstC);
+    VB_CHECK_LAUNCH();
+    GemmArgs h{};
+    h.M = n1; h.N = k; h.K = n2; h.batch = 1;
+    h.opA = OP_N; h.opB = OP_T;
+    h.A = M; h.lda = n2; h.B = s->Z; h.ldb = n2; h.C = dstA; h.ldc = k;
+    h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+    h.a_size = (long long)n1 * n2; h.b_size = (long long)k * n2; h.c_size = (long long)n1 * k;
+    VB_TRY(zgemm(h, st));
+    const long long nc = (long long)n1 * k;
+    VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
+    VB_TRY(vec_scale_inv(dstA, nc, s->d_nrm, st));
+  }
+  *k_out = k;
+  return VB_OK;
+}
+
+vb_status merge(vb_mps *s, int i) {
+  const int mL = s->bond[i], mM = s->bond[i + 1], mR = s->bond[i + 2];
+  const int d1 = s->dims[i], d2 = s->dims[i + 1];
+  GemmArgs g{};
+  g.M = mL * d1; g.N = d2 * mR; g.K = mM; g.batch = 1;
+  g.opA = OP_N; g.opB = OP_N;
+  g.A = s->A[i]; g.lda = mM; g.B = s->A[i + 1]; g.ldb = g.N; g.C = s->theta; g.ldc = g.N;
+  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.a_size = (long long)mL * d1 * mM; g.b_size = (long long)mM * d2 * mR; g.c_size = s->theta_cap;
+  return zgemm(g, s->st);
+}
+
+vb_status set_device_of(vb_mps *s) {
+  int dev = -1;
+  VB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev != s->device) VB_TRY_CUDA(cudaSetDevice(s->device));
+  return VB_OK;
+}
+
+// allocate all buffers of a new MPS handle
+vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
+  if (!mpo || !opts || !out) return fail(VB_EINVAL, "mps: null argument");
+  if (opts->m_cap < 1) return fail(VB_EINVAL, "mps: m_cap must be >= 1");
+  if (opts->dtype != VB_FP64 && opts->dtype != VB_MIXED) return fail(VB_EINVAL, "mps: bad dtype");
+  int kcap = opts->krylov_cap > 0 ? opts->krylov_cap : 40;
+  if (kcap > 64) return fail(VB_EINVAL, "mps: krylov_cap must be <= 64");
+  VB_TRY(mpo_upload(mpo));
+  vb_mps *s = new vb_mps();
+  s->n = mpo->n;
+  s->dtype = opts->dtype;
+  s->m_cap = opts->m_cap;
+  s->kcap = kcap;
+  s->st = (cudaStream_t)opts->cuda_stream;
+  s->alloc.user = opts->alloc;
+  s->alloc.stream = s->st;
+  s->mpo = mpo;
+  s->dims = mpo->dims;
+  cudaGetDevice(&s->device);
+  const int n = s->n;
+  s->bond.assign(n + 1, 1);
+  s->bcap.assign(n + 1, 1);
+  for (int b = 1; b < n; ++b) {
+    long long l = full_dim(s->dims, 0, b, opts->m_cap), r = full_dim(s->dims, b, n, opts->m_cap);
+    s->bcap[b] = (int)std::min<long long>(std::min(l, r), opts->m_cap);
+  }
+  auto fail_free = [&](vb_status st) {
+    for (void *p : s->owned) s->alloc.put(p);
+    delete s;
+    return st;
+  };
+  s->A.assign(n, nullptr);
+  s->L.assign(n + 1, nullptr);
+  s->R.assign(n + 1, nullptr);
+  long long inter = 0;
+  for (int p = 0; p < n; ++p) {
+    const MpoSite &S = mpo->sites[p];
+    size_t sa = (size_t)s->bcap[p] * S.d * s->bcap[p + 1];
+    vb_status e = mps_alloc(s, (void **)&s->A[p], sa * sizeof(cd));
+    if (e != VB_OK) return fail_free(e);
+    size_t se = (size_t)s->bcap[p] * S.wl * s->bcap[p];
+    e = mps_alloc(s, (void **)&s->L[p], se * sizeof(cd));
+    if (e != VB_OK) return fail_free(e);
+    e = mps_alloc(s, (void **)&s->R[p], se * sizeof(cd));
+    if (e != VB_OK) return fail_free(e);
+    // one-site intermediates
+    long long one = (long long)s->bcap[p] * S.d * s->bcap[p + 1] * std::max(S.wl, S.wr);
+    inter = std::max(inter, one);
+    s->nrho_cap = std::max<long long>(s->nrho_cap, (long long)s->bcap[p] * S.d);
+    s->nrho_cap = std::max<long long>(s->nrho_cap, (long long)S.d * s->bcap[p + 1]);
+    if (p + 1 < n) {
+      const MpoSite &S2 = mpo->sites[p + 1];
+      long long th = (long long)s->bcap[p] * S.d * S2.d * s->bcap[p + 2];
+      s->theta_cap = std::max(s->theta_cap, th);
+      int wmax = std::max(S.wl, std::max(S.wr, S2.wr));
+      inter = std::max(inter, th * wmax);
+    }
+  }
+  if (n == 1) s->theta_cap = std::max<long long>(s->theta_cap, s->dims[0]);
+  s->theta_cap = std::max<long long>(s->theta_cap, 1);
+  for (int p = 0; p < n; ++p)
+    s->theta_cap = std::max<long long>(s->theta_cap, (long long)s->bcap[p] * s->dims[p] * s->bcap[p + 1]);
+  s->theta_cap = (s->theta_cap + 31) / 32 * 32;
+  s->inter_cap = std::max<long long>(inter, 1);
+  {
+    vb_status e = VB_OK;
+    auto A2 = [&](void **p, size_t b) {
+      if (e == VB_OK) e = mps_alloc(s, p, b);
+    };
+    A2((void **)&s->L[n], sizeof(cd));
+    A2((void **)&s->R[n], sizeof(cd));
+    A2((void **)&s->theta, s->theta_cap * sizeof(cd));
+    A2((void **)&s->V, (size_t)(kcap + 1) * s->theta_cap * sizeof(cd));
+    A2((void **)&s->T1, s->inter_cap * sizeof(cd));
+    A2((void **)&s->T2, s->inter_cap * sizeof(cd));
+    const int nr = (int)s->nrho_cap;
+    s->kw_cap = std::min(nr, opts->m_cap + 1);
+    A2((void **)&s->rho, (size_t)nr * nr * sizeof(cd));
+    A2((void **)&s->Z, (size_t)(s->kw_cap) * nr * sizeof(cd));
+    A2(&s->eigw, EigWork::bytes(nr, s->kw_cap));
+    A2((void **)&s->d_nrm, 256);
+    A2((void **)&s->d_alpha, 128 * sizeof(double));
+    A2((void **)&s->d_beta, 128 * sizeof(double));
+    A2((void **)&s->d_bnext, 256);
+    A2((void **)&s->d_evals, (size_t)(s->kw_cap + 1) * sizeof(double));
+    A2((void **)&s->d_trace, 256);
+    A2((void **)&s->d_part, 512 * sizeof(double));
+    A2((void **)&s->d_pop, 64 * sizeof(double));
+    A2((void **)&s->d_c, 128 * sizeof(cd));
+    A2((void **)&s->d_c2, 128 * sizeof(cd));
+    A2((void **)&s->d_u, 128 * sizeof(cd));
+    A2((void **)&s->d_partc, (size_t)512 * 128 * sizeof(cd));
+    if (e != VB_OK) return fail_free(e);
+    if (s->dtype == VB_MIXED) {
+      size_t mb = 0;
+      for (int p = 0; p < n; ++p) {
+        mb = std::max(mb, heff_mixed_work_bytes(mpo, p, 0, s->bcap[p], s->bcap[p + 1]));
+        if (p + 1 < n) mb = std::max(mb, heff_mixed_work_bytes(mpo, p, 1, s->bcap[p], s->bcap[p + 2]));
+      }
+      s->mixw_bytes = mb;
+      A2(&s->mixw, mb);
+      if (e != VB_OK) return fail_free(e);
+    }
+  }
+  if (cudaHostAlloc((void **)&s->h_flag, 4 * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&s->d_flag, s->h_flag, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return fail_free(fail(VB_ECUDA, "mps: cudaHostAlloc (mapped) failed"));
+  }
+  // boundary environments = 1
+  cd one = mkc(1.0, 0.0);
+  if (cudaMemcpyAsync(s->L[0], &one, sizeof(cd), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemcpyAsync(s->R[n], &one, sizeof(cd), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaStreamSynchronize(s->st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(s->h_flag);
+    return fail_free(fail(VB_ECUDA, "mps: boundary upload failed"));
+  }
+  *out = s;
+  return VB_OK;
+}
+
+// build R[p] for p = n-1 .. 1 from the right-canonical tensors
+vb_status build_right_envs(vb_mps *s) {
+  for (int p = s->n - 1; p >= 1; --p)
+    VB_TRY(env_right(s->mpo, p, s->bond[p], s->bond[p + 1], s->R[p + 1], s->A[p], s->R[p], s->T1,
+                     s->T2, s->inter_cap, s->st));
+  return VB_OK;
+}
+
+}  // namespace
+}  // namespace vb
+
+extern "C" {
+
+vb_status mps_create(const vb_mpo *mpo, const int *init_index, const vb_mps_opts *opts,
+                     vb_mps **out) {
+  if (!mpo || !init_index || !opts || !out) return fail(VB_EINVAL, "mps_create: null argument");
+  *out = nullptr;
+  for (int p = 0; p < mpo->n; ++p)
+    if (init_index[p] < 0 || init_index[p] >= mpo->dims[p])
+      return fail(VB_EINVAL, "mps_create: init_index out of range at site " + std::to_string(p));
+  vb_mps *s = nullptr;
+  VB_TRY(mps_setup(mpo, opts, &s));
+  const int n = s->n;
+  // bond dimensions: 1, or the padded full dimensions (bounded by m_cap)
+  for (int b = 1; b < n; ++b) s->bond[b] = opts->pad_full ? s->bcap[b] : 1;
+  // right-orthonormal padded product state: first row carries the product
+  // state, the remaining rows are distinct unit vectors
+  for (int p = 0; p < n; ++p) {
+    const int dl = s->bond[p], d = s->dims[p], dr = s->bond[p + 1];
+    std::vector<cd> h((size_t)dl * d * dr, mkc(0, 0));
+    if (p == 0) {
+      h[(size_t)init_index[0] * dr] = mkc(1, 0);
+    } else {
+      const int cols = d * dr, first = init_index[p] * dr;
+      h[first] = mkc(1, 0);
+      int c = 0;
+      for (int r = 1; r < dl; ++r) {
+        if (c == first) ++c;
+        h[(size_t)r * cols + c] = mkc(1, 0);
+        ++c;
+      }
+    }
+    if (cudaMemcpyAsync(s->A[p], h.data(), h.size() * sizeof(cd), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+        cudaStreamSynchronize(s->st) != cudaSuccess) {
+      mps_destroy(s);
+      return fail(VB_ECUDA, "mps_create: upload failed");
+    }
+  }
+  vb_status e = build_right_envs(s);
+  if (e == VB_OK && cudaStreamSynchronize(s->st) != cudaSuccess) e = fail(VB_ECUDA, "mps_create: env build failed");
+  if (e != VB_OK) {
+    mps_destroy(s);
+    return e;
+  }
+  *out = s;
+  return VB_OK;
+}
+
+vb_status mps_create_from_tensors(const vb_mpo *mpo, const int *bond_dims,
+                                  const double *const *host_tensors, const vb_mps_opts *opts,
+                                  vb_mps **out) {
+  if (!mpo || !host_tensors || !opts || !out || (mpo->n > 1 && !bond_dims))
+    return fail(VB_EINVAL, "mps_create_from_tensors: null argument");
+  *out = nullptr;
+  vb_mps *s = nullptr;
+  VB_TRY(mps_setup(mpo, opts, &s));
+  const int n = s->n;
+  for (int b = 1; b < n; ++b) {
+    if (bond_dims[b - 1] < 1 || bond_dims[b - 1] > s->bcap[b]) {
+      mps_destroy(s);
+      return fail(VB_EINVAL, "mps_create_from_tensors: bond " + std::to_string(b - 1) +
+                                 " outside 1..min(m_cap, full dimension)");
+    }
+    s->bond[b] = bond_dims[b - 1];
+  }
+  for (int p = 0; p < n; ++p) {
+    size_t el = (size_t)s->bond[p] * s->dims[p] * s->bond[p + 1];
+    if (!host_tensors[p] ||
+        cudaMemcpyAsync(s->A[p], host_tensors[p], el * sizeof(cd), cudaMemcpyHostToDevice, s->st) != cudaSuccess) {
+      mps_destroy(s);
+      return fail(VB_EINVAL, "mps_create_from_tensors: upload of site " + std::to_string(p) + " failed");
+    }
+  }
+  vb_status e = build_right_envs(s);
+  if (e == VB_OK && cudaStreamSynchronize(s->st) != cudaSuccess) e = fail(VB_ECUDA, "env build failed");
+  if (e != VB_OK) {
+    mps_destroy(s);
+    return e;
+  }
+  *out = s;
+  return VB_OK;
+}
+
+vb_status mps_destroy(vb_mps *s) {
+  if (!s) return VB_OK;
+  cudaStreamSynchronize(s->st);
+  for (void *p : s->owned) s->alloc.put(p);
+  if (s->h_flag) cudaFreeHost(s->h_flag);
+  delete s;
+  return VB_OK;
+}
+
+int mps_n_sites(const vb_mps *s) { return s ? s->n : -1; }
+
+vb_status mps_bond_dims(const vb_mps *s, int *host_out) {
+  if (!s || !host_out) return fail(VB_EINVAL, "mps_bond_dims: null argument");
+  for (int b = 1; b < s->n; ++b) host_out[b - 1] = s->bond[b];
+  return VB_OK;
+}
+
+vb_status mps_get_site(const vb_mps *s, int site, double *host_out) {
+  if (!s || !host_out || site < 0 || site >= s->n) return fail(VB_EINVAL, "mps_get_site: bad argument");
+  size_t el = (size_t)s->bond[site] * s->dims[site] * s->bond[site + 1];
+  VB_TRY_CUDA(cudaMemcpyAsync(host_out, s->A[site], el * sizeof(cd), cudaMemcpyDeviceToHost, s->st));
+  VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  return VB_OK;
+}
+
+vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *o,
+                      vb_sweep_stats *stats) {
+  if (!s || !mpo || !o) return fail(VB_EINVAL, "tdvp2_sweep: null argument");
+  if (mpo != s->mpo) return fail(VB_EINVAL, "tdvp2_sweep: MPS was created for another MPO");
+  if (s->center != 0) return fail(VB_ESTATE, "tdvp2_sweep: center is not on site 0");
+  if (o->m_max < 1 || o->m_max > s->m_cap) return fail(VB_EINVAL, "tdvp2_sweep: m_max outside 1..m_cap");
+  if (o->krylov_max < 1 || o->krylov_max > s->kcap)
+    return fail(VB_EINVAL, "tdvp2_sweep: krylov_max outside 1..krylov_cap");
+  if (o->eps < 0 || o->zero_floor < 0 || !(o->krylov_tol > 0))
+    return fail(VB_EINVAL, "tdvp2_sweep: eps, zero_floor must be >= 0 and krylov_tol > 0");
+  if (s->n < 2) return fail(VB_EINVAL, "tdvp2_sweep: needs at least two sites");
+  VB_TRY(set_device_of(s));
+  const int n = s->n;
+  const double tau = 0.5 * dt_fs;
+  TruncOpts to{o->m_max, o->eps, o->zero_floor};
+  vb_sweep_stats st{};
+  auto evolve = [&](const HeffOp &op, cd *x, long long N, double dt) -> vb_status {
+    int it = 0, conv = 0;
+    VB_TRY(krylov_expm(s, op, x, N, dt, o->krylov_max, o->krylov_tol, &it, &conv));
+    st.krylov_iters_max = std::max(st.krylov_iters_max, it);
+    st.krylov_iters_total += it;
+    if (!conv) {
+      st.noconv++;
+      if (o->on_noconv) return fail(VB_ENOCONV, "Krylov exponential did not converge");
+    }
+    return VB_OK;
+  };
+  // left to right, tau = dt/2
+  for (int i = 0; i + 1 < n; ++i) {
+    const int mL = s->bond[i], mR = s->bond[i + 2], d1 = s->dims[i], d2 = s->dims[i + 1];
+    VB_TRY(merge(s, i));
+    HeffOp op{1, i, mL, mR, s->L[i], s->R[i + 2]};
+    VB_TRY(evolve(op, s->theta, (long long)mL * d1 * d2 * mR, tau));
+    int k = 0;
+    double disc = 0.0;
+    VB_TRY(split(s, true, mL, d1, d2, mR, to, s->A[i], s->A[i + 1], &k, &disc));
+    st.discarded_weight += disc;
+    s->bond[i + 1] = k;
+    VB_TRY(env_left(mpo, i, mL, k, s->L[i], s->A[i], s->L[i + 1], s->T1, s->T2, s->inter_cap, s->st));
+    if (i + 2 < n) {
+      HeffOp op1{0, i + 1, k, mR, s->L[i + 1], s->R[i + 2]};
+      VB_TRY(evolve(op1, s->A[i + 1], (long long)k * d2 * mR, -tau));
+    }
+  }
+  // right to left, tau = dt/2
+  for (int i = n - 2; i >= 0; --i) {
+    const int mL = s->bond[i], mR = s->bond[i + 2], d1 = s->dims[i], d2 = s->dims[i + 1];
+    VB_TRY(merge(s, i));
+    HeffOp op{1, i, mL, mR, s->L[i], s->R[i + 2]};
+    VB_TRY(evolve(op, s->theta, (long long)mL * d1 * d2 * mR, tau));
+    int k = 0;
+    double disc = 0.0;
+    VB_TRY(split(s, false, mL, d1, d2, mR, to, s->A[i], s->A[i + 1], &k, &disc));
+    st.discarded_weight += disc;
+    s->bond[i + 1] = k;
+    VB_TRY(env_right(mpo, i + 1, k, mR, s->R[i + 2], s->A[i + 1], s->R[i + 1], s->T1, s->T2, s->inter_cap,
+                     s->st));
+    if (i > 0) {
+      HeffOp op1{0, i, mL, k, s->L[i], s->R[i + 1]};
+      VB_TRY(evolve(op1, s->A[i], (long long)mL * d1 * k, -tau));
+    }
+  }
+  VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  for (int b = 1; b < n; ++b) st.max_bond = std::max(st.max_bond, s->bond[b]);
+  if (stats) *stats = st;
+  return VB_OK;
+}
+
+vb_status measure_populations(const vb_mps *s, double *pop_host) {
+  if (!s || !pop_host) return fail(VB_EINVAL, "measure_populations: null argument");
+  if (s->mpo->el_pos != 0) return fail(VB_EINVAL, "measure_populations: electronic site must be first");
+  if (s->center != 0) return fail(VB_ESTATE, "measure_populations: center is not on site 0");
+  const int d = s->dims[0];
+  if (d > 64) return fail(VB_EINVAL, "measure_populations: more than 64 electronic states");
+  populations_kernel<<<1, 256, 0, s->st>>>(s->A[0], d, s->bond[1], s->d_pop);
+  VB_CHECK_LAUNCH();
+  VB_TRY_CUDA(cudaMemcpyAsync(pop_host, s->d_pop, d * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  return VB_OK;
+}
+
+// ---- single operations on caller buffers
+size_t vb_heff_work_elems(const vb_mpo *mpo, int site, int mL, int mR, int two_site) {
+  if (!mpo || site < 0 || site >= mpo->n || (two_site && site + 1 >= mpo->n)) return 0;
+  const MpoSite &S = mpo->sites[site];
+  if (two_site) {
+    const MpoSite &S2 = mpo->sites[site + 1];
+    size_t th = (size_t)mL * S.d * S2.d * mR;
+    size_t w = std::max(S.wl, std::max(S.wr, S2.wr));
+    size_t mixed = (heff_mixed_work_bytes(mpo, site, 1, mL, mR) + sizeof(cd) - 1) / sizeof(cd);
+    return std::max(2 * th * w, mixed);
+  }
+  size_t one = (size_t)mL * S.d * mR * std::max(S.wl, S.wr);
+  size_t mixed = (heff_mixed_work_bytes(mpo, site, 0, mL, mR) + sizeof(cd) - 1) / sizeof(cd);
+  return std::max(2 * one, mixed);
+}
+
+vb_status vb_heff2_apply(const vb_mpo *mpo, int i, int mL, int mR, const double *L, const double *R,
+                         const double *theta, double *y, double *work, int dtype, void *stream) {
+  if (!mpo || i < 0 || i + 1 >= mpo->n || mL < 1 || mR < 1 || !L || !R || !theta || !y || !work)
+    return fail(VB_EINVAL, "vb_heff2_apply: bad argument");
+  VB_TRY(mpo_upload(mpo));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == VB_MIXED)
+    return heff_mixed_apply(mpo, i, 1, mL, mR, (const cd *)L, (const cd *)R, (const cd *)theta, (cd *)y,
+                            work, vb_heff_work_elems(mpo, i, mL, mR, 1) * sizeof(cd), st);
+  const MpoSite &S = mpo->sites[i], &S2 = mpo->sites[i + 1];
+  size_t th = (size_t)mL * S.d * S2.d * mR;
+  size_t w = std::max(S.wl, std::max(S.wr, S2.wr));
+  cd *T1 = (cd *)work, *T2 = T1 + th * w;
+  return heff2_fp64(mpo, i, mL, mR, (const cd *)L, (const cd *)R, (const cd *)theta, (cd *)y, T1, T2,
+                    (long long)(th * w), st);
+}
+
+vb_status vb_heff1_apply(const vb_mpo *mpo, int j, int mL, int mR, const double *L, const double *R,
+                         const double *C, double *y, double *work, int dtype, void *stream) {
+  if (!mpo || j < 0 || j >= mpo->n || mL < 1 || mR < 1 || !L || !R || !C || !y || !work)
+    return fail(VB_EINVAL, "vb_heff1_apply: bad argument");
+  VB_TRY(mpo_upload(mpo));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == VB_MIXED)
+    return heff_mixed_apply(mpo, j, 0, mL, mR, (const cd *)L, (const cd *)R, (const cd *)C, (cd *)y, work,
+                            vb_heff_work_elems(mpo, j, mL, mR, 0) * sizeof(cd), st);
+  const MpoSite &S = mpo->sites[j];
+  size_t one = (size_t)mL * S.d * mR * std::max(S.wl, S.wr);
+  cd *T1 = (cd *)work, *T2 = T1 + one;
+  return heff1_fp64(mpo, j, mL, mR, (const cd *)L, (const cd *)R, (const cd *)C, (cd *)y, T1, T2,
+                    (long long)one, st);
+}
+
+size_t vb_env_work_elems(const vb_mpo *mpo, int site, int mL, int mR) {
+  if (!mpo || site < 0 || site >= mpo->n) return 0;
+  const MpoSite &S = mpo->sites[site];
+  return 2 * (size_t)mL * S.d * mR * std::max(S.wl, S.wr);
+}
+
+vb_status vb_env_left_update(const vb_mpo *mpo, int p, int mL, int mR, const double *L, const double *A,
+                             double *Lnew, double *work, void *stream) {
+  if (!mpo || p < 0 || p >= mpo->n || mL < 1 || mR < 1 || !L || !A || !Lnew || !work)
+    return fail(VB_EINVAL, "vb_env_left_update: bad argument");
+  VB_TRY(mpo_upload(mpo));
+  size_t half = vb_env_work_elems(mpo, p, mL, mR) / 2;
+  return env_left(mpo, p, mL, mR, (const cd *)L, (const cd *)A, (cd *)Lnew, (cd *)work, (cd *)work + half,
+                  (long long)half, (cudaStream_t)stream);
+}
+
+vb_status vb_env_right_update(const vb_mpo *mpo, int p, int mL, int mR, const double *R, const double *B,
+                              double *Rnew, double *work, void *stream) {
+  if (!mpo || p < 0 || p >= mpo->n || mL < 1 || mR < 1 || !R || !B || !Rnew || !work)
+    return fail(VB_EINVAL, "vb_env_right_update: bad argument");
+  VB_TRY(mpo_upload(mpo));
+  size_t half = vb_env_work_elems(mpo, p, mL, mR) / 2;
+  return env_right(mpo, p, mL, mR, (const cd *)R, (const cd *)B, (cd *)Rnew, (cd *)work, (cd *)work + half,
+                   (long long)half, (cudaStream_t)stream);
+}
+
+size_t vb_eig_work_bytes(int n, int k_want) {
+  if (n < 1 || k_want < 1) return 0;
+  return EigWork::bytes(n, k_want);
+}
+
+vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *evals, double *evecs,
+                          void *work, void *stream) {
+  if (n < 1 || !rho || k_want < 1 || k_want > n || k_vec < 0 || k_vec > k_want || !evals || !work ||
+      (k_vec > 0 && !evecs))
+    return fail(VB_EINVAL, "vb_herm_eig_top: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  VB_TRY(eig_values(n, (cd *)rho, k_want, evals, work, st));
+  if (k_vec > 0) VB_TRY(eig_vectors(n, (cd *)rho, k_want, k_vec, evals, (cd *)evecs, work, st));
+  return VB_OK;
+}
+
+}  // extern "C"
