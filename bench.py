@@ -1,0 +1,355 @@
+"""Benchmark: 2TDVP time steps (sweeps) of the internal-conversion-like model.
+
+Workload: 2 electronic states + 24 harmonic modes (d_I in 10..30), linear,
+quadratic intra-mode and 24 bilinear inter-mode couplings (seed 1002), max
+bond dimension 64, DBSS threshold 1e-8, dt = 0.5 fs. One step = one 2TDVP
+time step (left-to-right + right-to-left half sweeps). The timed state is a
+random right-canonical MPS with every bond at min(64, full dimension), i.e.
+the steady state at the bond cap that a long propagation reaches.
+
+Prints ONE JSON line (rank 0). `value` is device-timed sweeps/s summed over
+ranks (each rank propagates its own replica: a single trajectory does not
+shard); `e2e` is the same metric through the C ABI with host buffers;
+`roofline` describes the H_eff products (the path's dominant operation)
+measured live with CUDA events; `cpu_baseline` times the CPU oracle on a
+bounded sample of the same sweep. `--impl reference` times that oracle as
+the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import vibmodels as vm  # noqa: E402
+
+METRIC = "2TDVP sweeps/s & H_eff·ψ TFLOP/s (% peak), mixed vs FP64 at stated population error"
+UNIT = "sweeps/s"
+M_MAX = 64
+EPS = 1e-8
+DT_FS = 0.5
+STATE_SEED = 424242
+WORKLOAD = ("internal-conversion-like: 2 states + 24 modes (d 10-30, seed 1002), linear + quadratic "
+            "+ 24 bilinear couplings, max bond 64, DBSS 1e-8, dt 0.5 fs, bond-saturated state")
+# GB300 FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 / bf16 tensor-core ratio
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler_start():
+    fd, path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+    os.close(fd)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200", "-f", path], stdout=subprocess.DEVNULL,
+                                stderr=subprocess.DEVNULL)
+    except OSError:
+        proc = None
+    return proc, path
+
+
+def _clock_sampler_stop(proc, path, gpu_index):
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    if proc is None:
+        return out
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        with open(path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9 or not c[0].isdigit() or int(c[0]) != gpu_index:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    smax.append(float(c[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(path)
+    except OSError:
+        pass
+    if sm:
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+               "samples": len(sm)}
+    return out
+
+
+def _oracle_sample(model, tensors, budget_s: float):
+    """Time the CPU oracle on the first two-site updates of one sweep of the
+    same workload, growing the sample until about budget_s seconds are spent;
+    returns (sweeps/s extrapolated by update count, updates timed, seconds,
+    environment set-up seconds). The first updates sit at the chain end where
+    bonds are small, so the extrapolation overstates the oracle's speed."""
+    import copy
+
+    from oracle import mpo as ompo
+    from oracle import tdvp as otdvp
+    W = ompo.build_mpo(model)
+    n = len(tensors)
+    per_sweep = 2 * (n - 1)
+    t0 = time.perf_counter()
+    base = otdvp.Tdvp2(otdvp.MPS([t.copy() for t in tensors]), W,
+                       otdvp.TdvpOptions(m_max=M_MAX, eps=EPS, krylov_max=30, krylov_tol=1e-13))
+    setup = time.perf_counter() - t0
+    pairs, elapsed = 1, 0.0
+    while True:
+        sim = copy.deepcopy(base)
+        t0 = time.perf_counter()
+        sim.step(DT_FS, max_pairs=pairs)
+        elapsed = time.perf_counter() - t0
+        if elapsed >= 0.5 * budget_s or pairs >= per_sweep:
+            break
+        pairs += 1
+    return (pairs / per_sweep) / elapsed, pairs, elapsed, setup
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    model = vm.model_internal_conversion()
+    tensors = vm.random_right_canonical_mps(STATE_SEED, vm.local_dims(model), M_MAX)
+    budget = max(4.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        _oracle_sample(model, tensors, min(budget, 2.0))
+    vals, pairs_l, secs = [], [], []
+    for _ in range(args.steps):
+        v, pairs, el, _ = _oracle_sample(model, tensors, budget)
+        vals.append(v)
+        pairs_l.append(pairs)
+        secs.append(el)
+    value = float(np.mean(vals))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "first two-site updates of one sweep, extrapolated"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{pairs_l[-1]} of {2 * (len(tensors) - 1)} two-site updates of one "
+                                   f"sweep per step ({secs[-1]:.1f} s), extrapolated by update count"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1908_10588_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1908_10588_gb300 as P
+
+    dtype = P.VB_MIXED if args.dtype == "mixed" else P.VB_FP64
+    model = vm.model_internal_conversion()
+    dims = vm.local_dims(model)
+    tensors = vm.random_right_canonical_mps(STATE_SEED + rank, dims, M_MAX)
+    mpo = P.Mpo(model)
+    stream = torch.cuda.current_stream()
+    mps = P.Mps(mpo, m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=stream, tensors=tensors)
+    sweep_kw = dict(m_max=M_MAX, eps=EPS, zero_floor=1e-14, krylov_max=30, krylov_tol=1e-13)
+    for _ in range(args.warmup):
+        mps.sweep(DT_FS, **sweep_kw)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the library's stream)
+    P.vb_profile_read(reset=True)
+    P.vb_profile_enable(True)
+    launches0 = P.vb_kernel_launches()
+    proc, cpath = _clock_sampler_start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(mps.sweep(DT_FS, **sweep_kw))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = _clock_sampler_stop(proc, cpath, local)
+    launches = P.vb_kernel_launches() - launches0
+    P.vb_profile_enable(False)
+    prof = P.vb_profile_read(reset=True)
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1e3)
+    pops = mps.populations()
+    bonds = mps.bond_dims()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = 0 if args.no_e2e else 1
+    h2d = sum(t.nbytes for t in tensors)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        m2 = P.Mps(mpo, m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=stream, tensors=tensors)
+        m2.sweep(DT_FS, **sweep_kw)
+        out = m2.tensors()
+        pe = m2.populations()
+        d2h = sum(o.nbytes for o in out) + pe.nbytes
+        m2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = ws * e2e_steps / e2e_s if e2e_steps else None
+
+    # ---- roofline of the H_eff products
+    peaks, src = _peaks()
+    h2 = prof["heff2"]
+    heff_ms = h2["ms"] + prof["heff1"]["ms"]
+    heff_flops = h2["flops"] + prof["heff1"]["flops"]
+    achieved = heff_flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else 0.0
+    if dtype == P.VB_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz (nominal)"}
+    else:
+        pk = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk, "traffic": None,
+                "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio"}
+    roof["kernel"] = "H_eff products (two- and one-site), algorithmic flops / event time"
+    roof["heff_calls"] = h2["calls"] + prof["heff1"]["calls"]
+    roof["heff_ms_per_call"] = heff_ms / max(1, roof["heff_calls"])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if dtype == P.VB_FP64 else "c64-tf32x3/f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_sites": len(dims), "m_max": M_MAX, "eps": EPS, "dt_fs": DT_FS,
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "per-step working set (Krylov basis ~0.8 GB) exceeds L2"},
+        "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
+        "heff_tflops": achieved,
+        "krylov_iters_max": max(s.krylov_iters_max for s in stats),
+        "max_bond": max(bonds),
+        "populations": [float(x) for x in pops],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, pairs, el, _ = _oracle_sample(model, tensors, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{pairs} of {2 * (len(dims) - 1)} two-site updates of one sweep "
+                                          f"({el:.1f} s), extrapolated by update count"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mps.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_kernel_case(args):
+    """One H_eff,2 product at the largest two-site shape of the workload
+    (mL = mR = 64, the two largest adjacent d), repeated --steps times; a
+    small, self-contained case for profiler captures (about 1.5 GB)."""
+    import torch
+    from paper_1908_10588_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1908_10588_gb300 as P
+    dtype = P.VB_MIXED if args.dtype == "mixed" else P.VB_FP64
+    model = vm.model_internal_conversion()
+    dims = vm.local_dims(model)
+    i = max(range(1, len(dims) - 2), key=lambda k: dims[k] * dims[k + 1])
+    mpo = P.Mpo(model)
+    wl, d1, _ = mpo.site_dims(i)
+    _, d2, wr = mpo.site_dims(i + 1)
+    rng = np.random.Generator(np.random.PCG64(5))
+    L = torch.from_numpy(vm.random_hermitian_env(rng, M_MAX, wl)).cuda()
+    R = torch.from_numpy(vm.random_hermitian_env(rng, M_MAX, wr)).cuda()
+    x = torch.from_numpy(vm.random_complex(rng, (M_MAX, d1, d2, M_MAX))).cuda()
+    y = torch.empty_like(x)
+    work = torch.empty(P.vb_heff_work_elems(mpo, i, M_MAX, M_MAX, True), dtype=torch.complex128, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        P.vb_heff2_apply(mpo, i, M_MAX, M_MAX, L, R, x, y, work, dtype, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        P.vb_heff2_apply(mpo, i, M_MAX, M_MAX, L, R, x, y, work, dtype, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": "heff2", "site": i, "d1": d1, "d2": d2, "w_in": wl, "w_out": wr,
+                      "ms_per_apply": ms}), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-case", default=None, choices=[None, "heff2"])
+    args = ap.parse_args()
+    if args.kernel_case:
+        return run_kernel_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -181,6 +181,25 @@ vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *eva
                           double *evecs, void *work, void *stream);
 size_t vb_eig_work_bytes(int n, int k_want);
 
+/* ---- measurement (not part of the method; the paper has no counterpart).
+ * Number of CUDA kernels this library has launched since it was loaded. */
+unsigned long long vb_kernel_launches(void);
+
+/* Per-phase device time of tdvp2_sweep measured with CUDA events recorded on
+ * the handle's stream around every phase (0 = H_eff,2 products, 1 = H_eff,1
+ * products, 2 = Krylov vector work and the small exponential, 3 = split:
+ * reduced density matrix, eigensolver and the new tensors, 4 = environment
+ * updates, 5 = merge of two sites). heff_flops[c] counts the algorithmic
+ * floating-point operations of the H_eff products of class c (a complex
+ * multiply-add is 8, real-times-complex 4, an identity-block add 2). */
+typedef struct {
+  double ms[8];
+  long long calls[8];
+  double heff_flops[2];
+} vb_profile;
+vb_status vb_profile_enable(int on);
+vb_status vb_profile_read(vb_profile *out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

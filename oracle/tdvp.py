@@ -118,31 +118,31 @@ def padded_product_mps(dims, indices, m_pad=None) -> MPS:
 # -------------------------------------------------------------- contractions
 def env_left_update(L, A, W):
     """L_new[y', v, y] = sum conj(A[x,s',y']) L[x,w,z] W[w,s',s,v] A[z,s,y]."""
-    T1 = np.einsum("xwz,zsy->xwsy", L, A)
-    T2 = np.einsum("wpsv,xwsy->xpvy", W, T1)
-    return np.einsum("xpq,xpvy->qvy", np.conj(A), T2)
+    T1 = np.einsum("xwz,zsy->xwsy", L, A, optimize=True)
+    T2 = np.einsum("wpsv,xwsy->xpvy", W, T1, optimize=True)
+    return np.einsum("xpq,xpvy->qvy", np.conj(A), T2, optimize=True)
 
 
 def env_right_update(R, B, W):
     """R_new[a', w, a] = sum conj(B[a',t',y]) R[y,v,z] W[w,t',t,v] B[a,t,z]."""
-    T1 = np.einsum("atz,yvz->atyv", B, R)
-    T2 = np.einsum("wqtv,atyv->awqy", W, T1)
-    return np.einsum("xqy,awqy->xwa", np.conj(B), T2)
+    T1 = np.einsum("atz,yvz->atyv", B, R, optimize=True)
+    T2 = np.einsum("wqtv,atyv->awqy", W, T1, optimize=True)
+    return np.einsum("xqy,awqy->xwa", np.conj(B), T2, optimize=True)
 
 
 def heff2_apply(L, Wi, Wj, R, theta):
     """y = H_eff,2 theta in the order L, W_i, W_{i+1}, R."""
-    T1 = np.einsum("xwa,astb->xwstb", L, theta)
-    T2 = np.einsum("wpsv,xwstb->xpvtb", Wi, T1)
-    T3 = np.einsum("vqtu,xpvtb->xpqub", Wj, T2)
-    return np.einsum("yub,xpqub->xpqy", R, T3)
+    T1 = np.einsum("xwa,astb->xwstb", L, theta, optimize=True)
+    T2 = np.einsum("wpsv,xwstb->xpvtb", Wi, T1, optimize=True)
+    T3 = np.einsum("vqtu,xpvtb->xpqub", Wj, T2, optimize=True)
+    return np.einsum("yub,xpqub->xpqy", R, T3, optimize=True)
 
 
 def heff1_apply(L, W, R, C):
     """y = H_eff,1 C in the order L, W, R."""
-    T1 = np.einsum("xwa,atb->xwtb", L, C)
-    T2 = np.einsum("wqtv,xwtb->xqvb", W, T1)
-    return np.einsum("yvb,xqvb->xqy", R, T2)
+    T1 = np.einsum("xwa,atb->xwtb", L, C, optimize=True)
+    T2 = np.einsum("wqtv,xwtb->xqvb", W, T1, optimize=True)
+    return np.einsum("yvb,xqvb->xqy", R, T2, optimize=True)
 
 
 # ------------------------------------------------------ Krylov exponential
@@ -282,16 +282,22 @@ class Tdvp2:
             st.noconv += 1
         return y
 
-    def step(self, dt_fs: float) -> StepStats:
+    def step(self, dt_fs: float, max_pairs: int | None = None) -> StepStats:
         """One time step = left-to-right half sweep with dt/2 followed by the
-        right-to-left half sweep with dt/2."""
+        right-to-left half sweep with dt/2. `max_pairs` stops after that many
+        two-site updates (a bounded timing sample; the state is then left
+        mid-sweep and the step is not complete)."""
         st = StepStats()
+        done = 0
         A, W, L, R = self.mps.A, self.W, self.L, self.R
         n = self.mps.n
         tau = 0.5 * dt_fs
         # left to right
         for i in range(n - 1):
-            theta = np.einsum("asx,xtb->astb", A[i], A[i + 1])
+            if max_pairs is not None and done >= max_pairs:
+                return st
+            done += 1
+            theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
             Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
             theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
             A[i], C, disc = split_left(theta, self.opts)
@@ -303,7 +309,10 @@ class Tdvp2:
             A[i + 1] = C
         # right to left
         for i in range(n - 2, -1, -1):
-            theta = np.einsum("asx,xtb->astb", A[i], A[i + 1])
+            if max_pairs is not None and done >= max_pairs:
+                return st
+            done += 1
+            theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
             Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
             theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
             C, A[i + 1], disc = split_right(theta, self.opts)

@@ -24,7 +24,8 @@ EXPORTED = [
     "mpo_site_tensor", "mps_create", "mps_create_from_tensors", "mps_destroy", "mps_n_sites",
     "mps_bond_dims", "mps_get_site", "tdvp2_sweep", "measure_populations", "vb_heff2_apply",
     "vb_heff1_apply", "vb_heff_work_elems", "vb_env_left_update", "vb_env_right_update",
-    "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes",
+    "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
+    "vb_profile_enable", "vb_profile_read",
 ]
 
 
@@ -54,6 +55,13 @@ class vb_mps_opts(C.Structure):
 class vb_tdvp_opts(C.Structure):
     _fields_ = [("m_max", C.c_int), ("eps", C.c_double), ("zero_floor", C.c_double),
                 ("krylov_max", C.c_int), ("krylov_tol", C.c_double), ("on_noconv", C.c_int)]
+
+
+class vb_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("calls", C.c_longlong * 8), ("heff_flops", C.c_double * 2)]
+
+
+PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge"]
 
 
 class vb_sweep_stats(C.Structure):
@@ -96,6 +104,9 @@ def lib():
         "vb_env_work_elems": (sz, [vp, i, i, i]),
         "vb_herm_eig_top": (i, [i, vp, i, i, vp, vp, vp, vp]),
         "vb_eig_work_bytes": (sz, [i, i]),
+        "vb_kernel_launches": (C.c_ulonglong, []),
+        "vb_profile_enable": (i, [i]),
+        "vb_profile_read": (i, [C.POINTER(vb_profile), i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -315,3 +326,20 @@ def vb_eig_work_bytes(n, k_want) -> int:
 def vb_herm_eig_top(n, rho, k_want, k_vec, evals, evecs, work, stream=None):
     check(lib().vb_herm_eig_top(n, _ptr(rho), k_want, k_vec, _ptr(evals), _ptr(evecs), _ptr(work),
                                 _stream_ptr(stream)))
+
+
+def vb_kernel_launches() -> int:
+    return int(lib().vb_kernel_launches())
+
+
+def vb_profile_enable(on: bool = True):
+    check(lib().vb_profile_enable(int(on)))
+
+
+def vb_profile_read(reset: bool = True) -> dict:
+    p = vb_profile()
+    check(lib().vb_profile_read(C.byref(p), int(reset)))
+    out = {name: {"ms": p.ms[k], "calls": int(p.calls[k])} for k, name in enumerate(PHASES)}
+    out["heff2"]["flops"] = p.heff_flops[0]
+    out["heff1"]["flops"] = p.heff_flops[1]
+    return out

@@ -31,7 +31,19 @@ const char *get_error();
     if (_s != VB_OK) return _s;    \
   } while (0)
 
-#define VB_CHECK_LAUNCH() VB_TRY_CUDA(cudaGetLastError())
+void count_launch();
+#define VB_CHECK_LAUNCH()  \
+  do {                     \
+    ::vb::count_launch();  \
+    VB_TRY_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// ---- per-phase event profiler (host side, single-threaded use)
+enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5 };
+bool prof_on();
+void prof_begin(int phase, cudaStream_t st);
+void prof_end(int phase, cudaStream_t st, double flops);
+void prof_collect();  // after a stream synchronisation: fold finished events into the totals
 
 inline vb_status fail(vb_status s, const std::string &msg) {
   set_error(msg);

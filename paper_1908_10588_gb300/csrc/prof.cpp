@@ -1,0 +1,109 @@
+// Launch counter and per-phase CUDA-event profiler used by the benchmark.
+#include <atomic>
+#include <cstring>
+#include <vector>
+
+#include "common.h"
+
+namespace vb {
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+struct Pending {
+  int phase;
+  cudaEvent_t a, b;
+  double flops;
+};
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> open_start;  // per phase
+  double ms[8] = {0};
+  long long calls[8] = {0};
+  double flops[2] = {0, 0};
+} g_prof;
+
+cudaEvent_t take_event() {
+  if (!g_prof.pool.empty()) {
+    cudaEvent_t e = g_prof.pool.back();
+    g_prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool prof_on() { return g_prof.on; }
+
+void prof_begin(int phase, cudaStream_t st) {
+  if (!g_prof.on) return;
+  if (g_prof.open_start.size() < 8) g_prof.open_start.assign(8, nullptr);
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, st);
+  g_prof.open_start[phase] = e;
+}
+
+void prof_end(int phase, cudaStream_t st, double flops) {
+  if (!g_prof.on || g_prof.open_start.size() < 8 || !g_prof.open_start[phase]) return;
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, st);
+  g_prof.pending.push_back(Pending{phase, g_prof.open_start[phase], e, flops});
+  g_prof.open_start[phase] = nullptr;
+}
+
+void prof_collect() {
+  if (g_prof.pending.empty()) return;
+  std::vector<Pending> keep;
+  for (const Pending &p : g_prof.pending) {
+    if (cudaEventQuery(p.b) != cudaSuccess) {
+      cudaGetLastError();
+      keep.push_back(p);
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    g_prof.ms[p.phase] += ms;
+    g_prof.calls[p.phase] += 1;
+    if (p.phase < 2) g_prof.flops[p.phase] += p.flops;
+    g_prof.pool.push_back(p.a);
+    g_prof.pool.push_back(p.b);
+  }
+  g_prof.pending.swap(keep);
+}
+
+}  // namespace vb
+
+extern "C" {
+
+unsigned long long vb_kernel_launches(void) { return vb::g_launches.load(); }
+
+vb_status vb_profile_enable(int on) {
+  vb::g_prof.on = on != 0;
+  return VB_OK;
+}
+
+vb_status vb_profile_read(vb_profile *out, int reset) {
+  if (!out) return vb::fail(VB_EINVAL, "vb_profile_read: null argument");
+  vb::prof_collect();
+  std::memset(out, 0, sizeof(*out));
+  for (int i = 0; i < 8; ++i) {
+    out->ms[i] = vb::g_prof.ms[i];
+    out->calls[i] = vb::g_prof.calls[i];
+  }
+  out->heff_flops[0] = vb::g_prof.flops[0];
+  out->heff_flops[1] = vb::g_prof.flops[1];
+  if (reset) {
+    for (int i = 0; i < 8; ++i) {
+      vb::g_prof.ms[i] = 0;
+      vb::g_prof.calls[i] = 0;
+    }
+    vb::g_prof.flops[0] = vb::g_prof.flops[1] = 0;
+  }
+  return VB_OK;
+}
+
+}  // extern "C"

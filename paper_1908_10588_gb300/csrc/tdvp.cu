@@ -262,13 +262,40 @@ struct HeffOp {
   const cd *L, *R;
 };
 
+// algorithmic floating-point operations of one W-site application to
+// `outer` stacked vectors: a non-identity d x d block costs 4 d^2 per vector
+// (real operator times complex data), an identity block 2 d
+double wsite_flops(const MpoSite &S, double outer) {
+  double f = 0.0;
+  for (const MpoBlock &B : S.blocks) f += B.ident ? 2.0 * S.d : 4.0 * S.d * S.d;
+  return f * outer;
+}
+
+double heff_flops(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
+  const MpoSite &S = mpo->sites[site];
+  if (two_site) {
+    const MpoSite &S2 = mpo->sites[site + 1];
+    const double th = (double)mL * S.d * S2.d * mR;
+    return 8.0 * th * mL * S.wl + wsite_flops(S, (double)mL * S2.d * mR) +
+           wsite_flops(S2, (double)mL * S.d * mR) + 8.0 * th * S2.wr * mR;
+  }
+  const double c = (double)mL * S.d * mR;
+  return 8.0 * c * mL * S.wl + wsite_flops(S, (double)mL * mR) + 8.0 * c * S.wr * mR;
+}
+
 vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
+  const int ph = op.two_site ? PH_HEFF2 : PH_HEFF1;
+  prof_begin(ph, s->st);
+  vb_status r;
   if (s->dtype == VB_MIXED)
-    return heff_mixed_apply(s->mpo, op.site, op.two_site, op.mL, op.mR, op.L, op.R, x, y, s->mixw,
-                            s->mixw_bytes, s->st);
-  if (op.two_site)
-    return heff2_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
-  return heff1_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
+    r = heff_mixed_apply(s->mpo, op.site, op.two_site, op.mL, op.mR, op.L, op.R, x, y, s->mixw,
+                         s->mixw_bytes, s->st);
+  else if (op.two_site)
+    r = heff2_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
+  else
+    r = heff1_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
+  prof_end(ph, s->st, prof_on() ? heff_flops(s->mpo, op.site, op.two_site, op.mL, op.mR) : 0.0);
+  return r;
 }
 
 // ---- x <- exp(-i H dt/hbar) x by Lanczos with full re-orthogonalisation
@@ -280,14 +307,17 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
   cd *V = s->V;
   kmax = (int)std::min<long long>(std::min(kmax, s->kcap), N);
   const double tau = dt_fs / HBAR_EV_FS;
+  prof_begin(PH_KRYLOV, st);
   VB_TRY(vec_norm2(x, N, s->d_nrm, s->d_part, np, st));
   VB_TRY(vec_copy_scaled(x, V, N, st));
   VB_TRY(vec_scale_inv(V, N, s->d_nrm, st));
+  prof_end(PH_KRYLOV, st, 0.0);
   int kdim = 0;
   *converged = 0;
   for (int k = 0; k < kmax; ++k) {
     cd *w = V + (k + 1) * ldv;
     VB_TRY(apply_heff(s, op, V + k * ldv, w));
+    prof_begin(PH_KRYLOV, st);
     VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st));
     VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
     VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st));
@@ -297,6 +327,7 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     VB_TRY(vec_norm2(w, N, s->d_bnext, s->d_part, np, st));
     VB_TRY(tridiag_expm(s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     VB_TRY_CUDA(cudaMemcpyAsync(s->d_flag + 1, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    prof_end(PH_KRYLOV, st, 0.0);
     VB_TRY_CUDA(cudaStreamSynchronize(st));
     const double err = s->h_flag[0], b = s->h_flag[1];
     kdim = k + 1;
@@ -305,11 +336,15 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       *converged = 1;
       break;
     }
+    prof_begin(PH_KRYLOV, st);
     VB_TRY_CUDA(cudaMemcpyAsync(s->d_beta + k, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
     VB_TRY(vec_scale_inv(w, N, s->d_bnext, st));
+    prof_end(PH_KRYLOV, st, 0.0);
   }
   *iters = kdim;
+  prof_begin(PH_KRYLOV, st);
   VB_TRY(vec_combine(V, ldv, kdim, s->d_u, s->d_nrm, x, N, st));
+  prof_end(PH_KRYLOV, st, 0.0);
   return VB_OK;
 }
 
@@ -702,15 +737,21 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
   // left to right, tau = dt/2
   for (int i = 0; i + 1 < n; ++i) {
     const int mL = s->bond[i], mR = s->bond[i + 2], d1 = s->dims[i], d2 = s->dims[i + 1];
+    prof_begin(PH_MERGE, s->st);
     VB_TRY(merge(s, i));
+    prof_end(PH_MERGE, s->st, 0.0);
     HeffOp op{1, i, mL, mR, s->L[i], s->R[i + 2]};
     VB_TRY(evolve(op, s->theta, (long long)mL * d1 * d2 * mR, tau));
     int k = 0;
     double disc = 0.0;
+    prof_begin(PH_SPLIT, s->st);
     VB_TRY(split(s, true, mL, d1, d2, mR, to, s->A[i], s->A[i + 1], &k, &disc));
+    prof_end(PH_SPLIT, s->st, 0.0);
     st.discarded_weight += disc;
     s->bond[i + 1] = k;
+    prof_begin(PH_ENV, s->st);
     VB_TRY(env_left(mpo, i, mL, k, s->L[i], s->A[i], s->L[i + 1], s->T1, s->T2, s->inter_cap, s->st));
+    prof_end(PH_ENV, s->st, 0.0);
     if (i + 2 < n) {
       HeffOp op1{0, i + 1, k, mR, s->L[i + 1], s->R[i + 2]};
       VB_TRY(evolve(op1, s->A[i + 1], (long long)k * d2 * mR, -tau));
@@ -719,22 +760,29 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
   // right to left, tau = dt/2
   for (int i = n - 2; i >= 0; --i) {
     const int mL = s->bond[i], mR = s->bond[i + 2], d1 = s->dims[i], d2 = s->dims[i + 1];
+    prof_begin(PH_MERGE, s->st);
     VB_TRY(merge(s, i));
+    prof_end(PH_MERGE, s->st, 0.0);
     HeffOp op{1, i, mL, mR, s->L[i], s->R[i + 2]};
     VB_TRY(evolve(op, s->theta, (long long)mL * d1 * d2 * mR, tau));
     int k = 0;
     double disc = 0.0;
+    prof_begin(PH_SPLIT, s->st);
     VB_TRY(split(s, false, mL, d1, d2, mR, to, s->A[i], s->A[i + 1], &k, &disc));
+    prof_end(PH_SPLIT, s->st, 0.0);
     st.discarded_weight += disc;
     s->bond[i + 1] = k;
+    prof_begin(PH_ENV, s->st);
     VB_TRY(env_right(mpo, i + 1, k, mR, s->R[i + 2], s->A[i + 1], s->R[i + 1], s->T1, s->T2, s->inter_cap,
                      s->st));
+    prof_end(PH_ENV, s->st, 0.0);
     if (i > 0) {
       HeffOp op1{0, i, mL, k, s->L[i], s->R[i + 1]};
       VB_TRY(evolve(op1, s->A[i], (long long)mL * d1 * k, -tau));
     }
   }
   VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  prof_collect();
   for (int b = 1; b < n; ++b) st.max_bond = std::max(st.max_bond, s->bond[b]);
   if (stats) *stats = st;
   return VB_OK;

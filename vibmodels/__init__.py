@@ -252,3 +252,36 @@ def random_isometry_rows(rng: np.random.Generator, rows: int, cols: int) -> np.n
     ph = np.diag(r) / np.abs(np.diag(r))
     q = q * ph[None, :]
     return np.conj(q.T)
+
+
+def bond_caps(dims, m_max: int) -> list:
+    """min(m_max, full dimension) of every bond of a chain with site dims."""
+    out = []
+    n = len(dims)
+    for b in range(n - 1):
+        left = 1
+        for d in dims[: b + 1]:
+            left = min(left * int(d), 1 << 40)
+        right = 1
+        for d in dims[b + 1:]:
+            right = min(right * int(d), 1 << 40)
+        out.append(int(min(left, right, m_max)))
+    return out
+
+
+def random_right_canonical_mps(seed: int, dims, m_max: int) -> list:
+    """Random MPS with every bond at min(m_max, full dimension): sites
+    1..n-1 right-orthonormal (complex Gaussian rows orthonormalised by a
+    library QR), site 0 a normalised random tensor. Stands in for a
+    bond-saturated state of a long propagation."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    D = [1] + bond_caps(dims, m_max) + [1]
+    ts = []
+    for p, d in enumerate(dims):
+        if p == 0:
+            t = random_complex(rng, (1, d, D[1]))
+            t = t / np.linalg.norm(t)
+        else:
+            t = random_isometry_rows(rng, D[p], d * D[p + 1]).reshape(D[p], d, D[p + 1])
+        ts.append(np.ascontiguousarray(t, dtype=np.complex128))
+    return ts
