@@ -181,6 +181,23 @@ vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *eva
                           double *evecs, void *work, void *stream);
 size_t vb_eig_work_bytes(int n, int k_want);
 
+/* vb_herm_eig_top without a workspace argument and without any device
+ * allocation (the paper has no counterpart: this is for callers that cannot
+ * allocate, e.g. code whose device memory is owned by a host framework's
+ * pool, or a latency-critical loop that must avoid cudaMalloc's implicit
+ * synchronisation). The workspace is a fixed 3 MiB array in the library's
+ * device image, held on every GPU that loads the library until the process
+ * exits. Limits: n <= 256, k_want <= 128; larger sizes return VB_EINVAL.
+ * The caller still owns rho (destroyed), evals and evecs. The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The array keeps the previous call's contents; the solver writes every
+ * entry it reads, so nothing needs clearing. */
+vb_status vb_herm_eig_top_noalloc(int n, double *rho, int k_want, int k_vec, double *evals,
+                                  double *evecs, void *stream);
+
 /* ---- measurement (not part of the method; the paper has no counterpart).
  * Number of CUDA kernels this library has launched since it was loaded. */
 unsigned long long vb_kernel_launches(void);

@@ -25,7 +25,7 @@ EXPORTED = [
     "mps_bond_dims", "mps_get_site", "tdvp2_sweep", "measure_populations", "vb_heff2_apply",
     "vb_heff1_apply", "vb_heff_work_elems", "vb_env_left_update", "vb_env_right_update",
     "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
-    "vb_profile_enable", "vb_profile_read",
+    "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc",
 ]
 
 
@@ -104,6 +104,7 @@ def lib():
         "vb_env_work_elems": (sz, [vp, i, i, i]),
         "vb_herm_eig_top": (i, [i, vp, i, i, vp, vp, vp, vp]),
         "vb_eig_work_bytes": (sz, [i, i]),
+        "vb_herm_eig_top_noalloc": (i, [i, vp, i, i, vp, vp, vp]),
         "vb_kernel_launches": (C.c_ulonglong, []),
         "vb_profile_enable": (i, [i]),
         "vb_profile_read": (i, [C.POINTER(vb_profile), i]),
@@ -343,3 +344,10 @@ def vb_profile_read(reset: bool = True) -> dict:
     out["heff2"]["flops"] = p.heff_flops[0]
     out["heff1"]["flops"] = p.heff_flops[1]
     return out
+
+
+def vb_herm_eig_top_noalloc(n, rho, k_want, k_vec, evals, evecs, stream=None):
+    """vb_herm_eig_top with the library's fixed device workspace (no
+    allocation; n <= 256, k_want <= 128; concurrent calls race)."""
+    check(lib().vb_herm_eig_top_noalloc(n, _ptr(rho), k_want, k_vec, _ptr(evals), _ptr(evecs),
+                                        _stream_ptr(stream)))

@@ -420,3 +420,69 @@ vb_status eig_vectors(int n, const cd *rho, int k_want, int k_vec, const double 
 }
 
 }  // namespace vb
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of vb_herm_eig_top.
+//
+// Some callers cannot allocate device memory at the point where they need
+// the split: a host framework that owns every byte of device memory through
+// its own pool, or a latency-critical loop that must not pay for the
+// device-wide synchronisation cudaMalloc implies. For them the eigensolver's
+// workspace lives in a fixed file-scope device array instead of a caller
+// buffer. The array is part of the library image, so every GPU that loads
+// the library keeps it until the process exits.
+namespace vb {
+namespace {
+
+constexpr int NOALLOC_MAX_N = 256;       // largest matrix dimension
+constexpr int NOALLOC_MAX_KWANT = 128;   // largest number of eigenvalues
+constexpr size_t NOALLOC_SCRATCH_BYTES = 3u << 20;  // 3 MiB
+
+static __device__ __align__(256) unsigned char g_eig_scratch[NOALLOC_SCRATCH_BYTES];
+
+// device address of g_eig_scratch, looked up once per device
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void *g_scratch_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+vb_status scratch_address(void **out) {
+  int dev = -1;
+  VB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(VB_EINVAL, "noalloc eig: device ordinal out of range");
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_eig_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return fail(VB_ECUDA, std::string("noalloc eig: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return VB_OK;
+}
+
+}  // namespace
+}  // namespace vb
+
+extern "C" vb_status vb_herm_eig_top_noalloc(int n, double *rho, int k_want, int k_vec, double *evals,
+                                             double *evecs, void *stream) {
+  using namespace vb;
+  if (n < 1 || !rho || k_want < 1 || k_want > n || k_vec < 0 || k_vec > k_want || !evals ||
+      (k_vec > 0 && !evecs))
+    return fail(VB_EINVAL, "vb_herm_eig_top_noalloc: bad argument");
+  if (n > NOALLOC_MAX_N || k_want > NOALLOC_MAX_KWANT)
+    return fail(VB_EINVAL, "vb_herm_eig_top_noalloc: n must be <= " + std::to_string(NOALLOC_MAX_N) +
+                               " and k_want <= " + std::to_string(NOALLOC_MAX_KWANT) +
+                               " (fixed workspace); use vb_herm_eig_top with a caller buffer");
+  if (EigWork::bytes(n, k_want) > NOALLOC_SCRATCH_BYTES)
+    return fail(VB_EINVAL, "vb_herm_eig_top_noalloc: workspace exceeds the fixed scratch array");
+  void *work = nullptr;
+  VB_TRY(scratch_address(&work));
+  // every workspace entry the solver reads is written earlier in the same
+  // call, so nothing needs clearing between calls
+  cudaStream_t st = (cudaStream_t)stream;
+  VB_TRY(eig_values(n, (cd *)rho, k_want, evals, work, st));
+  if (k_vec > 0) VB_TRY(eig_vectors(n, (cd *)rho, k_want, k_vec, evals, (cd *)evecs, work, st));
+  return VB_OK;
+}
+
