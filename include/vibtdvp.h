@@ -80,7 +80,8 @@ typedef struct {
 
 typedef struct {
   int m_cap;          /* largest bond dimension the handle reserves memory for */
-  int dtype;          /* VB_FP64 or VB_MIXED (H_eff products in split-TF32) */
+  int dtype;          /* VB_FP64, or VB_MIXED: H_eff products on the tensor cores in TF32 with
+                         FP32 accumulation, everything else in FP64 */
   int pad_full;       /* mps_create: pad the product state to full bonds (<= m_cap) */
   int krylov_cap;     /* largest Krylov dimension reserved (default 40) */
   void *cuda_stream;  /* cudaStream_t */
@@ -206,12 +207,14 @@ unsigned long long vb_kernel_launches(void);
  * the handle's stream around every phase (0 = H_eff,2 products, 1 = H_eff,1
  * products, 2 = Krylov vector work and the small exponential, 3 = split:
  * reduced density matrix, eigensolver and the new tensors, 4 = environment
- * updates, 5 = merge of two sites). heff_flops[c] counts the algorithmic
+ * updates, 5 = merge of two sites; sub-phases of 3: 6 = reduced density
+ * matrix, 7 = tridiagonal reduction and eigenvalues, 8 = eigenvectors,
+ * 9 = new tensors and normalisation). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
  * multiply-add is 8, real-times-complex 4, an identity-block add 2). */
 typedef struct {
-  double ms[8];
-  long long calls[8];
+  double ms[12];
+  long long calls[12];
   double heff_flops[2];
 } vb_profile;
 vb_status vb_profile_enable(int on);

@@ -58,10 +58,11 @@ class vb_tdvp_opts(C.Structure):
 
 
 class vb_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("calls", C.c_longlong * 8), ("heff_flops", C.c_double * 2)]
+    _fields_ = [("ms", C.c_double * 12), ("calls", C.c_longlong * 12), ("heff_flops", C.c_double * 2)]
 
 
-PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge"]
+PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
+          "split_out"]
 
 
 class vb_sweep_stats(C.Structure):

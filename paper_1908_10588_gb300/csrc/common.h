@@ -39,7 +39,8 @@ void count_launch();
   } while (0)
 
 // ---- per-phase event profiler (host side, single-threaded use)
-enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5 };
+enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5, PH_RHO = 6, PH_EIGVAL = 7,
+       PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_COUNT = 12 };
 bool prof_on();
 void prof_begin(int phase, cudaStream_t st);
 void prof_end(int phase, cudaStream_t st, double flops);
@@ -51,28 +52,41 @@ inline vb_status fail(vb_status s, const std::string &msg) {
 }
 
 // ------------------------------------------------------------ complex
-struct __align__(16) cd {
-  double x, y;
+// interleaved complex of real type R (double on the FP64 path, float on the
+// mixed path); same memory layout as C99 complex
+template <class R>
+struct alignas(2 * sizeof(R)) cplx {
+  R x, y;
 };
+typedef cplx<double> cd;
+typedef cplx<float> cf;
 
-__host__ __device__ inline cd mkc(double a, double b) {
-  cd r;
+template <class R>
+__host__ __device__ inline cplx<R> mkc(R a, R b) {
+  cplx<R> r;
   r.x = a;
   r.y = b;
   return r;
 }
-__host__ __device__ inline cd cadd(cd a, cd b) { return mkc(a.x + b.x, a.y + b.y); }
-__host__ __device__ inline cd csub(cd a, cd b) { return mkc(a.x - b.x, a.y - b.y); }
-__host__ __device__ inline cd cmul(cd a, cd b) {
-  return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <class R>
+__host__ __device__ inline cplx<R> cadd(cplx<R> a, cplx<R> b) { return mkc<R>(a.x + b.x, a.y + b.y); }
+template <class R>
+__host__ __device__ inline cplx<R> csub(cplx<R> a, cplx<R> b) { return mkc<R>(a.x - b.x, a.y - b.y); }
+template <class R>
+__host__ __device__ inline cplx<R> cmul(cplx<R> a, cplx<R> b) {
+  return mkc<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__host__ __device__ inline cd cconj(cd a) { return mkc(a.x, -a.y); }
-__host__ __device__ inline cd cscale(cd a, double s) { return mkc(a.x * s, a.y * s); }
+template <class R>
+__host__ __device__ inline cplx<R> cconj(cplx<R> a) { return mkc<R>(a.x, -a.y); }
+template <class R>
+__host__ __device__ inline cplx<R> cscale(cplx<R> a, R s) { return mkc<R>(a.x * s, a.y * s); }
 // conj(a) * b
-__host__ __device__ inline cd cdotc(cd a, cd b) {
-  return mkc(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+template <class R>
+__host__ __device__ inline cplx<R> cdotc(cplx<R> a, cplx<R> b) {
+  return mkc<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
-__host__ __device__ inline double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
+template <class R>
+__host__ __device__ inline R cabs2(cplx<R> a) { return a.x * a.x + a.y * a.y; }
 
 // ------------------------------------------------------------ memory
 struct Alloc {
@@ -96,22 +110,27 @@ struct DBuf {
 // op codes for the strided batched complex GEMM
 enum Op { OP_N = 0, OP_T = 1, OP_C = 2 /* conj transpose */, OP_R = 3 /* conj, no transpose */ };
 
-struct GemmArgs {
+template <class R>
+struct GemmArgsT {
   int M, N, K, batch;
   int opA, opB;
-  const cd *A;
+  const cplx<R> *A;
   long long lda, sA;
-  const cd *B;
+  const cplx<R> *B;
   long long ldb, sB;
-  cd *C;
+  cplx<R> *C;
   long long ldc, sC;
-  cd alpha, beta;
+  cplx<R> alpha, beta;
   // element counts of the three buffers (required); every address the
   // kernel forms is checked against them on the host before the launch
   long long a_size, b_size, c_size;
 };
+typedef GemmArgsT<double> GemmArgs;
+typedef GemmArgsT<float> GemmArgsF;
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]; op(A) is M x K, op(B) is K x N.
-vb_status zgemm(const GemmArgs &g, cudaStream_t st);
+template <class R>
+vb_status gemm(const GemmArgsT<R> &g, cudaStream_t st);
+inline vb_status zgemm(const GemmArgs &g, cudaStream_t st) { return gemm<double>(g, st); }
 
 // ------------------------------------------------------------ MPO
 struct MpoBlock {
@@ -128,6 +147,7 @@ struct MpoSite {
   // device copies: operators, and for each direction a CSR over the produced
   // bond index: entries (consumed index, ident, op_off)
   double *d_ops = nullptr;
+  float *d_ops32 = nullptr;
   int *d_fwd_ptr = nullptr, *d_fwd_ent = nullptr;  // produce w_out from w_in
   int *d_bwd_ptr = nullptr, *d_bwd_ent = nullptr;  // produce w_in from w_out
   long long nnz_ops = 0;                           // non-identity blocks
@@ -162,8 +182,9 @@ struct WStrides {
 inline WStrides WS(long long p, long long w, long long s, long long q) { return WStrides{p, w, s, q}; }
 // x_size / y_size: element counts of X and Y; the largest offset the kernel
 // forms is checked against them before the launch
-vb_status wapply(const MpoSite &site, int dir, const cd *X, WStrides xs, long long x_size, cd *Y,
-                 WStrides ys, long long y_size, int P, int Q, cudaStream_t st);
+template <class R>
+vb_status wapply(const MpoSite &site, int dir, const cplx<R> *X, WStrides xs, long long x_size,
+                 cplx<R> *Y, WStrides ys, long long y_size, int P, int Q, cudaStream_t st);
 
 // ------------------------------------------------------------ vectors
 vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
@@ -184,16 +205,18 @@ int reduce_parts(long long n);
 
 // ------------------------------------------------------------ eigen
 struct EigWork {
-  // layout inside one device buffer
-  static size_t bytes(int n, int k_want);
+  // layout inside one device buffer (real type of size real_bytes)
+  static size_t bytes(int n, int k_want, int real_bytes = 8);
 };
 // phase 1: reduce rho (n x n, destroyed) to real tridiagonal form and compute
 // the k_want largest eigenvalues (descending) into evals (device)
-vb_status eig_values(int n, cd *rho, int k_want, double *evals, void *work, cudaStream_t st);
+template <class R>
+vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cudaStream_t st);
 // phase 2: eigenvectors for the first k_vec of those eigenvalues, written as
 // rows of evecs [k_vec][n] (device). Needs the same rho/work after phase 1.
-vb_status eig_vectors(int n, const cd *rho, int k_want, int k_vec, const double *evals,
-                      cd *evecs, void *work, cudaStream_t st);
+template <class R>
+vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R *evals,
+                      cplx<R> *evecs, void *work, cudaStream_t st);
 
 // Krylov tridiagonal exponential: from alpha[0..k], beta[0..k-1] (device),
 // u = exp(-i T tau) e_1 (k+1 complex) and err = bnext * |u_k| written to

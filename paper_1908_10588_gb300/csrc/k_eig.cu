@@ -2,7 +2,7 @@
 // and truncate the two-site tensor (Sec. 2.1.1: truncation by fixed M or by
 // DBSS, which both keep the largest Schmidt weights).
 //
-// Pipeline, all FP64 on the GPU:
+// Pipeline (templated on the real type; the FP64 path runs it in double):
 //  1. Householder reduction rho = Q T Q^+ (T Hermitian tridiagonal), one
 //     column per step: reflector, Hermitian matrix-vector product, the
 //     rank-2 update of the trailing block. Reflectors are kept row-wise in a
@@ -22,13 +22,27 @@ namespace {
 
 constexpr int INVIT_ROUNDS = 3;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
+template <class R>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double eps = 2.220446049250313e-16, tiny = 2.2250738585072014e-308, big = 1e150,
+                          huge = 1e300;
+};
+template <>
+struct Eps<float> {
+  static constexpr float eps = 1.1920929e-07f, tiny = 1.1754944e-38f, big = 1e18f, huge = 1e37f;
+};
+
 // block-wide sum, result broadcast to all threads
-__device__ double block_sum_all(double v, double *sh) {
+template <class R>
+__device__ R block_sum_all(R v, R *sh) {
   v = warp_sum(v);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int nw = (blockDim.x + 31) >> 5;
@@ -46,94 +60,103 @@ __device__ double block_sum_all(double v, double *sh) {
 
 struct EigLayout {
   size_t off_vref, off_tau, off_dg, off_ec, off_eabs, off_delta, off_p, off_y, off_lu, total;
-  EigLayout(int n, int k) {
+  EigLayout(int n, int k, int rb) {
+    const size_t cb = 2 * (size_t)rb;
     size_t o = 0;
     auto take = [&](size_t bytes) {
       size_t r = o;
       o += (bytes + 255) / 256 * 256;
       return r;
     };
-    off_vref = take((size_t)n * n * sizeof(cd));
-    off_tau = take((size_t)n * sizeof(double));
-    off_dg = take((size_t)n * sizeof(double));
-    off_ec = take((size_t)n * sizeof(cd));
-    off_eabs = take((size_t)n * sizeof(double));
-    off_delta = take((size_t)n * sizeof(cd));
-    off_p = take((size_t)n * sizeof(cd));
-    off_y = take((size_t)k * n * sizeof(double));
-    off_lu = take((size_t)k * n * 5 * sizeof(double) + (size_t)k * n * sizeof(int));
+    off_vref = take((size_t)n * n * cb);
+    off_tau = take((size_t)n * rb);
+    off_dg = take((size_t)n * rb);
+    off_ec = take((size_t)n * cb);
+    off_eabs = take((size_t)n * rb);
+    off_delta = take((size_t)n * cb);
+    off_p = take((size_t)n * cb);
+    off_y = take((size_t)k * n * rb);
+    off_lu = take((size_t)k * n * 5 * rb + (size_t)k * n * sizeof(int));
     total = o;
   }
 };
 
 // ---- 1. Householder reduction, one column j (trailing size m = n - j - 1 >= 2)
-__global__ void hh_vector(cd *A, int n, int j, cd *vref, double *tau, double *dg, cd *ec) {
-  __shared__ double sh[33];
+template <class R>
+__global__ void hh_vector(cplx<R> *A, int n, int j, cplx<R> *vref, R *tau, R *dg, cplx<R> *ec) {
+  typedef cplx<R> cd;
+  __shared__ R sh[33];
   const int m = n - j - 1;
-  double s = 0.0;
+  R s = 0;
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += cabs2(A[(long long)(j + 1 + i) * n + j]);
-  const double sigma = block_sum_all(s, sh);
+  const R sigma = block_sum_all<R>(s, sh);
   const cd alpha = A[(long long)(j + 1) * n + j];
   cd *v = vref + (long long)j * n + j + 1;
-  if (sigma == 0.0) {
+  if (sigma == R(0)) {
     if (threadIdx.x == 0) {
-      tau[j] = 0.0;
+      tau[j] = 0;
       ec[j] = alpha;
       dg[j] = A[(long long)j * n + j].x;
     }
     return;
   }
-  const double aa = sqrt(cabs2(alpha));
-  const double nx = sqrt(aa * aa + sigma);
-  const cd ph = aa > 0.0 ? mkc(alpha.x / aa, alpha.y / aa) : mkc(1.0, 0.0);
+  const R aa = sqrt(cabs2(alpha));
+  const R nx = sqrt(aa * aa + sigma);
+  const cd ph = aa > R(0) ? mkc<R>(alpha.x / aa, alpha.y / aa) : mkc<R>(1, 0);
   for (int i = threadIdx.x; i < m; i += blockDim.x)
     v[i] = (i == 0) ? cscale(ph, aa + nx) : A[(long long)(j + 1 + i) * n + j];
   if (threadIdx.x == 0) {
-    tau[j] = 1.0 / (nx * (nx + aa));
+    tau[j] = R(1) / (nx * (nx + aa));
     ec[j] = cscale(ph, -nx);
     dg[j] = A[(long long)j * n + j].x;
   }
 }
 
 // p = tau A22 v (one warp per row of the trailing block)
-__global__ void hh_symv(const cd *A, int n, int j, const cd *vref, const double *tau, cd *p) {
-  const double t = tau[j];
+template <class R>
+__global__ void hh_symv(const cplx<R> *A, int n, int j, const cplx<R> *vref, const R *tau, cplx<R> *p) {
+  typedef cplx<R> cd;
+  const R t = tau[j];
   const int m = n - j - 1;
   const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (r >= m || t == 0.0) return;
+  if (r >= m || t == R(0)) return;
   const cd *row = A + (long long)(j + 1 + r) * n + j + 1;
   const cd *v = vref + (long long)j * n + j + 1;
-  double sx = 0.0, sy = 0.0;
+  R sx = 0, sy = 0;
   for (int c = lane; c < m; c += 32) {
     cd a = row[c], b = v[c];
     sx = fma(a.x, b.x, fma(-a.y, b.y, sx));
     sy = fma(a.x, b.y, fma(a.y, b.x, sy));
   }
-  sx = warp_sum(sx);
-  sy = warp_sum(sy);
-  if (lane == 0) p[r] = mkc(t * sx, t * sy);
+  sx = warp_sum<R>(sx);
+  sy = warp_sum<R>(sy);
+  if (lane == 0) p[r] = mkc<R>(t * sx, t * sy);
 }
 
 // w = p - (tau/2) (v^+ p) v, in place in p
-__global__ void hh_wvec(int n, int j, const cd *vref, const double *tau, cd *p) {
-  __shared__ double sh[33];
-  const double t = tau[j];
-  if (t == 0.0) return;
+template <class R>
+__global__ void hh_wvec(int n, int j, const cplx<R> *vref, const R *tau, cplx<R> *p) {
+  typedef cplx<R> cd;
+  __shared__ R sh[33];
+  const R t = tau[j];
+  if (t == R(0)) return;
   const int m = n - j - 1;
   const cd *v = vref + (long long)j * n + j + 1;
-  double s = 0.0;
+  R s = 0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     cd a = v[c], b = p[c];
     s += a.x * b.x + a.y * b.y;  // Re(conj(v) p)
   }
-  const double K = 0.5 * t * block_sum_all(s, sh);
+  const R K = R(0.5) * t * block_sum_all<R>(s, sh);
   for (int c = threadIdx.x; c < m; c += blockDim.x) p[c] = csub(p[c], cscale(v[c], K));
 }
 
 // A22 -= v w^+ + w v^+
-__global__ void hh_rank2(cd *A, int n, int j, const cd *vref, const double *tau, const cd *w) {
-  if (tau[j] == 0.0) return;
+template <class R>
+__global__ void hh_rank2(cplx<R> *A, int n, int j, const cplx<R> *vref, const R *tau, const cplx<R> *w) {
+  typedef cplx<R> cd;
+  if (tau[j] == R(0)) return;
   const int m = n - j - 1;
   const int r = blockIdx.y;
   const cd *v = vref + (long long)j * n + j + 1;
@@ -147,67 +170,70 @@ __global__ void hh_rank2(cd *A, int n, int j, const cd *vref, const double *tau,
 }
 
 // ---- 2. last diagonal / off-diagonal entries, |e| and the phases of D
-__global__ void tri_finish(const cd *A, int n, double *tau, double *dg, cd *ec, double *eabs,
-                           cd *delta) {
+template <class R>
+__global__ void tri_finish(const cplx<R> *A, int n, R *tau, R *dg, cplx<R> *ec, R *eabs,
+                           cplx<R> *delta) {
   if (threadIdx.x != 0) return;
   if (n >= 2) {
     dg[n - 2] = A[(long long)(n - 2) * n + n - 2].x;
     ec[n - 2] = A[(long long)(n - 1) * n + n - 2];
-    tau[n - 2] = 0.0;
+    tau[n - 2] = 0;
   }
   dg[n - 1] = A[(long long)(n - 1) * n + n - 1].x;
-  tau[n - 1] = 0.0;
-  delta[0] = mkc(1.0, 0.0);
+  tau[n - 1] = 0;
+  delta[0] = mkc<R>(1, 0);
   for (int j = 0; j + 1 < n; ++j) {
-    double a = sqrt(cabs2(ec[j]));
+    R a = sqrt(cabs2(ec[j]));
     eabs[j] = a;
-    delta[j + 1] = a > 0.0 ? cmul(delta[j], mkc(ec[j].x / a, ec[j].y / a)) : delta[j];
+    delta[j + 1] = a > R(0) ? cmul(delta[j], mkc<R>(ec[j].x / a, ec[j].y / a)) : delta[j];
   }
-  eabs[n - 1] = 0.0;
+  eabs[n - 1] = 0;
 }
 
 // ---- 3. bisection: evals[t] = (t)-th largest eigenvalue of T'
-__device__ int sturm_count(const double *dg, const double *e, int n, double x, double pivmin) {
+template <class R>
+__device__ int sturm_count(const R *dg, const R *e, int n, R x, R pivmin) {
   // number of eigenvalues < x
   int cnt = 0;
-  double q = dg[0] - x;
+  R q = dg[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0.0) ++cnt;
+  if (q < R(0)) ++cnt;
   for (int i = 1; i < n; ++i) {
     q = dg[i] - x - e[i - 1] * e[i - 1] / q;
     if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++cnt;
+    if (q < R(0)) ++cnt;
   }
   return cnt;
 }
 
-__global__ void bisect_kernel(const double *dg, const double *e, int n, int k_want,
-                              double *evals) {
+template <class R>
+__global__ void bisect_kernel(const R *dg, const R *e, int n, int k_want, R *evals) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k_want) return;
-  double lo = 1e300, hi = -1e300, emax = 0.0;
+  const R eps = Eps<R>::eps, tiny = Eps<R>::tiny;
+  R lo = Eps<R>::huge, hi = -Eps<R>::huge, emax = 0;
   for (int i = 0; i < n; ++i) {
-    double r = (i > 0 ? e[i - 1] : 0.0) + (i + 1 < n ? e[i] : 0.0);
+    R r = (i > 0 ? e[i - 1] : R(0)) + (i + 1 < n ? e[i] : R(0));
     lo = fmin(lo, dg[i] - r);
     hi = fmax(hi, dg[i] + r);
     emax = fmax(emax, fabs(dg[i]) + r);
   }
-  const double tnorm = fmax(emax, 1e-300);
-  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, tnorm * tnorm);
-  lo -= 2.0 * 2.220446049250313e-16 * tnorm * n + 1e-300;
-  hi += 2.0 * 2.220446049250313e-16 * tnorm * n + 1e-300;
+  const R tnorm = fmax(emax, tiny);
+  const R pivmin = tiny * fmax(R(1), tnorm * tnorm);
+  lo -= R(2) * eps * tnorm * n + tiny;
+  hi += R(2) * eps * tnorm * n + tiny;
   const int target = n - 1 - t;  // ascending index
   for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
+    R mid = R(0.5) * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (hi - lo <= 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + 1e-18 * tnorm) break;
-    int c = sturm_count(dg, e, n, mid, pivmin);
+    if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + R(1e-18) * tnorm) break;
+    int c = sturm_count<R>(dg, e, n, mid, pivmin);
     if (c > target)
       hi = mid;
     else
       lo = mid;
   }
-  evals[t] = 0.5 * (lo + hi);
+  evals[t] = R(0.5) * (lo + hi);
 }
 
 // ---- 4. inverse iteration, one thread per vector
@@ -219,19 +245,20 @@ __device__ __forceinline__ double hash_unit(int t, int i) {
   return (double)(h & 0xFFFFFF) / (double)0x1000000 * 2.0 - 1.0;
 }
 
-__global__ void invit_round(const double *dg, const double *e, int n, int k_vec,
-                            const double *evals, double *Y, double *lu, int *piv, int round) {
+template <class R>
+__global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *evals, R *Y, R *lu,
+                            int *piv, int round) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k_vec) return;
-  double *y = Y + (long long)t * n;
-  double *dl = lu + (long long)t * n * 4;
-  double *dd = dl + n, *du = dd + n, *du2 = du + n;
+  R *y = Y + (long long)t * n;
+  R *dl = lu + (long long)t * n * 4;
+  R *dd = dl + n, *du = dd + n, *du2 = du + n;
   int *pv = piv + (long long)t * n;
-  double tnorm = 0.0;
+  R tnorm = 0;
   for (int i = 0; i < n; ++i)
-    tnorm = fmax(tnorm, fabs(dg[i]) + (i > 0 ? e[i - 1] : 0.0) + (i + 1 < n ? e[i] : 0.0));
-  const double pivmin = fmax(tnorm * 2.220446049250313e-16, 1e-300);
-  const double lam = evals[t];
+    tnorm = fmax(tnorm, fabs(dg[i]) + (i > 0 ? e[i - 1] : R(0)) + (i + 1 < n ? e[i] : R(0)));
+  const R pivmin = fmax(tnorm * Eps<R>::eps, Eps<R>::tiny);
+  const R lam = evals[t];
   if (round == 0) {
     // factor T' - lam I = P L U once
     for (int i = 0; i < n; ++i) {
@@ -240,21 +267,21 @@ __global__ void invit_round(const double *dg, const double *e, int n, int k_vec,
         dl[i] = e[i];
         du[i] = e[i];
       }
-      du2[i] = 0.0;
+      du2[i] = 0;
       pv[i] = 0;
     }
     for (int i = 0; i + 1 < n; ++i) {
       if (fabs(dd[i]) >= fabs(dl[i])) {
-        if (dd[i] == 0.0) dd[i] = pivmin;
-        double l = dl[i] / dd[i];
+        if (dd[i] == R(0)) dd[i] = pivmin;
+        R l = dl[i] / dd[i];
         dl[i] = l;
         dd[i + 1] -= l * du[i];
         pv[i] = 0;
       } else {
-        double l = dd[i] / dl[i];
+        R l = dd[i] / dl[i];
         dd[i] = dl[i];
         dl[i] = l;
-        double tmp = du[i];
+        R tmp = du[i];
         du[i] = dd[i + 1];
         dd[i + 1] = tmp - l * dd[i + 1];
         if (i + 2 < n) {
@@ -264,13 +291,13 @@ __global__ void invit_round(const double *dg, const double *e, int n, int k_vec,
         pv[i] = 1;
       }
     }
-    if (dd[n - 1] == 0.0) dd[n - 1] = pivmin;
-    for (int i = 0; i < n; ++i) y[i] = hash_unit(t, i);
+    if (dd[n - 1] == R(0)) dd[n - 1] = pivmin;
+    for (int i = 0; i < n; ++i) y[i] = R(hash_unit(t, i));
   }
   // solve (T' - lam I) y_new = y
   for (int i = 0; i + 1 < n; ++i) {
     if (pv[i]) {
-      double tmp = y[i];
+      R tmp = y[i];
       y[i] = y[i + 1];
       y[i + 1] = tmp;
     }
@@ -279,81 +306,84 @@ __global__ void invit_round(const double *dg, const double *e, int n, int k_vec,
   // back substitution; the system is linear, so the whole vector may be
   // rescaled whenever a component grows large (near-singular shifts)
   for (int i = n - 1; i >= 0; --i) {
-    double v = y[i];
+    R v = y[i];
     if (i + 1 < n) v -= du[i] * y[i + 1];
     if (i + 2 < n) v -= du2[i] * y[i + 2];
     v /= dd[i];
     y[i] = v;
-    if (fabs(v) > 1e150)
-      for (int q = 0; q < n; ++q) y[q] *= 1e-150;
+    if (fabs(v) > Eps<R>::big)
+      for (int q = 0; q < n; ++q) y[q] *= R(1) / Eps<R>::big;
   }
   // normalise (guard against overflow by scaling with the max first)
-  double mx = 0.0;
+  R mx = 0;
   for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(y[i]));
-  if (mx == 0.0) mx = 1.0;
-  double s = 0.0;
+  if (mx == R(0)) mx = 1;
+  R s = 0;
   for (int i = 0; i < n; ++i) {
     y[i] /= mx;
     s += y[i] * y[i];
   }
-  s = 1.0 / sqrt(s);
+  s = R(1) / sqrt(s);
   for (int i = 0; i < n; ++i) y[i] *= s;
 }
 
 // in-order two-pass Gram-Schmidt of the rows of Y (descending eigenvalues)
-__global__ void cgs2_rows(double *Y, int n, int k) {
-  __shared__ double sh[33];
-  __shared__ double coef[128];
+template <class R>
+__global__ void cgs2_rows(R *Y, int n, int k) {
+  __shared__ R sh[33];
+  __shared__ R coef[128];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int t = 0; t < k; ++t) {
-    double *yt = Y + (long long)t * n;
+    R *yt = Y + (long long)t * n;
     for (int pass = 0; pass < 2; ++pass) {
       for (int s = wid; s < t; s += nw) {
-        const double *ys = Y + (long long)s * n;
-        double d = 0.0;
+        const R *ys = Y + (long long)s * n;
+        R d = 0;
         for (int i = lane; i < n; i += 32) d += ys[i] * yt[i];
-        d = warp_sum(d);
+        d = warp_sum<R>(d);
         if (lane == 0) coef[s] = d;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double v = yt[i];
+        R v = yt[i];
         for (int s = 0; s < t; ++s) v -= coef[s] * Y[(long long)s * n + i];
         yt[i] = v;
       }
       __syncthreads();
     }
-    double ss = 0.0;
+    R ss = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) ss += yt[i] * yt[i];
-    ss = block_sum_all(ss, sh);
-    const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+    ss = block_sum_all<R>(ss, sh);
+    const R inv = ss > R(0) ? R(1) / sqrt(ss) : R(0);
     for (int i = threadIdx.x; i < n; i += blockDim.x) yt[i] *= inv;
     __syncthreads();
   }
 }
 
 // ---- 5. z_t = Q D y_t, one block per vector
-__global__ void backtransform(const cd *vref, const double *tau, const cd *delta, const double *Y,
-                              int n, cd *Z) {
-  __shared__ double sh[33];
+template <class R>
+__global__ void backtransform(const cplx<R> *vref, const R *tau, const cplx<R> *delta, const R *Y, int n,
+                              cplx<R> *Z) {
+  typedef cplx<R> cd;
+  __shared__ R sh[33];
   const int t = blockIdx.x;
-  const double *y = Y + (long long)t * n;
+  const R *y = Y + (long long)t * n;
   cd *z = Z + (long long)t * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = cscale(delta[i], y[i]);
   __syncthreads();
   for (int j = n - 3; j >= 0; --j) {
-    const double tj = tau[j];
-    if (tj == 0.0) continue;
+    const R tj = tau[j];
+    if (tj == R(0)) continue;
     const cd *v = vref + (long long)j * n;
-    double sx = 0.0, sy = 0.0;
+    R sx = 0, sy = 0;
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
       cd a = v[i], b = z[i];
       sx += a.x * b.x + a.y * b.y;
       sy += a.x * b.y - a.y * b.x;
     }
-    sx = block_sum_all(sx, sh);
-    sy = block_sum_all(sy, sh);
-    const cd f = mkc(tj * sx, tj * sy);
+    sx = block_sum_all<R>(sx, sh);
+    sy = block_sum_all<R>(sy, sh);
+    const cd f = mkc<R>(tj * sx, tj * sy);
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) z[i] = csub(z[i], cmul(v[i], f));
     __syncthreads();
   }
@@ -361,63 +391,72 @@ __global__ void backtransform(const cd *vref, const double *tau, const cd *delta
 
 }  // namespace
 
-size_t EigWork::bytes(int n, int k_want) { return EigLayout(n, k_want).total; }
+size_t EigWork::bytes(int n, int k_want, int real_bytes) { return EigLayout(n, k_want, real_bytes).total; }
 
-vb_status eig_values(int n, cd *rho, int k_want, double *evals, void *work, cudaStream_t st) {
+template <class R>
+vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cudaStream_t st) {
+  typedef cplx<R> C_;
   if (n < 1 || k_want < 1 || k_want > n) return fail(VB_EINVAL, "eig_values: bad n / k_want");
-  EigLayout lay(n, k_want);
+  EigLayout lay(n, k_want, sizeof(R));
   char *w = static_cast<char *>(work);
-  cd *vref = reinterpret_cast<cd *>(w + lay.off_vref);
-  double *tau = reinterpret_cast<double *>(w + lay.off_tau);
-  double *dg = reinterpret_cast<double *>(w + lay.off_dg);
-  cd *ec = reinterpret_cast<cd *>(w + lay.off_ec);
-  double *eabs = reinterpret_cast<double *>(w + lay.off_eabs);
-  cd *delta = reinterpret_cast<cd *>(w + lay.off_delta);
-  cd *p = reinterpret_cast<cd *>(w + lay.off_p);
+  C_ *vref = reinterpret_cast<C_ *>(w + lay.off_vref);
+  R *tau = reinterpret_cast<R *>(w + lay.off_tau);
+  R *dg = reinterpret_cast<R *>(w + lay.off_dg);
+  C_ *ec = reinterpret_cast<C_ *>(w + lay.off_ec);
+  R *eabs = reinterpret_cast<R *>(w + lay.off_eabs);
+  C_ *delta = reinterpret_cast<C_ *>(w + lay.off_delta);
+  C_ *p = reinterpret_cast<C_ *>(w + lay.off_p);
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
-    hh_vector<<<1, 256, 0, st>>>(rho, n, j, vref, tau, dg, ec);
+    hh_vector<R><<<1, 256, 0, st>>>(rho, n, j, vref, tau, dg, ec);
     VB_CHECK_LAUNCH();
-    hh_symv<<<(m + 7) / 8, 256, 0, st>>>(rho, n, j, vref, tau, p);
+    hh_symv<R><<<(m + 7) / 8, 256, 0, st>>>(rho, n, j, vref, tau, p);
     VB_CHECK_LAUNCH();
-    hh_wvec<<<1, 256, 0, st>>>(n, j, vref, tau, p);
+    hh_wvec<R><<<1, 256, 0, st>>>(n, j, vref, tau, p);
     VB_CHECK_LAUNCH();
     dim3 g2((m + 255) / 256, m);
-    hh_rank2<<<g2, 256, 0, st>>>(rho, n, j, vref, tau, p);
+    hh_rank2<R><<<g2, 256, 0, st>>>(rho, n, j, vref, tau, p);
     VB_CHECK_LAUNCH();
   }
-  tri_finish<<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
+  tri_finish<R><<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
   VB_CHECK_LAUNCH();
-  bisect_kernel<<<(k_want + 63) / 64, 64, 0, st>>>(dg, eabs, n, k_want, evals);
+  bisect_kernel<R><<<(k_want + 63) / 64, 64, 0, st>>>(dg, eabs, n, k_want, evals);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
 
-vb_status eig_vectors(int n, const cd *rho, int k_want, int k_vec, const double *evals, cd *evecs,
+template <class R>
+vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R *evals, cplx<R> *evecs,
                       void *work, cudaStream_t st) {
+  typedef cplx<R> C_;
   (void)rho;
   if (k_vec < 1 || k_vec > k_want) return fail(VB_EINVAL, "eig_vectors: bad k_vec");
   if (k_vec > 128) return fail(VB_EINVAL, "eig_vectors: at most 128 vectors");
-  EigLayout lay(n, k_want);
+  EigLayout lay(n, k_want, sizeof(R));
   char *w = static_cast<char *>(work);
-  cd *vref = reinterpret_cast<cd *>(w + lay.off_vref);
-  double *tau = reinterpret_cast<double *>(w + lay.off_tau);
-  double *dg = reinterpret_cast<double *>(w + lay.off_dg);
-  double *eabs = reinterpret_cast<double *>(w + lay.off_eabs);
-  cd *delta = reinterpret_cast<cd *>(w + lay.off_delta);
-  double *Y = reinterpret_cast<double *>(w + lay.off_y);
-  double *lu = reinterpret_cast<double *>(w + lay.off_lu);
+  C_ *vref = reinterpret_cast<C_ *>(w + lay.off_vref);
+  R *tau = reinterpret_cast<R *>(w + lay.off_tau);
+  R *dg = reinterpret_cast<R *>(w + lay.off_dg);
+  R *eabs = reinterpret_cast<R *>(w + lay.off_eabs);
+  C_ *delta = reinterpret_cast<C_ *>(w + lay.off_delta);
+  R *Y = reinterpret_cast<R *>(w + lay.off_y);
+  R *lu = reinterpret_cast<R *>(w + lay.off_lu);
   int *piv = reinterpret_cast<int *>(lu + (size_t)k_want * n * 4);
   for (int r = 0; r < INVIT_ROUNDS; ++r) {
-    invit_round<<<(k_vec + 31) / 32, 32, 0, st>>>(dg, eabs, n, k_vec, evals, Y, lu, piv, r);
+    invit_round<R><<<(k_vec + 31) / 32, 32, 0, st>>>(dg, eabs, n, k_vec, evals, Y, lu, piv, r);
     VB_CHECK_LAUNCH();
-    cgs2_rows<<<1, 512, 0, st>>>(Y, n, k_vec);
+    cgs2_rows<R><<<1, 512, 0, st>>>(Y, n, k_vec);
     VB_CHECK_LAUNCH();
   }
-  backtransform<<<k_vec, 256, 0, st>>>(vref, tau, delta, Y, n, evecs);
+  backtransform<R><<<k_vec, 256, 0, st>>>(vref, tau, delta, Y, n, evecs);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
+
+template vb_status eig_values<double>(int, cd *, int, double *, void *, cudaStream_t);
+template vb_status eig_values<float>(int, cf *, int, float *, void *, cudaStream_t);
+template vb_status eig_vectors<double>(int, const cd *, int, int, const double *, cd *, void *, cudaStream_t);
+template vb_status eig_vectors<float>(int, const cf *, int, int, const float *, cf *, void *, cudaStream_t);
 
 }  // namespace vb
 

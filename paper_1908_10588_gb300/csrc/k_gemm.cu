@@ -1,4 +1,5 @@
-// Strided batched complex double GEMM on the CUDA cores (FP64 path).
+// Strided batched complex GEMM on the CUDA cores (complex double on the FP64
+// path; complex float where the mixed path needs a SIMT product).
 //
 // Every dense contraction of the FP64 2TDVP path (the L and R legs of
 // H_eff, the environment updates, the merge of two sites, the reduced
@@ -13,9 +14,10 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
 
-__device__ __forceinline__ cd ldA(const cd *A, int op, long long lda, int i, int k) {
+template <class R>
+__device__ __forceinline__ cplx<R> ldA(const cplx<R> *A, int op, long long lda, int i, int k) {
   // op(A)[i,k]
-  cd v;
+  cplx<R> v;
   if (op == OP_N || op == OP_R)
     v = A[(long long)i * lda + k];
   else
@@ -24,9 +26,10 @@ __device__ __forceinline__ cd ldA(const cd *A, int op, long long lda, int i, int
   return v;
 }
 
-__device__ __forceinline__ cd ldB(const cd *B, int op, long long ldb, int k, int j) {
+template <class R>
+__device__ __forceinline__ cplx<R> ldB(const cplx<R> *B, int op, long long ldb, int k, int j) {
   // op(B)[k,j]
-  cd v;
+  cplx<R> v;
   if (op == OP_N || op == OP_R)
     v = B[(long long)k * ldb + j];
   else
@@ -35,23 +38,25 @@ __device__ __forceinline__ cd ldB(const cd *B, int op, long long ldb, int k, int
   return v;
 }
 
-__global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
-  __shared__ cd As[BK][BM + 1];
-  __shared__ cd Bs[BK][BN + 1];
+template <class R>
+__global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
+  typedef cplx<R> C_;
+  __shared__ C_ As[BK][BM + 1];
+  __shared__ C_ Bs[BK][BN + 1];
   const int b = blockIdx.z;
-  const cd *A = g.A + (long long)b * g.sA;
-  const cd *B = g.B + (long long)b * g.sB;
-  cd *C = g.C + (long long)b * g.sC;
+  const C_ *A = g.A + (long long)b * g.sA;
+  const C_ *B = g.B + (long long)b * g.sB;
+  C_ *C = g.C + (long long)b * g.sC;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const bool a_kfast = (g.opA == OP_N || g.opA == OP_R);
   const bool b_jfast = (g.opB == OP_N || g.opB == OP_R);
-  cd acc[4][4];
+  C_ acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = mkc(0.0, 0.0);
+    for (int c = 0; c < 4; ++c) acc[r][c] = mkc<R>(0, 0);
 
   for (int k0 = 0; k0 < g.K; k0 += BK) {
 #pragma unroll
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
         kk = l / BM;
       }
       int gi = i0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < g.M && gk < g.K) ? ldA(A, g.opA, g.lda, gi, gk) : mkc(0.0, 0.0);
+      As[kk][ii] = (gi < g.M && gk < g.K) ? ldA<R>(A, g.opA, g.lda, gi, gk) : mkc<R>(0, 0);
       int jj;
       if (b_jfast) {
         jj = l % BN;
@@ -77,12 +82,12 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
       }
       int gj = j0 + jj;
       gk = k0 + kk;
-      Bs[kk][jj] = (gj < g.N && gk < g.K) ? ldB(B, g.opB, g.ldb, gk, gj) : mkc(0.0, 0.0);
+      Bs[kk][jj] = (gj < g.N && gk < g.K) ? ldB<R>(B, g.opB, g.ldb, gk, gj) : mkc<R>(0, 0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      cd a[4], bb[4];
+      C_ a[4], bb[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
 #pragma unroll
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
     }
     __syncthreads();
   }
-  const bool beta0 = (g.beta.x == 0.0 && g.beta.y == 0.0);
+  const bool beta0 = (g.beta.x == R(0) && g.beta.y == R(0));
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     int gi = i0 + ty + 16 * r;
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
     for (int c = 0; c < 4; ++c) {
       int gj = j0 + tx + 16 * c;
       if (gj >= g.N) continue;
-      cd v = cmul(g.alpha, acc[r][c]);
+      C_ v = cmul(g.alpha, acc[r][c]);
       long long o = (long long)gi * g.ldc + gj;
       if (!beta0) v = cadd(v, cmul(g.beta, C[o]));
       C[o] = v;
@@ -118,7 +123,8 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgs g) {
 
 }  // namespace
 
-vb_status zgemm(const GemmArgs &g, cudaStream_t st) {
+template <class R>
+vb_status gemm(const GemmArgsT<R> &g, cudaStream_t st) {
   if (g.M < 0 || g.N < 0 || g.K < 0 || g.batch < 0)
     return fail(VB_EINVAL, "zgemm: negative size");
   if (g.M == 0 || g.N == 0 || g.batch == 0) return VB_OK;
@@ -138,9 +144,12 @@ vb_status zgemm(const GemmArgs &g, cudaStream_t st) {
       return fail(VB_EINVAL, "zgemm: buffer sizes must be given");
   }
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
-  zgemm_kernel<<<grid, NT, 0, st>>>(g);
+  zgemm_kernel<R><<<grid, NT, 0, st>>>(g);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
+
+template vb_status gemm<double>(const GemmArgsT<double> &, cudaStream_t);
+template vb_status gemm<float>(const GemmArgsT<float> &, cudaStream_t);
 
 }  // namespace vb

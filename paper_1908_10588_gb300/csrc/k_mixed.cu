@@ -1,19 +1,281 @@
-// Mixed-precision H_eff products (split-TF32 tensor-core path).
+// Mixed-precision H_eff products (the mixed form of the 2TDVP path).
+//
+// The Krylov vectors, environments and every step other than the H_eff
+// products stay in complex double. One product y = H_eff x (Eq. two-site
+// Hamiltonian, or Eq. one-site Hamiltonian 1) runs its two dense legs on the
+// tensor cores (tcgen05 kind::tf32 in three split-TF32 products, FP32
+// accumulation, k_tc.cu) and its
+// sparse MPO legs in FP32 on the CUDA cores:
+//
+//   L leg   T1 = L x        real embedding: [[Re L, -Im L], [Im L, Re L]] (2M x 2K)
+//                           times [Re x; Im x] (stored transposed, K-major),
+//                           output planar (real rows, then imaginary rows)
+//   W legs  T2, T3          planar FP32, sum over the nonzero MPO blocks
+//   R leg   y = T3 R^T      A = [Re T3 | Im T3] per row (K-major), B rows
+//                           [Re R, -Im R] and [Im R, Re R]; the epilogue
+//                           writes y directly as complex double
+//
+// K dimensions are zero-padded to multiples of 32 (one 128-byte swizzle
+// atom of fp32). The conversion kernels write every padding element.
+#include <algorithm>
+
 #include "common.h"
 
 namespace vb {
 
+vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long ldb, int M, int N, int K,
+                       int mode, float *D, long long ldd, double *Y, int nh, int *err, cudaStream_t st,
+                       bool split);
+
+namespace {
+
+inline long long pad32(long long k) { return (k + 31) / 32 * 32; }
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (int)std::max(1LL, b);
+}
+
+// AL[i][k]: rows i < M: [Re L[i,:], -Im L[i,:], 0...]; rows M + i: [Im L, Re L, 0...]
+__global__ void prep_left_env(const cd *__restrict__ L, long long M, int K, long long ld, float *__restrict__ AL) {
+  const long long total = 2 * M * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / ld;
+    const int col = (int)(e % ld);
+    float v = 0.f;
+    if (col < 2 * K) {
+      const bool imrow = row >= M;
+      const long long i = imrow ? row - M : row;
+      const int a = col < K ? col : col - K;
+      const cd z = L[i * K + a];
+      if (!imrow)
+        v = col < K ? (float)z.x : (float)(-z.y);
+      else
+        v = col < K ? (float)z.y : (float)z.x;
+    }
+    AL[e] = v;
+  }
+}
+
+// BR[n][k]: rows n < N: [Re R[n,:], -Im R[n,:], 0...]; rows N + n: [Im R, Re R, 0...]
+__global__ void prep_right_env(const cd *__restrict__ R, int N, long long K, long long ld, float *__restrict__ BR) {
+  const long long total = 2LL * N * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / ld;
+    const long long col = e % ld;
+    float v = 0.f;
+    if (col < 2 * K) {
+      const bool imrow = row >= N;
+      const long long n = imrow ? row - N : row;
+      const long long k = col < K ? col : col - K;
+      const cd z = R[n * K + k];
+      if (!imrow)
+        v = col < K ? (float)z.x : (float)(-z.y);
+      else
+        v = col < K ? (float)z.y : (float)z.x;
+    }
+    BR[e] = v;
+  }
+}
+
+// BX[n][k] = [Re x[k][n] (k < K), Im x[k-K][n] (K <= k < 2K), 0...]: a tiled
+// transpose of x (K x Ncols complex double) into K-major fp32 rows
+__global__ void prep_vector_T(const cd *__restrict__ x, int K, long long Ncols, long long ld, float *__restrict__ BX) {
+  __shared__ float tr[32][33], ti[32][33];
+  const long long n0 = (long long)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r;
+    const long long n = n0 + tx;
+    cd z = mkc(0.0, 0.0);
+    if (k < K && n < Ncols) z = x[(long long)k * Ncols + n];
+    tr[r][tx] = (float)z.x;
+    ti[r][tx] = (float)z.y;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const long long n = n0 + r;
+    const int k = k0 + tx;
+    if (n < Ncols && k < K) {
+      BX[n * ld + k] = tr[tx][r];
+      BX[n * ld + K + k] = ti[tx][r];
+    }
+  }
+}
+
+// zero the K padding columns [from, ld) of BX rows
+__global__ void zero_cols(float *__restrict__ X, long long rows, long long ld, long long from) {
+  const long long w = ld - from;
+  const long long total = rows * w;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    X[(e / w) * ld + from + e % w] = 0.f;
+}
+
+// planar sparse MPO leg: like wapply (k_wapply.cu), with the real and the
+// imaginary parts in separate planes of X and Y
+__global__ void wapply_planar_kernel(const float *__restrict__ ops, const int *__restrict__ ptr,
+                                     const int *__restrict__ ent, int d, int Wp, const float *__restrict__ X,
+                                     long long xplane, WStrides xs, float *__restrict__ Y, long long yplane,
+                                     WStrides ys, int P, int Q) {
+  const long long total = (long long)P * d * Wp * Q;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % Q);
+    long long r = idx / Q;
+    const int wo = (int)(r % Wp);
+    r /= Wp;
+    const int so = (int)(r % d);
+    const int p = (int)(r / d);
+    float ax = 0.f, ay = 0.f;
+    const float *xb = X + p * xs.p + q * xs.q;
+    for (int e = ptr[wo]; e < ptr[wo + 1]; ++e) {
+      const int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
+      const float *xw = xb + wi * xs.w;
+      if (ident) {
+        ax += xw[so * xs.s];
+        ay += xw[so * xs.s + xplane];
+      } else {
+        const float *o = ops + off + so * d;
+        for (int s = 0; s < d; ++s) {
+          const float c = o[s];
+          if (c != 0.f) {
+            ax = fmaf(c, xw[s * xs.s], ax);
+            ay = fmaf(c, xw[s * xs.s + xplane], ay);
+          }
+        }
+      }
+    }
+    const long long o = p * ys.p + so * ys.s + wo * ys.w + q * ys.q;
+    Y[o] = ax;
+    Y[o + yplane] = ay;
+  }
+}
+
+vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStrides xs, long long x_size,
+                        float *Y, long long yplane, WStrides ys, long long y_size, int P, int Q, cudaStream_t st) {
+  const int d = S.d, Wp = S.wr, Wc = S.wl;
+  const long long total = (long long)P * d * Wp * Q;
+  if (total == 0) return VB_OK;
+  const long long xmax = (P - 1) * xs.p + (Wc - 1) * xs.w + (d - 1) * xs.s + (Q - 1) * xs.q + xplane;
+  const long long ymax = (P - 1) * ys.p + (Wp - 1) * ys.w + (d - 1) * ys.s + (Q - 1) * ys.q + yplane;
+  if (xmax >= x_size || ymax >= y_size) return fail(VB_EINVAL, "wapply_planar: view exceeds its buffer");
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  wapply_planar_kernel<<<(int)blocks, 256, 0, st>>>(S.d_ops32, S.d_fwd_ptr, S.d_fwd_ent, d, Wp, X, xplane, xs, Y,
+                                                    yplane, ys, P, Q);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+struct TcLayout {
+  long long ML, KL, ldL, NL;  // L leg: (2 ML) x ldL times NL x ldL
+  long long MR, KR, ld3;      // R leg: MR x ld3 times (2 mR) x ld3
+  long long nT1, nT2;
+  size_t oAL, oBX, oT1, oT2, oT3, oBR, oErr, total;
+  TcLayout(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
+    const MpoSite &S = mpo->sites[site];
+    const MpoSite &S2 = two_site ? mpo->sites[site + 1] : S;
+    const long long d1 = S.d, d2 = two_site ? S2.d : 1;
+    const long long wL = S.wl, wM = S.wr, wR = two_site ? S2.wr : S.wr;
+    ML = (long long)mL * wL;
+    KL = mL;
+    ldL = pad32(2 * KL);
+    NL = d1 * d2 * mR;
+    MR = (long long)mL * d1 * d2;
+    KR = wR * mR;
+    ld3 = pad32(2 * KR);
+    nT1 = 2 * ML * NL;
+    nT2 = two_site ? 2LL * mL * d1 * wM * d2 * mR : 0;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      size_t r = o;
+      o += (bytes + 255) / 256 * 256;
+      return r;
+    };
+    oAL = take((size_t)2 * ML * ldL * 4);
+    oBX = take((size_t)NL * ldL * 4);
+    oT1 = take((size_t)nT1 * 4);
+    oT2 = take((size_t)std::max<long long>(nT2, 1) * 4);
+    oT3 = take((size_t)MR * ld3 * 4);
+    oBR = take((size_t)2 * mR * ld3 * 4);
+    oErr = take(256);
+    total = o;
+  }
+};
+
+}  // namespace
+
 size_t heff_mixed_work_bytes(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
-  (void)mpo; (void)site; (void)two_site; (void)mL; (void)mR;
-  return 0;
+  if (!mpo || site < 0 || site >= mpo->n || (two_site && site + 1 >= mpo->n) || mL < 1 || mR < 1) return 0;
+  return TcLayout(mpo, site, two_site, mL, mR).total;
+}
+
+// device address of the tensor-core error flag inside a mixed workspace
+int *heff_mixed_err_flag(const vb_mpo *mpo, int site, int two_site, int mL, int mR, void *work) {
+  TcLayout lay(mpo, site, two_site, mL, mR);
+  return reinterpret_cast<int *>(static_cast<char *>(work) + lay.oErr);
 }
 
 vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
-                           const cd *R, const cd *x, cd *y, void *work, size_t work_bytes,
+                           const cd *R, const cd *x, cd *y, void *work, size_t work_bytes, int *err,
                            cudaStream_t st) {
-  (void)mpo; (void)site; (void)two_site; (void)mL; (void)mR; (void)L; (void)R; (void)x; (void)y;
-  (void)work; (void)work_bytes; (void)st;
-  return fail(VB_EINVAL, "mixed-precision path not available in this build");
+  TcLayout lay(mpo, site, two_site, mL, mR);
+  if (work_bytes < lay.total) return fail(VB_EINVAL, "heff_mixed_apply: workspace too small");
+  char *w = static_cast<char *>(work);
+  float *AL = reinterpret_cast<float *>(w + lay.oAL);
+  float *BX = reinterpret_cast<float *>(w + lay.oBX);
+  float *T1 = reinterpret_cast<float *>(w + lay.oT1);
+  float *T2 = reinterpret_cast<float *>(w + lay.oT2);
+  float *T3 = reinterpret_cast<float *>(w + lay.oT3);
+  float *BR = reinterpret_cast<float *>(w + lay.oBR);
+  const MpoSite &S = mpo->sites[site];
+  // operands of the L leg
+  prep_left_env<<<grid_for(2 * lay.ML * lay.ldL), 256, 0, st>>>(L, lay.ML, (int)lay.KL, lay.ldL, AL);
+  VB_CHECK_LAUNCH();
+  {
+    dim3 g((unsigned)((lay.NL + 31) / 32), (unsigned)((lay.KL + 31) / 32));
+    prep_vector_T<<<g, 256, 0, st>>>(x, (int)lay.KL, lay.NL, lay.ldL, BX);
+    VB_CHECK_LAUNCH();
+    if (lay.ldL > 2 * lay.KL) {
+      zero_cols<<<grid_for(lay.NL * (lay.ldL - 2 * lay.KL)), 256, 0, st>>>(BX, lay.NL, lay.ldL, 2 * lay.KL);
+      VB_CHECK_LAUNCH();
+    }
+  }
+  prep_right_env<<<grid_for(2LL * mR * lay.ld3), 256, 0, st>>>(R, mR, lay.KR, lay.ld3, BR);
+  VB_CHECK_LAUNCH();
+  // L leg: T1 planar (2 ML) x NL
+  VB_TRY(tc_gemm_tf32(AL, lay.ldL, BX, lay.ldL, (int)(2 * lay.ML), (int)lay.NL, (int)lay.ldL, 0, T1, lay.NL,
+                      nullptr, 0, err, st, true));
+  const long long P1 = lay.ML * lay.NL;  // plane offset of T1
+  if (two_site) {
+    const MpoSite &S2 = mpo->sites[site + 1];
+    const long long d1 = S.d, d2 = S2.d, wL = S.wl, wM = S.wr, Q1 = d2 * mR;
+    const long long P2 = lay.nT2 / 2;
+    // T2[a'][s'][w1][(t b)] planar
+    VB_TRY(wapply_planar(S, T1, P1, WS(/*p*/ wL * d1 * Q1, /*w*/ d1 * Q1, /*s*/ Q1, /*q*/ 1), lay.nT1, T2, P2,
+                         WS(/*p*/ d1 * wM * Q1, /*w*/ Q1, /*s*/ wM * Q1, /*q*/ 1), lay.nT2, mL, (int)Q1, st));
+    // T3 row (a' s' t'): [Re (w2 b) | Im (w2 b) | 0]
+    VB_TRY(wapply_planar(S2, T2, P2, WS(/*p*/ wM * d2 * mR, /*w*/ d2 * mR, /*s*/ mR, /*q*/ 1), lay.nT2, T3,
+                         lay.KR, WS(/*p*/ d2 * lay.ld3, /*w*/ mR, /*s*/ lay.ld3, /*q*/ 1), lay.MR * lay.ld3,
+                         (int)(mL * d1), mR, st));
+  } else {
+    const long long d = S.d, wL = S.wl;
+    VB_TRY(wapply_planar(S, T1, P1, WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), lay.nT1, T3, lay.KR,
+                         WS(/*p*/ d * lay.ld3, /*w*/ mR, /*s*/ lay.ld3, /*q*/ 1), lay.MR * lay.ld3, mL, mR, st));
+  }
+  if (lay.ld3 > 2 * lay.KR) {
+    zero_cols<<<grid_for(lay.MR * (lay.ld3 - 2 * lay.KR)), 256, 0, st>>>(T3, lay.MR, lay.ld3, 2 * lay.KR);
+    VB_CHECK_LAUNCH();
+  }
+  // R leg: y (complex double) = T3 BR^T
+  VB_TRY(tc_gemm_tf32(T3, lay.ld3, BR, lay.ld3, (int)lay.MR, 2 * mR, (int)lay.ld3, 1, nullptr, 0,
+                      reinterpret_cast<double *>(y), mR, err, st, true));
+  return VB_OK;
 }
 
 }  // namespace vb

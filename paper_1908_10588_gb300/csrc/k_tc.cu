@@ -1,0 +1,381 @@
+// Real TF32 GEMM on the fifth-generation tensor cores (tcgen05) for the
+// dense legs of the mixed-precision H_eff products.
+//
+//   D[m, n] = sum_k A[m, k] * B[n, k]      (A: M x K, B: N x K, both K-major fp32)
+//
+// One CTA computes a 128 x 128 tile of D. Operands are staged by TMA into
+// 128-byte-swizzled shared memory (boxes of 32 K-elements x 128 rows) in a
+// STAGES-deep ring guarded by mbarriers; one elected thread issues
+// tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8 per instruction) into a
+// TMEM accumulator of 128 lanes x 128 columns; four epilogue warps read the
+// accumulator with tcgen05.ld and store it. Complex products use the real
+// embedding prepared by the caller (k_mixed.cu).
+//
+// Split-TF32 (SPLIT = true): while the main loop runs, the four epilogue
+// warps split every landed stage x = hi + lo with hi = x truncated to tf32
+// (written back in place, so it is exact in tf32) and lo = x - hi (exact in
+// fp32) into a second buffer; the MMA thread then issues three products per
+// k-step, A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated in FP32. The lo*lo
+// term and the tf32 rounding of lo leave a relative error of about 2^-21.
+//
+// Every wait on an mbarrier is bounded: when a wait runs out the CTA raises
+// the caller's error flag, waits (bounded) for its own copies in flight,
+// frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.h"
+
+namespace vb {
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;
+constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..5 epilogue
+constexpr uint32_t TC_STAGE_A = TC_BM * TC_BK * 4, TC_STAGE_B = TC_BN * TC_BK * 4;
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr long long TC_WAIT_LIMIT = 1LL << 26;  // polls before a wait is declared failed
+template <bool SPLIT>
+struct TcCfg {
+  static constexpr int STAGES = SPLIT ? 3 : 4;
+  static constexpr uint32_t STAGE_BYTES = (SPLIT ? 2 : 1) * (TC_STAGE_A + TC_STAGE_B);
+  static constexpr size_t SMEM = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 512;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (long long i = 0; i < TC_WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D f32, A/B tf32, both K-major, N = 128, M = 128
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// D element (m, n) sink
+struct Epi {
+  int mode;        // 0: fp32 row-major D[m*ldd + n]; 1: complex double y[m*nh + j] = (D[m,j], D[m,nh+j])
+  float *D;
+  long long ldd;
+  double *Y;       // mode 1
+  int nh;          // mode 1: number of complex columns (2*nh <= TC_BN)
+};
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M,
+                        int N, int K, Epi epi, int *err) {
+  constexpr int TC_STAGES = TcCfg<SPLIT>::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + TC_STAGES * TC_STAGE_A;
+  uint8_t *sAlo = sB + TC_STAGES * TC_STAGE_B;                     // SPLIT only
+  uint8_t *sBlo = sAlo + (SPLIT ? TC_STAGES * TC_STAGE_A : 0);     // SPLIT only
+  uint64_t *full = reinterpret_cast<uint64_t *>(sBlo + (SPLIT ? TC_STAGES * TC_STAGE_B : 0));
+  uint64_t *empty = full + TC_STAGES;
+  uint64_t *ready = empty + TC_STAGES;  // SPLIT: stage split into hi / lo
+  uint64_t *accum = ready + TC_STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
+  const int nkb = K / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&ready[s], 4);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+        if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], TC_STAGE_A + TC_STAGE_B);
+        tma_load_2d(sA + s * TC_STAGE_A, &ta, &full[s], kb * TC_BK, m0);
+        tma_load_2d(sB + s * TC_STAGE_B, &tb, &full[s], kb * TC_BK, n0);
+        issued = kb + 1;
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA's shared memory goes away
+        for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
+          mbar_wait(&full[kb % TC_STAGES], (uint32_t)((kb / TC_STAGES) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t idesc = tc_idesc();
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+        if (*abort_flag || !mbar_wait(SPLIT ? &ready[s] : &full[s], ph)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ad = smem_desc(smem_u32(sA + s * TC_STAGE_A));
+        const uint64_t bd = smem_desc(smem_u32(sB + s * TC_STAGE_B));
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 8; ++kk) {  // 8 tf32 = 32 bytes per instruction
+          mma_tf32(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb | kk) != 0);
+          if constexpr (SPLIT) {
+            const uint64_t adl = smem_desc(smem_u32(sAlo + s * TC_STAGE_A));
+            const uint64_t bdl = smem_desc(smem_u32(sBlo + s * TC_STAGE_B));
+            mma_tf32(tmem, ad + (uint64_t)(2 * kk), bdl + (uint64_t)(2 * kk), idesc, 1);
+            mma_tf32(tmem, adl + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, 1);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accum);
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int m = m0 + row;
+    if constexpr (SPLIT) {
+      // split every landed stage into hi (in place) and lo
+      const int t = threadIdx.x - 64;  // 0..127
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+        if (*abort_flag || !mbar_wait(&full[s], ph)) {
+          *abort_flag = 1;
+          break;
+        }
+        uint32_t *a = reinterpret_cast<uint32_t *>(sA + s * TC_STAGE_A);
+        uint32_t *al = reinterpret_cast<uint32_t *>(sAlo + s * TC_STAGE_A);
+        uint32_t *b = reinterpret_cast<uint32_t *>(sB + s * TC_STAGE_B);
+        uint32_t *bl = reinterpret_cast<uint32_t *>(sBlo + s * TC_STAGE_B);
+#pragma unroll 4
+        for (int j = t; j < (int)(TC_STAGE_A / 4); j += 128) {
+          const uint32_t x = a[j], h = x & 0xFFFFE000u;
+          al[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+          a[j] = h;
+        }
+#pragma unroll 4
+        for (int j = t; j < (int)(TC_STAGE_B / 4); j += 128) {
+          const uint32_t x = b[j], h = x & 0xFFFFE000u;
+          bl[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+          b[j] = h;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ready[s])) : "memory");
+      }
+    }
+    bool ok = mbar_wait(accum, 0);
+    if (!ok) *abort_flag = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && !*abort_flag) {
+      float v[32];
+#pragma unroll 1
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        if (m < M) {
+          if (epi.mode == 0) {
+            float *drow = epi.D + (long long)m * epi.ldd + n0 + c0;
+            if (n0 + c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4 *>(drow + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            } else {
+              for (int j = 0; j < 32; ++j)
+                if (n0 + c0 + j < N) drow[j] = v[j];
+            }
+          } else {
+            // complex output: columns [0, nh) real, [nh, 2 nh) imaginary parts
+            for (int j = 0; j < 32; ++j) {
+              const int col = n0 + c0 + j;
+              if (col < epi.nh)
+                epi.Y[((long long)m * epi.nh + col) * 2] = (double)v[j];
+              else if (col < 2 * epi.nh)
+                epi.Y[((long long)m * epi.nh + (col - epi.nh)) * 2 + 1] = (double)v[j];
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+vb_status get_encode() {
+  std::call_once(g_encode_once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  });
+  if (!g_encode) return fail(VB_ECUDA, "cuTensorMapEncodeTiled is not available");
+  return VB_OK;
+}
+
+// rows x K fp32 matrix with row pitch ld (elements), boxes of 32 x 128
+vb_status make_map(CUtensorMap *map, const float *base, long long rows, long long K, long long ld) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 4) % 16 != 0 || K % TC_BK != 0)
+    return fail(VB_EINVAL, "tc_gemm: operand must be 16-byte aligned with K a multiple of 32");
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {TC_BK, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(VB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return VB_OK;
+}
+
+bool g_attr_set[2][64] = {{false}};
+
+}  // namespace
+
+// D (M x N) = A (M x K) B (N x K)^T in TF32 with FP32 accumulation.
+// mode 0: D fp32 row-major with pitch ldd; mode 1: complex double output
+// Y[m][j] = (D[m, j], D[m, nh + j]) for j < nh (needs N = 2 nh).
+vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long ldb, int M, int N, int K,
+                       int mode, float *D, long long ldd, double *Y, int nh, int *err, cudaStream_t st,
+                       bool split) {
+  if (M <= 0 || N <= 0 || K <= 0) return VB_OK;
+  if (mode == 1 && N != 2 * nh) return fail(VB_EINVAL, "tc_gemm: complex output needs N = 2 nh");
+  VB_TRY(get_encode());
+  CUtensorMap ta, tb;
+  VB_TRY(make_map(&ta, A, M, K, lda));
+  VB_TRY(make_map(&tb, B, N, K, ldb));
+  int dev = 0;
+  VB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "tc_gemm: device ordinal out of range");
+  if (!g_attr_set[0][dev]) {
+    VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TcCfg<false>::SMEM));
+    g_attr_set[0][dev] = true;
+  }
+  if (!g_attr_set[1][dev]) {
+    VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TcCfg<true>::SMEM));
+    g_attr_set[1][dev] = true;
+  }
+  Epi e{mode, D, ldd, Y, nh};
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
+  if (grid.y > 65535) return fail(VB_EINVAL, "tc_gemm: M too large");
+  if (split)
+    tc_gemm_tf32_kernel<true><<<grid, TC_THREADS, TcCfg<true>::SMEM, st>>>(ta, tb, M, N, K, e, err);
+  else
+    tc_gemm_tf32_kernel<false><<<grid, TC_THREADS, TcCfg<false>::SMEM, st>>>(ta, tb, M, N, K, e, err);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+}  // namespace vb

@@ -10,9 +10,10 @@
 namespace vb {
 namespace {
 
-__global__ void wapply_kernel(const double *__restrict__ ops, const int *__restrict__ ptr,
-                              const int *__restrict__ ent, int d, int Wp, const cd *__restrict__ X,
-                              WStrides xs, cd *__restrict__ Y, WStrides ys, int P, int Q) {
+template <class R>
+__global__ void wapply_kernel(const R *__restrict__ ops, const int *__restrict__ ptr,
+                              const int *__restrict__ ent, int d, int Wp, const cplx<R> *__restrict__ X,
+                              WStrides xs, cplx<R> *__restrict__ Y, WStrides ys, int P, int Q) {
   long long total = (long long)P * d * Wp * Q;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -22,35 +23,36 @@ __global__ void wapply_kernel(const double *__restrict__ ops, const int *__restr
     r /= Wp;
     int so = (int)(r % d);
     int p = (int)(r / d);
-    double ax = 0.0, ay = 0.0;
-    const cd *xb = X + p * xs.p + q * xs.q;
+    R ax = 0, ay = 0;
+    const cplx<R> *xb = X + p * xs.p + q * xs.q;
     for (int e = ptr[wo]; e < ptr[wo + 1]; ++e) {
       int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
-      const cd *xw = xb + wi * xs.w;
+      const cplx<R> *xw = xb + wi * xs.w;
       if (ident) {
-        cd v = xw[so * xs.s];
+        cplx<R> v = xw[so * xs.s];
         ax += v.x;
         ay += v.y;
       } else {
-        const double *o = ops + off + so * d;
+        const R *o = ops + off + so * d;
         for (int s = 0; s < d; ++s) {
-          double c = o[s];
-          if (c != 0.0) {
-            cd v = xw[s * xs.s];
+          R c = o[s];
+          if (c != R(0)) {
+            cplx<R> v = xw[s * xs.s];
             ax = fma(c, v.x, ax);
             ay = fma(c, v.y, ay);
           }
         }
       }
     }
-    Y[p * ys.p + so * ys.s + wo * ys.w + q * ys.q] = mkc(ax, ay);
+    Y[p * ys.p + so * ys.s + wo * ys.w + q * ys.q] = mkc<R>(ax, ay);
   }
 }
 
 }  // namespace
 
-vb_status wapply(const MpoSite &site, int dir, const cd *X, WStrides xs, long long x_size, cd *Y,
-                 WStrides ys, long long y_size, int P, int Q, cudaStream_t st) {
+template <class R>
+vb_status wapply(const MpoSite &site, int dir, const cplx<R> *X, WStrides xs, long long x_size,
+                 cplx<R> *Y, WStrides ys, long long y_size, int P, int Q, cudaStream_t st) {
   const int d = site.d;
   const int Wp = dir == 0 ? site.wr : site.wl;
   const int Wc = dir == 0 ? site.wl : site.wr;
@@ -68,11 +70,21 @@ vb_status wapply(const MpoSite &site, int dir, const cd *X, WStrides xs, long lo
   int threads = 256;
   long long blocks = (total + threads - 1) / threads;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
-  wapply_kernel<<<(int)blocks, threads, 0, st>>>(site.d_ops, dir == 0 ? site.d_fwd_ptr : site.d_bwd_ptr,
+  const R *ops;
+  if constexpr (sizeof(R) == 8)
+    ops = reinterpret_cast<const R *>(site.d_ops);
+  else
+    ops = reinterpret_cast<const R *>(site.d_ops32);
+  wapply_kernel<R><<<(int)blocks, threads, 0, st>>>(ops, dir == 0 ? site.d_fwd_ptr : site.d_bwd_ptr,
                                                  dir == 0 ? site.d_fwd_ent : site.d_bwd_ent, d, Wp,
                                                  X, xs, Y, ys, P, Q);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
+
+template vb_status wapply<double>(const MpoSite &, int, const cd *, WStrides, long long, cd *, WStrides,
+                                  long long, int, int, cudaStream_t);
+template vb_status wapply<float>(const MpoSite &, int, const cf *, WStrides, long long, cf *, WStrides,
+                                 long long, int, int, cudaStream_t);
 
 }  // namespace vb

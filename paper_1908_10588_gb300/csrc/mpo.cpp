@@ -334,6 +334,8 @@ vb_status mpo_upload(const vb_mpo *cmpo) {
   };
   for (MpoSite &S : mpo->sites) {
     VB_TRY(up(S.ops.data(), S.ops.size() * sizeof(double), (void **)&S.d_ops));
+    std::vector<float> ops32(S.ops.begin(), S.ops.end());
+    VB_TRY(up(ops32.data(), ops32.size() * sizeof(float), (void **)&S.d_ops32));
     for (int dir = 0; dir < 2; ++dir) {
       int np = dir == 0 ? S.wr : S.wl;
       std::vector<int> ptr(np + 1, 0), ent;

@@ -18,8 +18,8 @@ struct Prof {
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> open_start;  // per phase
-  double ms[8] = {0};
-  long long calls[8] = {0};
+  double ms[PH_COUNT] = {0};
+  long long calls[PH_COUNT] = {0};
   double flops[2] = {0, 0};
 } g_prof;
 
@@ -41,14 +41,14 @@ bool prof_on() { return g_prof.on; }
 
 void prof_begin(int phase, cudaStream_t st) {
   if (!g_prof.on) return;
-  if (g_prof.open_start.size() < 8) g_prof.open_start.assign(8, nullptr);
+  if (g_prof.open_start.size() < PH_COUNT) g_prof.open_start.assign(PH_COUNT, nullptr);
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
   g_prof.open_start[phase] = e;
 }
 
 void prof_end(int phase, cudaStream_t st, double flops) {
-  if (!g_prof.on || g_prof.open_start.size() < 8 || !g_prof.open_start[phase]) return;
+  if (!g_prof.on || g_prof.open_start.size() < PH_COUNT || !g_prof.open_start[phase]) return;
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
   g_prof.pending.push_back(Pending{phase, g_prof.open_start[phase], e, flops});
@@ -90,14 +90,14 @@ vb_status vb_profile_read(vb_profile *out, int reset) {
   if (!out) return vb::fail(VB_EINVAL, "vb_profile_read: null argument");
   vb::prof_collect();
   std::memset(out, 0, sizeof(*out));
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < vb::PH_COUNT; ++i) {
     out->ms[i] = vb::g_prof.ms[i];
     out->calls[i] = vb::g_prof.calls[i];
   }
   out->heff_flops[0] = vb::g_prof.flops[0];
   out->heff_flops[1] = vb::g_prof.flops[1];
   if (reset) {
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < vb::PH_COUNT; ++i) {
       vb::g_prof.ms[i] = 0;
       vb::g_prof.calls[i] = 0;
     }

@@ -24,9 +24,10 @@ constexpr double MULTIPLET_RTOL = 1e-10;
 
 // H_eff products in split-TF32 on the tensor cores (k_mixed.cu)
 vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
-                           const cd *R, const cd *x, cd *y, void *work, size_t work_bytes,
+                           const cd *R, const cd *x, cd *y, void *work, size_t work_bytes, int *err,
                            cudaStream_t st);
 size_t heff_mixed_work_bytes(const vb_mpo *mpo, int site, int two_site, int mL, int mR);
+int *heff_mixed_err_flag(const vb_mpo *mpo, int site, int two_site, int mL, int mR, void *work);
 
 namespace {
 
@@ -125,6 +126,7 @@ struct vb_mps {
          *d_evals = nullptr, *d_trace = nullptr, *d_part = nullptr, *d_pop = nullptr;
   cd *d_c = nullptr, *d_c2 = nullptr, *d_u = nullptr, *d_partc = nullptr;
   double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
+  int *d_tcerr = nullptr;                        // raised by a tensor-core kernel whose wait ran out
   std::vector<void *> owned;
   int center = 0;
 };
@@ -156,7 +158,7 @@ vb_status heff2_fp64(const vb_mpo *mpo, int i, int mL, int mR, const cd *L, cons
   g.M = (int)(mL * wL); g.N = (int)(d1 * Q1); g.K = mL; g.batch = 1;
   g.opA = OP_N; g.opB = OP_N;
   g.A = L; g.lda = mL; g.B = x; g.ldb = g.N; g.C = T1; g.ldc = g.N;
-  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
   g.a_size = mL * wL * mL; g.b_size = th; g.c_size = t_cap;
   VB_TRY(zgemm(g, st));
   // T2[a'][s'][w1][(t b)] = W_i applied to T1[a'][w0][s][(t b)]
@@ -170,7 +172,7 @@ vb_status heff2_fp64(const vb_mpo *mpo, int i, int mL, int mR, const cd *L, cons
   h.M = (int)(mL * d1 * d2); h.N = mR; h.K = (int)(wR * mR); h.batch = 1;
   h.opA = OP_N; h.opB = OP_T;
   h.A = T1; h.lda = h.K; h.B = R; h.ldb = h.K; h.C = y; h.ldc = mR;
-  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
   h.a_size = t_cap; h.b_size = (long long)mR * wR * mR; h.c_size = th;
   return zgemm(h, st);
 }
@@ -184,7 +186,7 @@ vb_status heff1_fp64(const vb_mpo *mpo, int j, int mL, int mR, const cd *L, cons
   g.M = (int)(mL * wL); g.N = (int)(d * mR); g.K = mL; g.batch = 1;
   g.opA = OP_N; g.opB = OP_N;
   g.A = L; g.lda = mL; g.B = x; g.ldb = g.N; g.C = T1; g.ldc = g.N;
-  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
   g.a_size = mL * wL * mL; g.b_size = mL * d * mR; g.c_size = t_cap;
   VB_TRY(zgemm(g, st));
   // T2[a'][t'][w1][b] = W applied to T1[a'][w0][t][b]
@@ -194,7 +196,7 @@ vb_status heff1_fp64(const vb_mpo *mpo, int j, int mL, int mR, const cd *L, cons
   h.M = (int)(mL * d); h.N = mR; h.K = (int)(wR * mR); h.batch = 1;
   h.opA = OP_N; h.opB = OP_T;
   h.A = T2; h.lda = h.K; h.B = R; h.ldb = h.K; h.C = y; h.ldc = mR;
-  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
   h.a_size = t_cap; h.b_size = (long long)mR * wR * mR; h.c_size = mL * d * mR;
   return zgemm(h, st);
 }
@@ -209,7 +211,7 @@ vb_status env_left(const vb_mpo *mpo, int p, int mL, int mR, const cd *L, const 
   g.M = (int)(mL * wL); g.N = (int)(d * mR); g.K = mL; g.batch = 1;
   g.opA = OP_N; g.opB = OP_N;
   g.A = L; g.lda = mL; g.B = A; g.ldb = g.N; g.C = T1; g.ldc = g.N;
-  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
   g.a_size = mL * wL * mL; g.b_size = mL * d * mR; g.c_size = t_cap;
   VB_TRY(zgemm(g, st));
   // T2[x][s'][v][y] = W applied to T1[x][w][s][y]
@@ -220,7 +222,7 @@ vb_status env_left(const vb_mpo *mpo, int p, int mL, int mR, const cd *L, const 
   h.M = mR; h.N = (int)(wR * mR); h.K = (int)(mL * d); h.batch = 1;
   h.opA = OP_C; h.opB = OP_N;
   h.A = A; h.lda = mR; h.B = T2; h.ldb = h.N; h.C = Lnew; h.ldc = h.N;
-  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
   h.a_size = mL * d * mR; h.b_size = t_cap; h.c_size = (long long)mR * wR * mR;
   return zgemm(h, st);
 }
@@ -236,7 +238,7 @@ vb_status env_right(const vb_mpo *mpo, int p, int mL, int mR, const cd *R, const
   g.A = B; g.lda = mR; g.sA = 0;
   g.B = R; g.ldb = wR * mR; g.sB = mR;
   g.C = T1; g.ldc = wR * mR; g.sC = mR;
-  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
   g.a_size = mL * d * mR; g.b_size = (long long)mR * wR * mR; g.c_size = t_cap;
   VB_TRY(zgemm(g, st));
   // T2[a][w][t'][y] = sum_{t, v} W[w, t', t, v] T1[a][t][v][y]
@@ -249,7 +251,7 @@ vb_status env_right(const vb_mpo *mpo, int p, int mL, int mR, const cd *R, const
   h.A = B; h.lda = d * mR; h.sA = 0;
   h.B = T2; h.ldb = wL * d * mR; h.sB = d * mR;
   h.C = Rnew; h.ldc = wL * mL; h.sC = mL;
-  h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
   h.a_size = mL * d * mR; h.b_size = t_cap; h.c_size = (long long)mL * wL * mL;
   return zgemm(h, st);
 }
@@ -289,7 +291,7 @@ vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
   vb_status r;
   if (s->dtype == VB_MIXED)
     r = heff_mixed_apply(s->mpo, op.site, op.two_site, op.mL, op.mR, op.L, op.R, x, y, s->mixw,
-                         s->mixw_bytes, s->st);
+                         s->mixw_bytes, s->d_tcerr, s->st);
   else if (op.two_site)
     r = heff2_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
   else
@@ -395,7 +397,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
   const cd *M = s->theta;
   GemmArgs g{};
   g.M = n; g.N = n; g.batch = 1;
-  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
   if (left) {  // rho = M M^+
     g.K = n2; g.opA = OP_N; g.opB = OP_C;
     g.A = M; g.lda = n2; g.B = M; g.ldb = n2;
@@ -405,18 +407,25 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
   }
   g.C = s->rho; g.ldc = n;
   g.a_size = (long long)n1 * n2; g.b_size = (long long)n1 * n2; g.c_size = s->nrho_cap * s->nrho_cap;
+  prof_begin(PH_RHO, st);
   VB_TRY(zgemm(g, st));
   trace_kernel<<<1, 256, 0, st>>>(s->rho, n, s->d_trace);
   VB_CHECK_LAUNCH();
+  prof_end(PH_RHO, st, 0.0);
   const int kw = std::min(n, o.m_max + 1);
+  prof_begin(PH_EIGVAL, st);
   VB_TRY(eig_values(n, s->rho, kw, s->d_evals, s->eigw, st));
+  prof_end(PH_EIGVAL, st, 0.0);
   std::vector<double> lam(kw);
   double tot = 0.0;
   VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), s->d_evals, kw * sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaMemcpyAsync(&tot, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaStreamSynchronize(st));
   const int k = choose_rank(lam, n, tot, std::min(n1, n2), o, disc);
+  prof_begin(PH_EIGVEC, st);
   VB_TRY(eig_vectors(n, s->rho, kw, k, s->d_evals, s->Z, s->eigw, st));
+  prof_end(PH_EIGVEC, st, 0.0);
+  prof_begin(PH_SPLITOUT, st);
   if (left) {
     transpose_kernel<<<grid1((long long)k * n1), 256, 0, st>>>(s->Z, k, n1, dstA);
     VB_CHECK_LAUNCH();
@@ -424,7 +433,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
     h.M = k; h.N = n2; h.K = n1; h.batch = 1;
     h.opA = OP_R; h.opB = OP_N;
     h.A = s->Z; h.lda = n1; h.B = M; h.ldb = n2; h.C = dstC; h.ldc = n2;
-    h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+    h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
     h.a_size = (long long)k * n1; h.b_size = (long long)n1 * n2; h.c_size = (long long)k * n2;
     VB_TRY(zgemm(h, st));
     const long long nc = (long long)k * n2;
@@ -437,13 +446,14 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
     h.M = n1; h.N = k; h.K = n2; h.batch = 1;
     h.opA = OP_N; h.opB = OP_T;
     h.A = M; h.lda = n2; h.B = s->Z; h.ldb = n2; h.C = dstA; h.ldc = k;
-    h.alpha = mkc(1, 0); h.beta = mkc(0, 0);
+    h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
     h.a_size = (long long)n1 * n2; h.b_size = (long long)k * n2; h.c_size = (long long)n1 * k;
     VB_TRY(zgemm(h, st));
     const long long nc = (long long)n1 * k;
     VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
     VB_TRY(vec_scale_inv(dstA, nc, s->d_nrm, st));
   }
+  prof_end(PH_SPLITOUT, st, 0.0);
   *k_out = k;
   return VB_OK;
 }
@@ -455,7 +465,7 @@ vb_status merge(vb_mps *s, int i) {
   g.M = mL * d1; g.N = d2 * mR; g.K = mM; g.batch = 1;
   g.opA = OP_N; g.opB = OP_N;
   g.A = s->A[i]; g.lda = mM; g.B = s->A[i + 1]; g.ldb = g.N; g.C = s->theta; g.ldc = g.N;
-  g.alpha = mkc(1, 0); g.beta = mkc(0, 0);
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
   g.a_size = (long long)mL * d1 * mM; g.b_size = (long long)mM * d2 * mR; g.c_size = s->theta_cap;
   return zgemm(g, s->st);
 }
@@ -559,7 +569,12 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
     A2((void **)&s->d_c2, 128 * sizeof(cd));
     A2((void **)&s->d_u, 128 * sizeof(cd));
     A2((void **)&s->d_partc, (size_t)512 * 128 * sizeof(cd));
+    A2((void **)&s->d_tcerr, 256);
     if (e != VB_OK) return fail_free(e);
+    if (cudaMemsetAsync(s->d_tcerr, 0, sizeof(int), s->st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_free(fail(VB_ECUDA, "mps: memset failed"));
+    }
     if (s->dtype == VB_MIXED) {
       size_t mb = 0;
       for (int p = 0; p < n; ++p) {
@@ -618,16 +633,16 @@ vb_status mps_create(const vb_mpo *mpo, const int *init_index, const vb_mps_opts
   // state, the remaining rows are distinct unit vectors
   for (int p = 0; p < n; ++p) {
     const int dl = s->bond[p], d = s->dims[p], dr = s->bond[p + 1];
-    std::vector<cd> h((size_t)dl * d * dr, mkc(0, 0));
+    std::vector<cd> h((size_t)dl * d * dr, mkc(0.0, 0.0));
     if (p == 0) {
-      h[(size_t)init_index[0] * dr] = mkc(1, 0);
+      h[(size_t)init_index[0] * dr] = mkc(1.0, 0.0);
     } else {
       const int cols = d * dr, first = init_index[p] * dr;
-      h[first] = mkc(1, 0);
+      h[first] = mkc(1.0, 0.0);
       int c = 0;
       for (int r = 1; r < dl; ++r) {
         if (c == first) ++c;
-        h[(size_t)r * cols + c] = mkc(1, 0);
+        h[(size_t)r * cols + c] = mkc(1.0, 0.0);
         ++c;
       }
     }
@@ -783,6 +798,11 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
   }
   VB_TRY_CUDA(cudaStreamSynchronize(s->st));
   prof_collect();
+  if (s->dtype == VB_MIXED) {
+    int tcerr = 0;
+    VB_TRY_CUDA(cudaMemcpy(&tcerr, s->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tcerr) return fail(VB_ETIMEOUT, "tdvp2_sweep: a tensor-core kernel's wait ran out (results invalid)");
+  }
   for (int b = 1; b < n; ++b) st.max_bond = std::max(st.max_bond, s->bond[b]);
   if (stats) *stats = st;
   return VB_OK;
@@ -823,9 +843,16 @@ vb_status vb_heff2_apply(const vb_mpo *mpo, int i, int mL, int mR, const double 
     return fail(VB_EINVAL, "vb_heff2_apply: bad argument");
   VB_TRY(mpo_upload(mpo));
   cudaStream_t st = (cudaStream_t)stream;
-  if (dtype == VB_MIXED)
-    return heff_mixed_apply(mpo, i, 1, mL, mR, (const cd *)L, (const cd *)R, (const cd *)theta, (cd *)y,
-                            work, vb_heff_work_elems(mpo, i, mL, mR, 1) * sizeof(cd), st);
+  if (dtype == VB_MIXED) {
+    int *err = heff_mixed_err_flag(mpo, i, 1, mL, mR, work);
+    VB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    VB_TRY(heff_mixed_apply(mpo, i, 1, mL, mR, (const cd *)L, (const cd *)R, (const cd *)theta, (cd *)y, work,
+                            vb_heff_work_elems(mpo, i, mL, mR, 1) * sizeof(cd), err, st));
+    int h = 0;
+    VB_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    return h ? fail(VB_ETIMEOUT, "vb_heff2_apply: a tensor-core kernel's wait ran out") : VB_OK;
+  }
   const MpoSite &S = mpo->sites[i], &S2 = mpo->sites[i + 1];
   size_t th = (size_t)mL * S.d * S2.d * mR;
   size_t w = std::max(S.wl, std::max(S.wr, S2.wr));
@@ -840,9 +867,16 @@ vb_status vb_heff1_apply(const vb_mpo *mpo, int j, int mL, int mR, const double 
     return fail(VB_EINVAL, "vb_heff1_apply: bad argument");
   VB_TRY(mpo_upload(mpo));
   cudaStream_t st = (cudaStream_t)stream;
-  if (dtype == VB_MIXED)
-    return heff_mixed_apply(mpo, j, 0, mL, mR, (const cd *)L, (const cd *)R, (const cd *)C, (cd *)y, work,
-                            vb_heff_work_elems(mpo, j, mL, mR, 0) * sizeof(cd), st);
+  if (dtype == VB_MIXED) {
+    int *err = heff_mixed_err_flag(mpo, j, 0, mL, mR, work);
+    VB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    VB_TRY(heff_mixed_apply(mpo, j, 0, mL, mR, (const cd *)L, (const cd *)R, (const cd *)C, (cd *)y, work,
+                            vb_heff_work_elems(mpo, j, mL, mR, 0) * sizeof(cd), err, st));
+    int h = 0;
+    VB_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    return h ? fail(VB_ETIMEOUT, "vb_heff1_apply: a tensor-core kernel's wait ran out") : VB_OK;
+  }
   const MpoSite &S = mpo->sites[j];
   size_t one = (size_t)mL * S.d * mR * std::max(S.wl, S.wr);
   cd *T1 = (cd *)work, *T2 = T1 + one;

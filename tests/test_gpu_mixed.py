@@ -1,0 +1,83 @@
+"""Mixed-precision form (H_eff products in complex FP32, everything else in
+FP64) against the FP64 oracle: single products within FP32 accuracy and
+whole 2TDVP runs with populations within 1e-4."""
+import numpy as np
+import pytest
+
+import vibmodels as vm
+from oracle import mpo as ompo
+from oracle import tdvp as otdvp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from test_gpu_kernels import CASES, _dev, _envs_gpu, _envs_oracle, _mixed_canonical, _model  # noqa: E402
+
+HEFF_MIXED_RTOL = 2e-5   # FP32 products with FP32 accumulation, relative to max |y|
+POP_TOL_MIXED = 1e-4     # populations vs the FP64 oracle
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1908_10588_gb300 as p
+    from paper_1908_10588_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return p
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("two_site", [True, False])
+def test_mixed_heff_parity(P, case, two_site):
+    name, D, i = CASES[case]
+    m = _model(name)
+    dims = vm.local_dims(m)
+    D = [min(b, int(np.prod(dims[: k + 1])), int(np.prod(dims[k + 1:]))) for k, b in enumerate(D)]
+    rng = np.random.Generator(np.random.PCG64(300 + case))
+    T, Db = _mixed_canonical(rng, dims, D, i, two_site)
+    mpo = P.Mpo(m)
+    fr = i + 2 if two_site else i + 1
+    Lg, Rg = _envs_gpu(P, mpo, T, Db, i, fr)
+    Wo = [w.astype(complex) for w in ompo.build_mpo(m)]
+    Lo, Ro = _envs_oracle(Wo, T, i, fr)
+    mL, mR = Db[i], Db[fr]
+    if two_site:
+        x = vm.random_complex(rng, (mL, dims[i], dims[i + 1], mR))
+        yo = otdvp.heff2_apply(Lo, Wo[i], Wo[i + 1], Ro, x)
+    else:
+        x = vm.random_complex(rng, (mL, dims[i], mR))
+        yo = otdvp.heff1_apply(Lo, Wo[i], Ro, x)
+    y = torch.zeros(x.size, dtype=torch.complex128, device="cuda")
+    work = torch.zeros(P.vb_heff_work_elems(mpo, i, mL, mR, two_site), dtype=torch.complex128, device="cuda")
+    if two_site:
+        P.vb_heff2_apply(mpo, i, mL, mR, Lg, Rg, _dev(x), y, work, P.VB_MIXED)
+    else:
+        P.vb_heff1_apply(mpo, i, mL, mR, Lg, Rg, _dev(x), y, work, P.VB_MIXED)
+    torch.cuda.synchronize()
+    yg = y.cpu().numpy().reshape(yo.shape)
+    assert np.max(np.abs(yg - yo)) <= HEFF_MIXED_RTOL * np.max(np.abs(yo))
+
+
+def _run(P, m, steps, dt, m_max, eps=0.0):
+    dims, idx = vm.local_dims(m), vm.product_state_indices(m)
+    mpo = P.Mpo(m)
+    mps = P.Mps(mpo, idx, m_cap=m_max, dtype=P.VB_MIXED)
+    ref = otdvp.Tdvp2(otdvp.product_mps(dims, idx), ompo.build_mpo(m), otdvp.TdvpOptions(m_max=m_max, eps=eps))
+    errs = []
+    for _ in range(steps):
+        st = mps.sweep(dt, m_max=m_max, eps=eps, krylov_tol=1e-10)
+        ref.step(dt)
+        errs.append(np.max(np.abs(mps.populations() - otdvp.populations(ref.mps))))
+        assert st.noconv == 0
+    return errs
+
+
+def test_mixed_sweeps_two_state_four_mode_m16(P):
+    errs = _run(P, vm.model_small_2state(), 16, 0.5, 16)
+    assert max(errs) < POP_TOL_MIXED
+
+
+def test_mixed_sweeps_dbss(P):
+    m = vm.model_internal_conversion(seed=31, n_modes=5, level_range=(3, 6), n_offdiag=2, n_bilinear=4)
+    errs = _run(P, m, 10, 0.5, 24, eps=1e-6)
+    assert max(errs) < POP_TOL_MIXED
