@@ -244,6 +244,27 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_val = ws * e2e_steps / e2e_s if e2e_steps else None
 
+    # ---- FP64 form beside the mixed one: one step from the same state, and the
+    # population difference between the two forms after that step
+    compare = None
+    if dtype == P.VB_MIXED and not args.no_fp64_compare:
+        m64 = P.Mps(mpo, m_cap=M_MAX, dtype=P.VB_FP64, krylov_cap=40, stream=stream, tensors=tensors)
+        m32 = P.Mps(mpo, m_cap=M_MAX, dtype=P.VB_MIXED, krylov_cap=40, stream=stream, tensors=tensors)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        m64.sweep(DT_FS, **sweep_kw)
+        c1.record(stream)
+        m32.sweep(DT_FS, **sweep_kw)
+        torch.cuda.synchronize()
+        fp64_ms = c0.elapsed_time(c1)
+        perr = float(np.max(np.abs(m64.populations() - m32.populations())))
+        compare = {"fp64_sweeps_per_s": 1e3 / fp64_ms, "fp64_ms_per_step": fp64_ms,
+                   "speedup_mixed_over_fp64": (1e3 / fp64_ms) and value / (ws * 1e3 / fp64_ms),
+                   "pop_err_mixed_vs_fp64_after_1_step": perr}
+        m64.close()
+        m32.close()
+
     # ---- roofline of the H_eff products
     peaks, src = _peaks()
     h2 = prof["heff2"]
@@ -258,7 +279,8 @@ def run_ours(args):
         pk = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                 "frac": achieved / pk, "traffic": None,
-                "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio"}
+                "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio (tf32 pipe)",
+                "useful_ceiling_split_tf32": pk / 3.0, "frac_of_useful_ceiling": achieved / (pk / 3.0)}
     roof["kernel"] = "H_eff products (two- and one-site), algorithmic flops / event time"
     roof["heff_calls"] = h2["calls"] + prof["heff1"]["calls"]
     roof["heff_ms_per_call"] = heff_ms / max(1, roof["heff_calls"])
@@ -267,7 +289,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if dtype == P.VB_FP64 else "c64-tf32x3/f64",
+        "dtype": "f64" if dtype == P.VB_FP64 else "tf32x3-f32acc/f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_sites": len(dims), "m_max": M_MAX, "eps": EPS, "dt_fs": DT_FS,
                    "parallelism": f"replicas x{ws}",
@@ -277,11 +299,16 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
+        "phase_share": {k: round(prof[k]["ms"] / max(1e-9, sum(prof[q]["ms"] for q in
+                                                                ("heff2", "heff1", "krylov", "split", "env", "merge"))), 4)
+                        for k in ("heff2", "heff1", "krylov", "split", "env", "merge")},
         "heff_tflops": achieved,
         "krylov_iters_max": max(s.krylov_iters_max for s in stats),
         "max_bond": max(bonds),
         "populations": [float(x) for x in pops],
     }
+    if compare is not None:
+        line["fp64_form"] = compare
     if rank == 0 and not args.no_cpu_baseline:
         v, pairs, el, _ = _oracle_sample(model, tensors, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -338,7 +365,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--dtype", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -209,7 +209,8 @@ unsigned long long vb_kernel_launches(void);
  * reduced density matrix, eigensolver and the new tensors, 4 = environment
  * updates, 5 = merge of two sites; sub-phases of 3: 6 = reduced density
  * matrix, 7 = tridiagonal reduction and eigenvalues, 8 = eigenvectors,
- * 9 = new tensors and normalisation). heff_flops[c] counts the algorithmic
+ * 9 = new tensors and normalisation; in the mixed form 10 and 11 are the
+ * FP32 eigenvalue and eigenvector stages inside 7). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
  * multiply-add is 8, real-times-complex 4, an identity-block add 2). */
 typedef struct {

@@ -62,7 +62,7 @@ class vb_profile(C.Structure):
 
 
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
-          "split_out"]
+          "split_out", "split_eig32_values", "split_eig32_vectors"]
 
 
 class vb_sweep_stats(C.Structure):

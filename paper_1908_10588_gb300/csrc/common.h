@@ -40,7 +40,7 @@ void count_launch();
 
 // ---- per-phase event profiler (host side, single-threaded use)
 enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5, PH_RHO = 6, PH_EIGVAL = 7,
-       PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_COUNT = 12 };
+       PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_EIG32VAL = 10, PH_EIG32VEC = 11, PH_COUNT = 12 };
 bool prof_on();
 void prof_begin(int phase, cudaStream_t st);
 void prof_end(int phase, cudaStream_t st, double flops);
@@ -207,6 +207,9 @@ int reduce_parts(long long n);
 struct EigWork {
   // layout inside one device buffer (real type of size real_bytes)
   static size_t bytes(int n, int k_want, int real_bytes = 8);
+  // synchronises st and returns VB_ETIMEOUT if a bounded wait of the last
+  // eig_values on this workspace ran out
+  static vb_status check(int n, int k_want, int real_bytes, const void *work, cudaStream_t st);
 };
 // phase 1: reduce rho (n x n, destroyed) to real tridiagonal form and compute
 // the k_want largest eigenvalues (descending) into evals (device)

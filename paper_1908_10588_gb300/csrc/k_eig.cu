@@ -59,7 +59,7 @@ __device__ R block_sum_all(R v, R *sh) {
 }
 
 struct EigLayout {
-  size_t off_vref, off_tau, off_dg, off_ec, off_eabs, off_delta, off_p, off_y, off_lu, total;
+  size_t off_vref, off_tau, off_dg, off_ec, off_eabs, off_delta, off_p, off_y, off_lu, off_part, off_bar, total;
   EigLayout(int n, int k, int rb) {
     const size_t cb = 2 * (size_t)rb;
     size_t o = 0;
@@ -77,6 +77,8 @@ struct EigLayout {
     off_p = take((size_t)n * cb);
     off_y = take((size_t)k * n * rb);
     off_lu = take((size_t)k * n * 5 * rb + (size_t)k * n * sizeof(int));
+    off_part = take((size_t)1024 * rb);
+    off_bar = take(256);  // barrier count, generation, error flag
     total = o;
   }
 };
@@ -389,9 +391,182 @@ __global__ void backtransform(const cplx<R> *vref, const R *tau, const cplx<R> *
   }
 }
 
+
+// ---- 1'. the whole Householder reduction in one cooperative launch
+//
+// One block per SM; the blocks meet at a bounded grid barrier twice per
+// column. Every block recomputes the reflector of column j from row j
+// (contiguous: A is kept Hermitian in both triangles, so row j holds the
+// conjugated column), so no barrier is needed for it.
+constexpr long long GB_LIMIT = 1LL << 27;  // polls before a barrier is declared failed (well over a second)
+
+__device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, unsigned int nblocks, int *err,
+                             int *sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (*(volatile int *)err) {
+      ok = 0;
+    } else {
+      const unsigned int g = *gen;
+      __threadfence();
+      const unsigned int arrived = atomicAdd(count, 1u);
+      if (arrived == nblocks - 1) {
+        atomicExch(count, 0u);
+        __threadfence();
+        atomicAdd((unsigned int *)gen, 1u);
+      } else {
+        long long i = 0;
+        while (*gen == g) {
+          if (++i > GB_LIMIT || ((i & 1023) == 0 && *(volatile int *)err)) {
+            atomicExch(err, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    *sh_ok = ok;
+  }
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
+template <class R>
+__global__ void __launch_bounds__(512) hh_tridiag_coop(cplx<R> *A, int n, cplx<R> *vref, R *tau, R *dg,
+                                                       cplx<R> *ec, cplx<R> *p, R *partial, unsigned int *bar,
+                                                       int *err) {
+  typedef cplx<R> cd;
+  __shared__ R sh[33];
+  __shared__ R shw[16];
+  __shared__ int sh_ok;
+  const unsigned int nb = gridDim.x;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + wib, GW = nb * wpb;
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    const cd *rowj = A + (long long)j * n + j + 1;  // conj of column j below the diagonal
+    R s = 0;
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += cabs2(rowj[i]);
+    const R sigma = block_sum_all<R>(s, sh);
+    const cd alpha = cconj(rowj[0]);
+    if (sigma == R(0)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        tau[j] = 0;
+        ec[j] = alpha;
+        dg[j] = A[(long long)j * n + j].x;
+      }
+      continue;  // identical decision in every block: no barrier needed
+    }
+    const R aa = sqrt(cabs2(alpha));
+    const R nx = sqrt(aa * aa + sigma);
+    const cd ph = aa > R(0) ? mkc<R>(alpha.x / aa, alpha.y / aa) : mkc<R>(1, 0);
+    const cd v0 = cscale(ph, aa + nx);
+    const R t = R(1) / (nx * (nx + aa));
+    if (blockIdx.x == 0) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) vref[(long long)j * n + j + 1 + i] = i == 0 ? v0 : cconj(rowj[i]);
+      if (threadIdx.x == 0) {
+        tau[j] = t;
+        ec[j] = cscale(ph, -nx);
+        dg[j] = A[(long long)j * n + j].x;
+      }
+    }
+    // p = t A22 v (one warp per row), with the partial sums of Re(v^+ p)
+    R wsum = 0;
+    for (int r = gw; r < m; r += GW) {
+      const cd *row = A + (long long)(j + 1 + r) * n + j + 1;
+      R sx = 0, sy = 0;
+      for (int c = lane; c < m; c += 32) {
+        const cd a = row[c];
+        const cd v = c == 0 ? v0 : cconj(rowj[c]);
+        sx = fma(a.x, v.x, fma(-a.y, v.y, sx));
+        sy = fma(a.x, v.y, fma(a.y, v.x, sy));
+      }
+      sx = warp_sum<R>(sx);
+      sy = warp_sum<R>(sy);
+      if (lane == 0) {
+        const cd pr = mkc<R>(t * sx, t * sy);
+        p[r] = pr;
+        const cd vr = r == 0 ? v0 : cconj(rowj[r]);
+        wsum += vr.x * pr.x + vr.y * pr.y;
+      }
+    }
+    if (lane == 0) shw[wib] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R b = 0;
+      for (int w = 0; w < wpb; ++w) b += shw[w];
+      partial[blockIdx.x] = b;
+    }
+    if (!grid_barrier(bar, bar + 1, nb, err, &sh_ok)) return;
+    // K = (t/2) Re(v^+ p); w = p - K v; A22 -= v w^+ + w v^+
+    R tot = 0;
+    for (unsigned int b = 0; b < nb; ++b) tot += partial[b];
+    const R K = R(0.5) * t * tot;
+    for (int r = gw; r < m; r += GW) {
+      cd *row = A + (long long)(j + 1 + r) * n + j + 1;
+      const cd vr = r == 0 ? v0 : cconj(rowj[r]);
+      const cd wr = csub(p[r], cscale(vr, K));
+      for (int c = lane; c < m; c += 32) {
+        const cd vc = c == 0 ? v0 : cconj(rowj[c]);
+        const cd wc = csub(p[c], cscale(vc, K));
+        const cd x = cadd(cmul(vr, cconj(wc)), cmul(wr, cconj(vc)));
+        row[c] = csub(row[c], x);
+      }
+    }
+    if (!grid_barrier(bar, bar + 1, nb, err, &sh_ok)) return;
+  }
+}
+
+// ---- 3'. multisection: one warp per eigenvalue, 32 Sturm counts per step
+template <class R>
+__global__ void multisect_kernel(const R *dg, const R *e, int n, int k_want, R *evals) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= k_want) return;
+  const R eps = Eps<R>::eps, tiny = Eps<R>::tiny;
+  R lo = Eps<R>::huge, hi = -Eps<R>::huge, emax = 0;
+  for (int i = 0; i < n; ++i) {
+    R r = (i > 0 ? e[i - 1] : R(0)) + (i + 1 < n ? e[i] : R(0));
+    lo = fmin(lo, dg[i] - r);
+    hi = fmax(hi, dg[i] + r);
+    emax = fmax(emax, fabs(dg[i]) + r);
+  }
+  const R tnorm = fmax(emax, tiny);
+  const R pivmin = tiny * fmax(R(1), tnorm * tnorm);
+  lo -= R(2) * eps * tnorm * n + tiny;
+  hi += R(2) * eps * tnorm * n + tiny;
+  const int target = n - 1 - t;  // ascending index: count(lo) <= target < count(hi)
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + R(1e-18) * tnorm) break;
+    const R x = lo + (hi - lo) * R(lane + 1) / R(33);
+    const int c = sturm_count<R>(dg, e, n, x, pivmin);
+    // largest lane whose point still has count <= target -> new lo; next point -> new hi
+    const unsigned int below = __ballot_sync(0xffffffffu, c <= target);
+    const int kb = below ? 31 - __clz(below) : -1;  // highest lane with c <= target
+    const R nlo = kb >= 0 ? __shfl_sync(0xffffffffu, x, kb) : lo;
+    const R nhi = kb < 31 ? __shfl_sync(0xffffffffu, x, kb + 1 > 31 ? 31 : kb + 1) : hi;
+    if (!(nlo > lo || nhi < hi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) evals[t] = R(0.5) * (lo + hi);
+}
+
 }  // namespace
 
 size_t EigWork::bytes(int n, int k_want, int real_bytes) { return EigLayout(n, k_want, real_bytes).total; }
+
+vb_status EigWork::check(int n, int k_want, int real_bytes, const void *work, cudaStream_t st) {
+  EigLayout lay(n, k_want, real_bytes);
+  const int *err = reinterpret_cast<const int *>(static_cast<const char *>(work) + lay.off_bar) + 2;
+  int h = 0;
+  VB_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(VB_ETIMEOUT, "eigensolver: a grid barrier of the tridiagonal reduction ran out");
+  return VB_OK;
+}
 
 template <class R>
 vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cudaStream_t st) {
@@ -406,21 +581,45 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
   R *eabs = reinterpret_cast<R *>(w + lay.off_eabs);
   C_ *delta = reinterpret_cast<C_ *>(w + lay.off_delta);
   C_ *p = reinterpret_cast<C_ *>(w + lay.off_p);
-  for (int j = 0; j + 2 < n; ++j) {
-    const int m = n - j - 1;
-    hh_vector<R><<<1, 256, 0, st>>>(rho, n, j, vref, tau, dg, ec);
-    VB_CHECK_LAUNCH();
-    hh_symv<R><<<(m + 7) / 8, 256, 0, st>>>(rho, n, j, vref, tau, p);
-    VB_CHECK_LAUNCH();
-    hh_wvec<R><<<1, 256, 0, st>>>(n, j, vref, tau, p);
-    VB_CHECK_LAUNCH();
-    dim3 g2((m + 255) / 256, m);
-    hh_rank2<R><<<g2, 256, 0, st>>>(rho, n, j, vref, tau, p);
-    VB_CHECK_LAUNCH();
+  if (n <= 64 || sizeof(R) == 8) {
+    // FP64 or small matrices: four launches per column. (In FP64 the reduction
+    // is bound by GB300's FP64 issue rate, where these per-column kernels
+    // spread the rank-2 update over every SM; the cooperative kernel wins in
+    // FP32, where barriers and launches dominate.)
+    VB_TRY_CUDA(cudaMemsetAsync(w + lay.off_bar, 0, 3 * sizeof(unsigned int), st));
+    // small matrices: four launches per column are cheaper than a grid-wide launch
+    for (int j = 0; j + 2 < n; ++j) {
+      const int m = n - j - 1;
+      hh_vector<R><<<1, 256, 0, st>>>(rho, n, j, vref, tau, dg, ec);
+      VB_CHECK_LAUNCH();
+      hh_symv<R><<<(m + 7) / 8, 256, 0, st>>>(rho, n, j, vref, tau, p);
+      VB_CHECK_LAUNCH();
+      hh_wvec<R><<<1, 256, 0, st>>>(n, j, vref, tau, p);
+      VB_CHECK_LAUNCH();
+      dim3 g2((m + 255) / 256, m);
+      hh_rank2<R><<<g2, 256, 0, st>>>(rho, n, j, vref, tau, p);
+      VB_CHECK_LAUNCH();
+    }
+  } else if (n > 2) {
+    R *part = reinterpret_cast<R *>(w + lay.off_part);
+    unsigned int *bar = reinterpret_cast<unsigned int *>(w + lay.off_bar);
+    int *err = reinterpret_cast<int *>(bar + 2);
+    VB_TRY_CUDA(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned int), st));
+    int dev = 0, sms = 0, per_sm = 0;
+    VB_TRY_CUDA(cudaGetDevice(&dev));
+    VB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_tridiag_coop<R>, 512, 0));
+    if (per_sm < 1) return fail(VB_ECUDA, "eig_values: cooperative kernel does not fit on an SM");
+    int nb = sms;  // one block per SM
+    if (nb > 1024) nb = 1024;
+    void *args[] = {(void *)&rho, (void *)&n, (void *)&vref, (void *)&tau, (void *)&dg, (void *)&ec,
+                    (void *)&p, (void *)&part, (void *)&bar, (void *)&err};
+    VB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)hh_tridiag_coop<R>, dim3(nb), dim3(512), args, 0, st));
+    count_launch();
   }
   tri_finish<R><<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
   VB_CHECK_LAUNCH();
-  bisect_kernel<R><<<(k_want + 63) / 64, 64, 0, st>>>(dg, eabs, n, k_want, evals);
+  multisect_kernel<R><<<(k_want * 32 + 255) / 256, 256, 0, st>>>(dg, eabs, n, k_want, evals);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
@@ -442,7 +641,9 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
   R *Y = reinterpret_cast<R *>(w + lay.off_y);
   R *lu = reinterpret_cast<R *>(w + lay.off_lu);
   int *piv = reinterpret_cast<int *>(lu + (size_t)k_want * n * 4);
-  for (int r = 0; r < INVIT_ROUNDS; ++r) {
+  // FP32 vectors only seed an FP64 Rayleigh-Ritz step: two rounds suffice there
+  const int rounds = sizeof(R) == 8 ? INVIT_ROUNDS : 2;
+  for (int r = 0; r < rounds; ++r) {
     invit_round<R><<<(k_vec + 31) / 32, 32, 0, st>>>(dg, eabs, n, k_vec, evals, Y, lu, piv, r);
     VB_CHECK_LAUNCH();
     cgs2_rows<R><<<1, 512, 0, st>>>(Y, n, k_vec);

@@ -21,6 +21,7 @@ using namespace vb;
 namespace vb {
 constexpr double HBAR_EV_FS = 0.6582119569;
 constexpr double MULTIPLET_RTOL = 1e-10;
+constexpr int MIXED_SPLIT_MIN_N = 192;
 
 // H_eff products in split-TF32 on the tensor cores (k_mixed.cu)
 vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
@@ -59,6 +60,27 @@ __global__ void conj_copy_kernel(const cd *src, long long n, cd *dst) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
     dst[e] = cconj(src[e]);
+}
+
+__global__ void c64_to_c32(const cd *__restrict__ x, cf *__restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = mkc<float>((float)x[i].x, (float)x[i].y);
+}
+
+__global__ void c32_to_c64(const cf *__restrict__ x, cd *__restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = mkc<double>((double)x[i].x, (double)x[i].y);
+}
+
+// G <- (3 I - G) / 2 (one Lowdin step towards G^{-1/2} for G close to I)
+__global__ void lowdin_kernel(cd *G, int r) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e / r, j = e % r;
+    cd g = G[e];
+    G[e] = mkc((i == j ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
+  }
 }
 
 __global__ void set_alpha_kernel(const cd *c, const cd *c2, int k, double *alpha) {
@@ -127,6 +149,12 @@ struct vb_mps {
   cd *d_c = nullptr, *d_c2 = nullptr, *d_u = nullptr, *d_partc = nullptr;
   double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
   int *d_tcerr = nullptr;                        // raised by a tensor-core kernel whose wait ran out
+  // mixed split: FP32 eigenvectors of rho, FP64 Rayleigh-Ritz
+  int rcap = 0;
+  cf *M32 = nullptr, *rho32 = nullptr, *Q32 = nullptr;
+  cd *Q64 = nullptr, *Qo = nullptr, *G = nullptr, *X = nullptr, *S = nullptr, *Zr = nullptr, *U = nullptr;
+  float *ev32 = nullptr;
+  void *eigw32 = nullptr, *eigwS = nullptr;
   std::vector<void *> owned;
   int center = 0;
 };
@@ -389,11 +417,18 @@ int choose_rank(const std::vector<double> &lam, int n, double tot, int rank_boun
 
 // theta (mL d1 x d2 mR) -> left-orthonormal A_i (into dstA) and C (into dstC),
 // or (right) C (dstA) and right-orthonormal B (dstC). Returns the new bond.
+vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o, cd *dstA,
+                      cd *dstC, int *k_out, double *disc);
+
 vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o,
                 cd *dstA, cd *dstC, int *k_out, double *disc) {
   cudaStream_t st = s->st;
   const int n1 = mL * d1, n2 = d2 * mR;
   const int n = left ? n1 : n2;
+  // mixed form: FP32 eigenvectors + FP64 Rayleigh-Ritz once the matrix is
+  // large enough for the FP64 reduction to matter
+  if (s->dtype == VB_MIXED && n > MIXED_SPLIT_MIN_N && o.m_max + 1 + 8 <= s->rcap)
+    return split_mixed(s, left, mL, d1, d2, mR, o, dstA, dstC, k_out, disc);
   const cd *M = s->theta;
   GemmArgs g{};
   g.M = n; g.N = n; g.batch = 1;
@@ -421,6 +456,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
   VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), s->d_evals, kw * sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaMemcpyAsync(&tot, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaStreamSynchronize(st));
+  VB_TRY(EigWork::check(n, kw, sizeof(double), s->eigw, st));
   const int k = choose_rank(lam, n, tot, std::min(n1, n2), o, disc);
   prof_begin(PH_EIGVEC, st);
   VB_TRY(eig_vectors(n, s->rho, kw, k, s->d_evals, s->Z, s->eigw, st));
@@ -449,6 +485,115 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
     h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
     h.a_size = (long long)n1 * n2; h.b_size = (long long)k * n2; h.c_size = (long long)n1 * k;
     VB_TRY(zgemm(h, st));
+    const long long nc = (long long)n1 * k;
+    VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
+    VB_TRY(vec_scale_inv(dstA, nc, s->d_nrm, st));
+  }
+  prof_end(PH_SPLITOUT, st, 0.0);
+  *k_out = k;
+  return VB_OK;
+}
+
+// Mixed form of the split: the r = min(n, m_max + 33, 128) leading
+// eigenvectors of rho come from the FP32 eigensolver; the truncation itself
+// is done in FP64 by a Rayleigh-Ritz step on their span: the basis is
+// re-orthonormalised (one Lowdin step), S = Q^+ rho Q is formed from FP64
+// products with theta and diagonalised in FP64, and the kept weights, the
+// discarded weight (against tr rho = |theta|^2) and the new tensors all come
+// from the FP64 Ritz pairs.
+vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o, cd *dstA,
+                      cd *dstC, int *k_out, double *disc) {
+  cudaStream_t st = s->st;
+  const int n1 = mL * d1, n2 = d2 * mR;
+  const int n = left ? n1 : n2;
+  const long long nm = (long long)n1 * n2;
+  const cd *M = s->theta;
+  const int kw = std::min(n, o.m_max + 1);
+  const int r = std::min(n, std::min(kw + 32, s->rcap));
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  auto G64 = [&](int Mm, int Nn, int Kk, int opA, const cd *A, long long lda, long long asz, int opB, const cd *B,
+                 long long ldb, long long bsz, cd *C, long long ldc, long long csz) {
+    GemmArgs g{};
+    g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    return zgemm(g, st);
+  };
+  // ---- FP32 eigenvectors of rho
+  prof_begin(PH_RHO, st);
+  c64_to_c32<<<grid1(nm), 256, 0, st>>>(M, s->M32, nm);
+  VB_CHECK_LAUNCH();
+  {
+    GemmArgsF g{};
+    g.M = n; g.N = n; g.batch = 1;
+    g.alpha = mkc(1.f, 0.f); g.beta = mkc(0.f, 0.f);
+    g.A = s->M32; g.lda = n2; g.B = s->M32; g.ldb = n2;
+    if (left) {
+      g.K = n2; g.opA = OP_N; g.opB = OP_C;
+    } else {
+      g.K = n1; g.opA = OP_C; g.opB = OP_N;
+    }
+    g.C = s->rho32; g.ldc = n;
+    g.a_size = nm; g.b_size = nm; g.c_size = s->nrho_cap * s->nrho_cap;
+    VB_TRY(gemm<float>(g, st));
+  }
+  VB_TRY(vec_norm2(M, nm, s->d_trace, s->d_part, reduce_parts(nm), st));
+  prof_end(PH_RHO, st, 0.0);
+  prof_begin(PH_EIGVAL, st);
+  prof_begin(PH_EIG32VAL, st);
+  VB_TRY(eig_values<float>(n, s->rho32, r, s->ev32, s->eigw32, st));
+  prof_end(PH_EIG32VAL, st, 0.0);
+  prof_begin(PH_EIG32VEC, st);
+  VB_TRY(eig_vectors<float>(n, s->rho32, r, r, s->ev32, s->Q32, s->eigw32, st));
+  prof_end(PH_EIG32VEC, st, 0.0);
+  VB_TRY(EigWork::check(n, r, 4, s->eigw32, st));
+  // ---- FP64 Rayleigh-Ritz on the span of the FP32 vectors (rows of Q)
+  c32_to_c64<<<grid1((long long)r * n), 256, 0, st>>>(s->Q32, s->Q64, (long long)r * n);
+  VB_CHECK_LAUNCH();
+  const long long rn = (long long)r * n, rr = (long long)r * r;
+  VB_TRY(G64(r, r, n, OP_N, s->Q64, n, rn, OP_C, s->Q64, n, rn, s->G, r, rr));  // G = Q Q^+
+  lowdin_kernel<<<grid1(rr), 256, 0, st>>>(s->G, r);
+  VB_CHECK_LAUNCH();
+  VB_TRY(G64(r, n, r, OP_N, s->G, r, rr, OP_N, s->Q64, n, rn, s->Qo, n, rn));  // Qo = (3I - G)/2 Q
+  if (left) {
+    // X = conj(Qo) M  (r x n2);  S = X X^+
+    VB_TRY(G64(r, n2, n1, OP_R, s->Qo, n1, rn, OP_N, M, n2, nm, s->X, n2, (long long)r * n2));
+    VB_TRY(G64(r, r, n2, OP_N, s->X, n2, (long long)r * n2, OP_C, s->X, n2, (long long)r * n2, s->S, r, rr));
+  } else {
+    // X = M Qo^T  (n1 x r);  S = X^+ X
+    VB_TRY(G64(n1, r, n2, OP_N, M, n2, nm, OP_T, s->Qo, n2, rn, s->X, r, (long long)n1 * r));
+    VB_TRY(G64(r, r, n1, OP_C, s->X, r, (long long)n1 * r, OP_N, s->X, r, (long long)n1 * r, s->S, r, rr));
+  }
+  const int kws = std::min(r, kw);
+  VB_TRY(eig_values(r, s->S, kws, s->d_evals, s->eigwS, st));
+  std::vector<double> lam(kws);
+  double nrm = 0.0;
+  VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), s->d_evals, kws * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaMemcpyAsync(&nrm, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  VB_TRY(EigWork::check(r, kws, sizeof(double), s->eigwS, st));
+  prof_end(PH_EIGVAL, st, 0.0);
+  const int k = choose_rank(lam, n, nrm * nrm, std::min(n1, n2), o, disc);
+  prof_begin(PH_EIGVEC, st);
+  VB_TRY(eig_vectors(r, s->S, kws, k, s->d_evals, s->Zr, s->eigwS, st));
+  prof_end(PH_EIGVEC, st, 0.0);
+  prof_begin(PH_SPLITOUT, st);
+  const long long kr = (long long)k * r;
+  if (left) {
+    // Ritz vectors U = Z Qo (k x n1): A = U^T; C = conj(Z) X (k x n2)
+    VB_TRY(G64(k, n1, r, OP_N, s->Zr, r, kr, OP_N, s->Qo, n1, rn, s->U, n1, (long long)k * n1));
+    transpose_kernel<<<grid1((long long)k * n1), 256, 0, st>>>(s->U, k, n1, dstA);
+    VB_CHECK_LAUNCH();
+    VB_TRY(G64(k, n2, r, OP_R, s->Zr, r, kr, OP_N, s->X, n2, (long long)r * n2, dstC, n2, (long long)k * n2));
+    const long long nc = (long long)k * n2;
+    VB_TRY(vec_norm2(dstC, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
+    VB_TRY(vec_scale_inv(dstC, nc, s->d_nrm, st));
+  } else {
+    // Ritz vectors V = Z Qo (k x n2): B = conj(V); C = X Z^T (n1 x k)
+    VB_TRY(G64(k, n2, r, OP_N, s->Zr, r, kr, OP_N, s->Qo, n2, rn, s->U, n2, (long long)k * n2));
+    conj_copy_kernel<<<grid1((long long)k * n2), 256, 0, st>>>(s->U, (long long)k * n2, dstC);
+    VB_CHECK_LAUNCH();
+    VB_TRY(G64(n1, k, r, OP_N, s->X, r, (long long)n1 * r, OP_T, s->Zr, r, kr, dstA, k, (long long)n1 * k));
     const long long nc = (long long)n1 * k;
     VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
     VB_TRY(vec_scale_inv(dstA, nc, s->d_nrm, st));
@@ -583,6 +728,22 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       }
       s->mixw_bytes = mb;
       A2(&s->mixw, mb);
+      const long long nr2 = s->nrho_cap;
+      s->rcap = (int)std::min<long long>(nr2, std::min(opts->m_cap + 1 + 32, 128));
+      const long long rc = std::max(s->rcap, 1);
+      A2((void **)&s->M32, s->theta_cap * sizeof(cf));
+      A2((void **)&s->rho32, (size_t)nr2 * nr2 * sizeof(cf));
+      A2((void **)&s->Q32, (size_t)rc * nr2 * sizeof(cf));
+      A2((void **)&s->Q64, (size_t)rc * nr2 * sizeof(cd));
+      A2((void **)&s->Qo, (size_t)rc * nr2 * sizeof(cd));
+      A2((void **)&s->U, (size_t)rc * nr2 * sizeof(cd));
+      A2((void **)&s->X, (size_t)rc * nr2 * sizeof(cd));
+      A2((void **)&s->G, (size_t)rc * rc * sizeof(cd));
+      A2((void **)&s->S, (size_t)rc * rc * sizeof(cd));
+      A2((void **)&s->Zr, (size_t)rc * rc * sizeof(cd));
+      A2((void **)&s->ev32, (size_t)rc * sizeof(float));
+      A2(&s->eigw32, EigWork::bytes((int)nr2, (int)rc, 4));
+      A2(&s->eigwS, EigWork::bytes((int)rc, (int)rc, 8));
       if (e != VB_OK) return fail_free(e);
     }
   }
@@ -923,7 +1084,7 @@ vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *eva
   cudaStream_t st = (cudaStream_t)stream;
   VB_TRY(eig_values(n, (cd *)rho, k_want, evals, work, st));
   if (k_vec > 0) VB_TRY(eig_vectors(n, (cd *)rho, k_want, k_vec, evals, (cd *)evecs, work, st));
-  return VB_OK;
+  return EigWork::check(n, k_want, sizeof(double), work, st);
 }
 
 }  // extern "C"

@@ -81,3 +81,20 @@ def test_mixed_sweeps_dbss(P):
     m = vm.model_internal_conversion(seed=31, n_modes=5, level_range=(3, 6), n_offdiag=2, n_bilinear=4)
     errs = _run(P, m, 10, 0.5, 24, eps=1e-6)
     assert max(errs) < POP_TOL_MIXED
+
+
+def test_mixed_sweeps_large_split_rayleigh_ritz(P):
+    # bonds up to 32 with d = 12..16: reduced density matrices of dimension
+    # > 192 go through the FP32-eigenvector + FP64 Rayleigh-Ritz split
+    m = vm.model_internal_conversion(seed=41, n_modes=5, level_range=(12, 16), n_offdiag=2, n_bilinear=4)
+    dims = vm.local_dims(m)
+    ts = vm.random_right_canonical_mps(77, dims, 32)
+    mpo = P.Mpo(m)
+    mps = P.Mps(mpo, m_cap=32, dtype=P.VB_MIXED, tensors=ts)
+    ref = otdvp.Tdvp2(otdvp.MPS(ts), ompo.build_mpo(m), otdvp.TdvpOptions(m_max=32, eps=1e-8))
+    assert max(32 * d for d in dims) > 192
+    for _ in range(4):
+        st = mps.sweep(0.5, m_max=32, eps=1e-8, krylov_tol=1e-10)
+        ref.step(0.5)
+        assert st.noconv == 0
+        assert np.max(np.abs(mps.populations() - otdvp.populations(ref.mps))) < POP_TOL_MIXED
