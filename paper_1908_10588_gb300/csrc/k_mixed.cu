@@ -117,7 +117,11 @@ __global__ void zero_cols(float *__restrict__ X, long long rows, long long ld, l
 }
 
 // planar sparse MPO leg: like wapply (k_wapply.cu), with the real and the
-// imaginary parts in separate planes of X and Y
+// imaginary parts in separate planes of X and Y. One thread per output
+// element; consecutive threads take consecutive q, so the re-reads of an
+// input column by the d outputs s' are served from L1. (Staging the inputs
+// in shared memory per block or per slab was measured slower on the largest
+// pair of the internal-conversion workload.)
 __global__ void wapply_planar_kernel(const float *__restrict__ ops, const int *__restrict__ ptr,
                                      const int *__restrict__ ent, int d, int Wp, const float *__restrict__ X,
                                      long long xplane, WStrides xs, float *__restrict__ Y, long long yplane,

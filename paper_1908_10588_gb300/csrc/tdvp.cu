@@ -494,7 +494,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
   return VB_OK;
 }
 
-// Mixed form of the split: the r = min(n, m_max + 33, 128) leading
+// Mixed form of the split: the r = min(n, m_max + 17, 128) leading
 // eigenvectors of rho come from the FP32 eigensolver; the truncation itself
 // is done in FP64 by a Rayleigh-Ritz step on their span: the basis is
 // re-orthonormalised (one Lowdin step), S = Q^+ rho Q is formed from FP64
@@ -509,7 +509,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, cons
   const long long nm = (long long)n1 * n2;
   const cd *M = s->theta;
   const int kw = std::min(n, o.m_max + 1);
-  const int r = std::min(n, std::min(kw + 32, s->rcap));
+  const int r = std::min(n, std::min(kw + 16, s->rcap));
   const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
   auto G64 = [&](int Mm, int Nn, int Kk, int opA, const cd *A, long long lda, long long asz, int opB, const cd *B,
                  long long ldb, long long bsz, cd *C, long long ldc, long long csz) {
