@@ -124,6 +124,13 @@ struct GemmArgsT {
   // element counts of the three buffers (required); every address the
   // kernel forms is checked against them on the host before the launch
   long long a_size, b_size, c_size;
+  // optional split-K (batch must be 1): the K range is cut into chunks of kc
+  // that run as separate CTAs into ws (ws_elems >= chunks * M * N), then an
+  // ordered reduction writes C; used when M x N alone gives too few CTAs
+  cplx<R> *ws;
+  long long ws_elems;
+  // internal: set by gemm() for the chunk launch
+  long long kc, kfull;
 };
 typedef GemmArgsT<double> GemmArgs;
 typedef GemmArgsT<float> GemmArgsF;

@@ -74,10 +74,10 @@ struct EigLayout {
     off_ec = take((size_t)n * cb);
     off_eabs = take((size_t)n * rb);
     off_delta = take((size_t)n * cb);
-    off_p = take((size_t)n * cb);
+    off_p = take((size_t)2 * n * cb);
     off_y = take((size_t)k * n * rb);
     off_lu = take((size_t)k * n * 5 * rb + (size_t)k * n * sizeof(int));
-    off_part = take((size_t)1024 * rb);
+    off_part = take((size_t)2 * 1024 * rb);
     off_bar = take(256);  // barrier count, generation, error flag
     total = o;
   }
@@ -182,6 +182,23 @@ __global__ void tri_finish(const cplx<R> *A, int n, R *tau, R *dg, cplx<R> *ec, 
     tau[n - 2] = 0;
   }
   dg[n - 1] = A[(long long)(n - 1) * n + n - 1].x;
+  tau[n - 1] = 0;
+  delta[0] = mkc<R>(1, 0);
+  for (int j = 0; j + 1 < n; ++j) {
+    R a = sqrt(cabs2(ec[j]));
+    eabs[j] = a;
+    delta[j + 1] = a > R(0) ? cmul(delta[j], mkc<R>(ec[j].x / a, ec[j].y / a)) : delta[j];
+  }
+  eabs[n - 1] = 0;
+}
+
+// after hh_tridiag_fused: dg[0..n-2], ec[0..n-2] are already set; only the
+// last diagonal element is read from A
+template <class R>
+__global__ void tri_finish_fused(const cplx<R> *A, int n, R *tau, R *dg, cplx<R> *ec, R *eabs, cplx<R> *delta) {
+  if (threadIdx.x != 0) return;
+  dg[n - 1] = A[(long long)(n - 1) * n + n - 1].x;
+  tau[n - 2] = 0;
   tau[n - 1] = 0;
   delta[0] = mkc<R>(1, 0);
   for (int j = 0; j + 1 < n; ++j) {
@@ -519,6 +536,188 @@ __global__ void __launch_bounds__(512) hh_tridiag_coop(cplx<R> *A, int n, cplx<R
   }
 }
 
+// ---- 1''. the reduction with one grid barrier per column (look-ahead)
+//
+// Invariant at the top of iteration j: the trailing block A22_j = A[j+1:, j+1:]
+// is stored up to date; every block holds the reflector v_j (shared memory);
+// p_j = tau_j A22_j v_j and the block partials of Re(v_j^+ p_j) are in
+// global memory. After the barrier each block forms w_j = p_j - K_j v_j,
+// recomputes the updated row j+1 on its own and derives reflector j+1 from
+// it, then one fused pass over its rows of A22_j applies the rank-2 update
+// and dots each updated row with v_{j+1}, producing p_{j+1}. Column j+1 and
+// row j+1 are not written back (their content lives in v_{j+1}, dg, ec).
+template <class R>
+__global__ void __launch_bounds__(512) hh_tridiag_fused(cplx<R> *A, int n, cplx<R> *vref, R *tau, R *dg,
+                                                        cplx<R> *ec, cplx<R> *p, R *partial, unsigned int *bar,
+                                                        int *err) {
+  typedef cplx<R> cd;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  cd *vbuf0 = reinterpret_cast<cd *>(fsm);
+  cd *vbuf1 = vbuf0 + n;
+  __shared__ R sh[33];
+  __shared__ R shw[16];
+  __shared__ int sh_ok;
+  __shared__ R s_tau;
+  const unsigned int nb = gridDim.x;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + wib, GW = nb * wpb;
+  cd *vcur = vbuf0, *vnext = vbuf1;
+  // double-buffered p and block partials: iteration j reads one, writes the other
+  cd *pcur = p, *pnext = p + n;
+  R *partcur = partial, *partnext = partial + 1024;
+  // reflector 0 from row 0 (redundantly in every block)
+  {
+    const int m = n - 1;
+    const cd *row0 = A + 1;
+    R s = 0;
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += cabs2(row0[i]);
+    const R sigma = block_sum_all<R>(s, sh);
+    const cd alpha = cconj(row0[0]);
+    R t = 0;
+    cd beta = alpha;
+    if (sigma != R(0)) {
+      const R aa = sqrt(cabs2(alpha));
+      const R nx = sqrt(aa * aa + sigma);
+      const cd ph = aa > R(0) ? mkc<R>(alpha.x / aa, alpha.y / aa) : mkc<R>(1, 0);
+      t = R(1) / (nx * (nx + aa));
+      beta = cscale(ph, -nx);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) vcur[i] = i == 0 ? cscale(ph, aa + nx) : cconj(row0[i]);
+    } else {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) vcur[i] = mkc<R>(0, 0);
+    }
+    if (threadIdx.x == 0) s_tau = t;
+    __syncthreads();
+    if (blockIdx.x == 0) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) vref[1 + i] = vcur[i];
+      if (threadIdx.x == 0) {
+        tau[0] = t;
+        ec[0] = beta;
+        dg[0] = A[0].x;
+      }
+    }
+    // p_0 = t A22_0 v_0
+    R wsum = 0;
+    for (int r = gw; r < m; r += GW) {
+      const cd *row = A + (long long)(1 + r) * n + 1;
+      R sx = 0, sy = 0;
+      for (int c = lane; c < m; c += 32) {
+        const cd a = row[c], v = vcur[c];
+        sx = fma(a.x, v.x, fma(-a.y, v.y, sx));
+        sy = fma(a.x, v.y, fma(a.y, v.x, sy));
+      }
+      sx = warp_sum<R>(sx);
+      sy = warp_sum<R>(sy);
+      if (lane == 0) {
+        const cd pr = mkc<R>(t * sx, t * sy);
+        pcur[r] = pr;
+        wsum += vcur[r].x * pr.x + vcur[r].y * pr.y;
+      }
+    }
+    if (lane == 0) shw[wib] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R b = 0;
+      for (int w = 0; w < wpb; ++w) b += shw[w];
+      partcur[blockIdx.x] = b;
+    }
+  }
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;  // size of A22_j
+    if (!grid_barrier(bar, bar + 1, nb, err, &sh_ok)) return;
+    const R t = s_tau;
+    R tot = 0;
+    for (unsigned int b = 0; b < nb; ++b) tot += partcur[b];
+    const R K = R(0.5) * t * tot;
+    // look-ahead: updated row 0 of A22_j, u(c) = A22_j[0][c] - (v_0 conj(w_c) + w_0 conj(v_c))
+    const cd *row0 = A + (long long)(j + 1) * n + (j + 1);
+    const cd v0 = vcur[0];
+    const cd w0 = csub(pcur[0], cscale(v0, K));
+    const bool last = (j + 1 == n - 2);  // no reflector after this one
+    R s = 0;
+    for (int c = 1 + threadIdx.x; c < m; c += blockDim.x) {
+      const cd vc = vcur[c], wc = csub(pcur[c], cscale(vc, K));
+      const cd u = csub(row0[c], cadd(cmul(v0, cconj(wc)), cmul(w0, cconj(vc))));
+      vnext[c - 1] = cconj(u);  // column j+1 below the diagonal
+      if (c >= 2) s += cabs2(u);
+    }
+    const R sigma = block_sum_all<R>(s, sh);  // includes a __syncthreads: vnext complete
+    const cd u0 = csub(row0[0], cadd(cmul(v0, cconj(w0)), cmul(w0, cconj(v0))));
+    R tn = 0;
+    if (!last) {
+      const cd alpha = vnext[0];
+      cd beta = alpha;
+      if (sigma != R(0)) {
+        const R aa = sqrt(cabs2(alpha));
+        const R nx = sqrt(aa * aa + sigma);
+        const cd ph = aa > R(0) ? mkc<R>(alpha.x / aa, alpha.y / aa) : mkc<R>(1, 0);
+        tn = R(1) / (nx * (nx + aa));
+        beta = cscale(ph, -nx);
+        __syncthreads();
+        if (threadIdx.x == 0) vnext[0] = cscale(ph, aa + nx);
+      } else {
+        __syncthreads();
+        for (int i = threadIdx.x; i < m - 1; i += blockDim.x) vnext[i] = mkc<R>(0, 0);
+      }
+      __syncthreads();
+      if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < m - 1; i += blockDim.x) vref[(long long)(j + 1) * n + (j + 2) + i] = vnext[i];
+        if (threadIdx.x == 0) {
+          tau[j + 1] = tn;
+          ec[j + 1] = beta;
+          dg[j + 1] = u0.x;
+        }
+      }
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+      tau[j + 1] = 0;
+      ec[j + 1] = vnext[0];
+      dg[j + 1] = u0.x;
+    }
+    // fused pass: update rows r >= 1 of A22_j (columns c >= 1) and dot with v_{j+1}
+    R wsum = 0;
+    for (int r = 1 + gw; r < m; r += GW) {
+      cd *row = A + (long long)(j + 1 + r) * n + (j + 1);
+      const cd vr = vcur[r], wr = csub(pcur[r], cscale(vr, K));
+      R sx = 0, sy = 0;
+      for (int c = 1 + lane; c < m; c += 32) {
+        const cd vc = vcur[c], wc = csub(pcur[c], cscale(vc, K));
+        const cd a = csub(row[c], cadd(cmul(vr, cconj(wc)), cmul(wr, cconj(vc))));
+        row[c] = a;
+        if (!last) {
+          const cd v = vnext[c - 1];
+          sx = fma(a.x, v.x, fma(-a.y, v.y, sx));
+          sy = fma(a.x, v.y, fma(a.y, v.x, sy));
+        }
+      }
+      if (!last) {
+        sx = warp_sum<R>(sx);
+        sy = warp_sum<R>(sy);
+        if (lane == 0) {
+          const cd pr = mkc<R>(tn * sx, tn * sy);
+          pnext[r - 1] = pr;
+          wsum += vnext[r - 1].x * pr.x + vnext[r - 1].y * pr.y;
+        }
+      }
+    }
+    if (lane == 0) shw[wib] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R b = 0;
+      for (int w = 0; w < wpb; ++w) b += shw[w];
+      partnext[blockIdx.x] = b;  // read by every block after the next barrier only
+      s_tau = tn;
+    }
+    cd *tv = vcur;
+    vcur = vnext;
+    vnext = tv;
+    cd *tp = pcur;
+    pcur = pnext;
+    pnext = tp;
+    R *tq = partcur;
+    partcur = partnext;
+    partnext = tq;
+  }
+}
+
 // ---- 3'. multisection: one warp per eigenvalue, 32 Sturm counts per step
 template <class R>
 __global__ void multisect_kernel(const R *dg, const R *e, int n, int k_want, R *evals) {
@@ -614,11 +813,21 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
     if (nb > 1024) nb = 1024;
     void *args[] = {(void *)&rho, (void *)&n, (void *)&vref, (void *)&tau, (void *)&dg, (void *)&ec,
                     (void *)&p, (void *)&part, (void *)&bar, (void *)&err};
+    const size_t vsm = (size_t)2 * n * sizeof(C_);
+    if (vsm <= 44 * 1024) {
+      // one barrier per column; the reflectors stay in shared memory
+      VB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)hh_tridiag_fused<R>, dim3(nb), dim3(512), args, vsm, st));
+      count_launch();
+      tri_finish_fused<R><<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
+      VB_CHECK_LAUNCH();
+      goto values;
+    }
     VB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)hh_tridiag_coop<R>, dim3(nb), dim3(512), args, 0, st));
     count_launch();
   }
   tri_finish<R><<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
   VB_CHECK_LAUNCH();
+values:
   multisect_kernel<R><<<(k_want * 32 + 255) / 256, 256, 0, st>>>(dg, eabs, n, k_want, evals);
   VB_CHECK_LAUNCH();
   return VB_OK;

@@ -7,6 +7,8 @@
 // operand views. GB300 has no FP64 tensor-core MMA kind, so this path runs
 // on the FP64 FMA units; the mixed-precision path replaces the H_eff legs
 // with tensor-core products.
+#include <algorithm>
+
 #include "common.h"
 
 namespace vb {
@@ -48,6 +50,8 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
   const C_ *B = g.B + (long long)b * g.sB;
   C_ *C = g.C + (long long)b * g.sC;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  // split-K chunk: only k < Kb of this batch entry
+  const int Kb = g.kc > 0 ? (int)min((long long)g.K, g.kfull - (long long)b * g.kc) : g.K;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const bool a_kfast = (g.opA == OP_N || g.opA == OP_R);
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = mkc<R>(0, 0);
 
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  for (int k0 = 0; k0 < Kb; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       int l = tid + r * NT;
@@ -71,7 +75,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
         kk = l / BM;
       }
       int gi = i0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < g.M && gk < g.K) ? ldA<R>(A, g.opA, g.lda, gi, gk) : mkc<R>(0, 0);
+      As[kk][ii] = (gi < g.M && gk < Kb) ? ldA<R>(A, g.opA, g.lda, gi, gk) : mkc<R>(0, 0);
       int jj;
       if (b_jfast) {
         jj = l % BN;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
       }
       int gj = j0 + jj;
       gk = k0 + kk;
-      Bs[kk][jj] = (gj < g.N && gk < g.K) ? ldB<R>(B, g.opB, g.ldb, gk, gj) : mkc<R>(0, 0);
+      Bs[kk][jj] = (gj < g.N && gk < Kb) ? ldB<R>(B, g.opB, g.ldb, gk, gj) : mkc<R>(0, 0);
     }
     __syncthreads();
 #pragma unroll
@@ -121,6 +125,22 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
   }
 }
 
+// C = alpha sum_b ws[b] + beta C, summed in chunk order (deterministic)
+template <class R>
+__global__ void splitk_reduce(const cplx<R> *__restrict__ ws, int chunks, int M, int N, cplx<R> *C, long long ldc,
+                              cplx<R> alpha, cplx<R> beta) {
+  const long long MN = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
+       e += (long long)gridDim.x * blockDim.x) {
+    cplx<R> s = mkc<R>(0, 0);
+    for (int b = 0; b < chunks; ++b) s = cadd(s, ws[(long long)b * MN + e]);
+    const long long o = (e / N) * ldc + e % N;
+    cplx<R> v = cmul(alpha, s);
+    if (!(beta.x == R(0) && beta.y == R(0))) v = cadd(v, cmul(beta, C[o]));
+    C[o] = v;
+  }
+}
+
 }  // namespace
 
 template <class R>
@@ -142,6 +162,39 @@ vb_status gemm(const GemmArgsT<R> &g, cudaStream_t st) {
       return fail(VB_EINVAL, "zgemm: operand view exceeds its buffer");
     if (g.a_size <= 0 || g.b_size <= 0 || g.c_size <= 0)
       return fail(VB_EINVAL, "zgemm: buffer sizes must be given");
+  }
+  const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.batch;
+  if (g.ws && g.batch == 1 && tiles < 76 && g.K >= 4 * BK * 8) {
+    // split K so that the launch fills the GPU
+    long long chunks = std::min<long long>((152 * 2 + tiles - 1) / tiles, g.K / (8 * BK));
+    chunks = std::max<long long>(chunks, 2);
+    long long kc = (g.K + chunks - 1) / chunks;
+    kc = (kc + BK - 1) / BK * BK;
+    chunks = (g.K + kc - 1) / kc;
+    if (chunks * (long long)g.M * g.N <= g.ws_elems && chunks <= 65535) {
+      GemmArgsT<R> h = g;
+      const bool a_kfast = (g.opA == OP_N || g.opA == OP_R), b_kslow = (g.opB == OP_N || g.opB == OP_R);
+      h.batch = (int)chunks;
+      h.sA = a_kfast ? kc : kc * g.lda;
+      h.sB = b_kslow ? kc * g.ldb : kc;
+      h.C = g.ws;
+      h.ldc = g.N;
+      h.sC = (long long)g.M * g.N;
+      h.alpha = mkc<R>(1, 0);
+      h.beta = mkc<R>(0, 0);
+      h.K = (int)kc;
+      h.kc = kc;
+      h.kfull = g.K;
+      dim3 grid2((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)chunks);
+      zgemm_kernel<R><<<grid2, NT, 0, st>>>(h);
+      VB_CHECK_LAUNCH();
+      const long long MN = (long long)g.M * g.N;
+      long long blocks = std::min<long long>((MN + 255) / 256, 152LL * 8);
+      splitk_reduce<R><<<(int)std::max(1LL, blocks), 256, 0, st>>>(g.ws, (int)chunks, g.M, g.N, g.C, g.ldc, g.alpha,
+                                                                  g.beta);
+      VB_CHECK_LAUNCH();
+      return VB_OK;
+    }
   }
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
   zgemm_kernel<R><<<grid, NT, 0, st>>>(g);

@@ -155,6 +155,8 @@ struct vb_mps {
   cd *Q64 = nullptr, *Qo = nullptr, *G = nullptr, *X = nullptr, *S = nullptr, *Zr = nullptr, *U = nullptr;
   float *ev32 = nullptr;
   void *eigw32 = nullptr, *eigwS = nullptr;
+  cd *skws = nullptr;  // split-K workspace of the Rayleigh-Ritz products
+  long long skws_elems = 0;
   std::vector<void *> owned;
   int center = 0;
 };
@@ -517,6 +519,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, cons
     g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
     g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    g.ws = s->skws; g.ws_elems = s->skws_elems;
     return zgemm(g, st);
   };
   // ---- FP32 eigenvectors of rho
@@ -744,6 +747,8 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       A2((void **)&s->ev32, (size_t)rc * sizeof(float));
       A2(&s->eigw32, EigWork::bytes((int)nr2, (int)rc, 4));
       A2(&s->eigwS, EigWork::bytes((int)rc, (int)rc, 8));
+      s->skws_elems = 48LL * rc * nr2;
+      A2((void **)&s->skws, (size_t)s->skws_elems * sizeof(cd));
       if (e != VB_OK) return fail_free(e);
     }
   }
