@@ -554,6 +554,7 @@ __global__ void __launch_bounds__(512) hh_tridiag_fused(cplx<R> *A, int n, cplx<
   extern __shared__ __align__(16) unsigned char fsm[];
   cd *vbuf0 = reinterpret_cast<cd *>(fsm);
   cd *vbuf1 = vbuf0 + n;
+  cd *wbuf = vbuf1 + n;  // w_j = p_j - K_j v_j of the current column
   __shared__ R sh[33];
   __shared__ R shw[16];
   __shared__ int sh_ok;
@@ -625,17 +626,24 @@ __global__ void __launch_bounds__(512) hh_tridiag_fused(cplx<R> *A, int n, cplx<
     const int m = n - j - 1;  // size of A22_j
     if (!grid_barrier(bar, bar + 1, nb, err, &sh_ok)) return;
     const R t = s_tau;
-    R tot = 0;
-    for (unsigned int b = 0; b < nb; ++b) tot += partcur[b];
-    const R K = R(0.5) * t * tot;
+    if (wib == 0) {
+      R ps = 0;
+      for (unsigned int b = lane; b < nb; b += 32) ps += partcur[b];
+      ps = warp_sum<R>(ps);
+      if (lane == 0) sh[32] = ps;
+    }
+    __syncthreads();
+    const R K = R(0.5) * t * sh[32];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) wbuf[c] = csub(pcur[c], cscale(vcur[c], K));
+    __syncthreads();
     // look-ahead: updated row 0 of A22_j, u(c) = A22_j[0][c] - (v_0 conj(w_c) + w_0 conj(v_c))
     const cd *row0 = A + (long long)(j + 1) * n + (j + 1);
     const cd v0 = vcur[0];
-    const cd w0 = csub(pcur[0], cscale(v0, K));
+    const cd w0 = wbuf[0];
     const bool last = (j + 1 == n - 2);  // no reflector after this one
     R s = 0;
     for (int c = 1 + threadIdx.x; c < m; c += blockDim.x) {
-      const cd vc = vcur[c], wc = csub(pcur[c], cscale(vc, K));
+      const cd vc = vcur[c], wc = wbuf[c];
       const cd u = csub(row0[c], cadd(cmul(v0, cconj(wc)), cmul(w0, cconj(vc))));
       vnext[c - 1] = cconj(u);  // column j+1 below the diagonal
       if (c >= 2) s += cabs2(u);
@@ -676,10 +684,11 @@ __global__ void __launch_bounds__(512) hh_tridiag_fused(cplx<R> *A, int n, cplx<
     R wsum = 0;
     for (int r = 1 + gw; r < m; r += GW) {
       cd *row = A + (long long)(j + 1 + r) * n + (j + 1);
-      const cd vr = vcur[r], wr = csub(pcur[r], cscale(vr, K));
+      const cd vr = vcur[r], wr = wbuf[r];
       R sx = 0, sy = 0;
+#pragma unroll 4
       for (int c = 1 + lane; c < m; c += 32) {
-        const cd vc = vcur[c], wc = csub(pcur[c], cscale(vc, K));
+        const cd vc = vcur[c], wc = wbuf[c];
         const cd a = csub(row[c], cadd(cmul(vr, cconj(wc)), cmul(wr, cconj(vc))));
         row[c] = a;
         if (!last) {
@@ -813,7 +822,7 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
     if (nb > 1024) nb = 1024;
     void *args[] = {(void *)&rho, (void *)&n, (void *)&vref, (void *)&tau, (void *)&dg, (void *)&ec,
                     (void *)&p, (void *)&part, (void *)&bar, (void *)&err};
-    const size_t vsm = (size_t)2 * n * sizeof(C_);
+    const size_t vsm = (size_t)3 * n * sizeof(C_);
     if (vsm <= 44 * 1024) {
       // one barrier per column; the reflectors stay in shared memory
       VB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)hh_tridiag_fused<R>, dim3(nb), dim3(512), args, vsm, st));
