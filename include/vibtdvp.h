@@ -210,12 +210,14 @@ unsigned long long vb_kernel_launches(void);
  * updates, 5 = merge of two sites; sub-phases of 3: 6 = reduced density
  * matrix, 7 = tridiagonal reduction and eigenvalues, 8 = eigenvectors,
  * 9 = new tensors and normalisation; in the mixed form 10 and 11 are the
- * FP32 eigenvalue and eigenvector stages inside 7). heff_flops[c] counts the algorithmic
+ * FP32 eigenvalue and eigenvector stages inside 7; 12, 13, 14 are the
+ * inverse iteration, Gram-Schmidt and back-transformation parts of every
+ * eigenvector stage). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
  * multiply-add is 8, real-times-complex 4, an identity-block add 2). */
 typedef struct {
-  double ms[12];
-  long long calls[12];
+  double ms[16];
+  long long calls[16];
   double heff_flops[2];
 } vb_profile;
 vb_status vb_profile_enable(int on);

@@ -58,11 +58,12 @@ class vb_tdvp_opts(C.Structure):
 
 
 class vb_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 12), ("calls", C.c_longlong * 12), ("heff_flops", C.c_double * 2)]
+    _fields_ = [("ms", C.c_double * 16), ("calls", C.c_longlong * 16), ("heff_flops", C.c_double * 2)]
 
 
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
-          "split_out", "split_eig32_values", "split_eig32_vectors"]
+          "split_out", "split_eig32_values", "split_eig32_vectors", "eigvec_invit", "eigvec_gram_schmidt",
+          "eigvec_backtransform"]
 
 
 class vb_sweep_stats(C.Structure):

@@ -15,6 +15,8 @@
 //     Gram-Schmidt (two passes) so that clustered eigenvalues get an
 //     orthonormal basis of their invariant subspace.
 //  5. Back-transformation z = Q D y.
+#include <algorithm>
+
 #include "common.h"
 
 namespace vb {
@@ -366,6 +368,70 @@ __global__ void cgs2_rows(R *Y, int n, int k) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         R v = yt[i];
         for (int s = 0; s < t; ++s) v -= coef[s] * Y[(long long)s * n + i];
+        yt[i] = v;
+      }
+      __syncthreads();
+    }
+    R ss = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ss += yt[i] * yt[i];
+    ss = block_sum_all<R>(ss, sh);
+    const R inv = ss > R(0) ? R(1) / sqrt(ss) : R(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) yt[i] *= inv;
+    __syncthreads();
+  }
+}
+
+// ---- 4'. block Gram-Schmidt of the rows of Y in panels of BGS_PANEL rows:
+// every panel is projected twice against all earlier rows (multi-block
+// kernels), then orthonormalised in order inside the panel (one block)
+constexpr int BGS_PANEL = 16;
+
+// C[s][p] = <Y_s, Y_{p0+p}>, s < p0, p < b: one warp per pair
+template <class R>
+__global__ void bgs_dots(const R *Y, int n, int p0, int b, R *C) {
+  const int pair = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (pair >= p0 * b) return;
+  const int s = pair / b, p = pair % b;
+  const R *ys = Y + (long long)s * n, *yp = Y + (long long)(p0 + p) * n;
+  R d = 0;
+  for (int i = lane; i < n; i += 32) d += ys[i] * yp[i];
+  d = warp_sum<R>(d);
+  if (lane == 0) C[s * b + p] = d;
+}
+
+// Y_{p0+p} -= sum_{s < p0} C[s][p] Y_s
+template <class R>
+__global__ void bgs_update(R *Y, int n, int p0, int b, const R *C) {
+  const long long total = (long long)b * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e / n), i = (int)(e % n);
+    R v = Y[(long long)(p0 + p) * n + i];
+    for (int s = 0; s < p0; ++s) v -= C[s * b + p] * Y[(long long)s * n + i];
+    Y[(long long)(p0 + p) * n + i] = v;
+  }
+}
+
+// in-panel two-pass Gram-Schmidt and normalisation of rows [p0, p0 + b)
+template <class R>
+__global__ void bgs_panel(R *Y, int n, int p0, int b) {
+  __shared__ R sh[33];
+  __shared__ R coef[BGS_PANEL];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = p0; t < p0 + b; ++t) {
+    R *yt = Y + (long long)t * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int s = p0 + wid; s < t; s += nw) {
+        const R *ys = Y + (long long)s * n;
+        R d = 0;
+        for (int i = lane; i < n; i += 32) d += ys[i] * yt[i];
+        d = warp_sum<R>(d);
+        if (lane == 0) coef[s - p0] = d;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        R v = yt[i];
+        for (int s = p0; s < t; ++s) v -= coef[s - p0] * Y[(long long)s * n + i];
         yt[i] = v;
       }
       __syncthreads();
@@ -862,13 +928,38 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
   // FP32 vectors only seed an FP64 Rayleigh-Ritz step: two rounds suffice there
   const int rounds = sizeof(R) == 8 ? INVIT_ROUNDS : 2;
   for (int r = 0; r < rounds; ++r) {
+    prof_begin(PH_INVIT, st);
     invit_round<R><<<(k_vec + 31) / 32, 32, 0, st>>>(dg, eabs, n, k_vec, evals, Y, lu, piv, r);
     VB_CHECK_LAUNCH();
-    cgs2_rows<R><<<1, 512, 0, st>>>(Y, n, k_vec);
-    VB_CHECK_LAUNCH();
+    prof_end(PH_INVIT, st, 0.0);
+    prof_begin(PH_CGS, st);
+    if (k_vec <= BGS_PANEL) {
+      cgs2_rows<R><<<1, 512, 0, st>>>(Y, n, k_vec);
+      VB_CHECK_LAUNCH();
+    } else {
+      R *C = reinterpret_cast<R *>(w + lay.off_part);  // 2048 reals; p0 * b <= 128 * 16
+      for (int p0 = 0; p0 < k_vec; p0 += BGS_PANEL) {
+        const int b = std::min(BGS_PANEL, k_vec - p0);
+        if (p0 > 0) {
+          for (int pass = 0; pass < 2; ++pass) {
+            const int pairs = p0 * b;
+            bgs_dots<R><<<(pairs * 32 + 255) / 256, 256, 0, st>>>(Y, n, p0, b, C);
+            VB_CHECK_LAUNCH();
+            const long long tot = (long long)b * n;
+            bgs_update<R><<<(int)std::min<long long>((tot + 255) / 256, 152LL * 8), 256, 0, st>>>(Y, n, p0, b, C);
+            VB_CHECK_LAUNCH();
+          }
+        }
+        bgs_panel<R><<<1, 512, 0, st>>>(Y, n, p0, b);
+        VB_CHECK_LAUNCH();
+      }
+    }
+    prof_end(PH_CGS, st, 0.0);
   }
+  prof_begin(PH_BACKT, st);
   backtransform<R><<<k_vec, 256, 0, st>>>(vref, tau, delta, Y, n, evecs);
   VB_CHECK_LAUNCH();
+  prof_end(PH_BACKT, st, 0.0);
   return VB_OK;
 }
 
