@@ -267,14 +267,14 @@ __device__ __forceinline__ double hash_unit(int t, int i) {
 }
 
 template <class R>
-__global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *evals, R *Y, R *lu,
-                            int *piv, int round) {
+__global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *evals, R *Y, R *lu, int *piv, int round) {
+  // the LU factors of all vectors are interleaved (element i of vector t at
+  // i * k_vec + t) so that the threads of a warp touch consecutive addresses
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k_vec) return;
   R *y = Y + (long long)t * n;
-  R *dl = lu + (long long)t * n * 4;
-  R *dd = dl + n, *du = dd + n, *du2 = du + n;
-  int *pv = piv + (long long)t * n;
+  const long long K = k_vec;
+  R *dl = lu, *dd = lu + (long long)n * K, *du = lu + 2LL * n * K, *du2 = lu + 3LL * n * K;
   R tnorm = 0;
   for (int i = 0; i < n; ++i)
     tnorm = fmax(tnorm, fabs(dg[i]) + (i > 0 ? e[i - 1] : R(0)) + (i + 1 < n ? e[i] : R(0)));
@@ -283,54 +283,57 @@ __global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *
   if (round == 0) {
     // factor T' - lam I = P L U once
     for (int i = 0; i < n; ++i) {
-      dd[i] = dg[i] - lam;
+      dd[i * K + t] = dg[i] - lam;
       if (i + 1 < n) {
-        dl[i] = e[i];
-        du[i] = e[i];
+        dl[i * K + t] = e[i];
+        du[i * K + t] = e[i];
       }
-      du2[i] = 0;
-      pv[i] = 0;
+      du2[i * K + t] = 0;
+      piv[i * K + t] = 0;
     }
     for (int i = 0; i + 1 < n; ++i) {
-      if (fabs(dd[i]) >= fabs(dl[i])) {
-        if (dd[i] == R(0)) dd[i] = pivmin;
-        R l = dl[i] / dd[i];
-        dl[i] = l;
-        dd[i + 1] -= l * du[i];
-        pv[i] = 0;
+      R ddi = dd[i * K + t], dli = dl[i * K + t];
+      if (fabs(ddi) >= fabs(dli)) {
+        if (ddi == R(0)) ddi = pivmin;
+        const R l = dli / ddi;
+        dd[i * K + t] = ddi;
+        dl[i * K + t] = l;
+        dd[(i + 1) * K + t] -= l * du[i * K + t];
+        piv[i * K + t] = 0;
       } else {
-        R l = dd[i] / dl[i];
-        dd[i] = dl[i];
-        dl[i] = l;
-        R tmp = du[i];
-        du[i] = dd[i + 1];
-        dd[i + 1] = tmp - l * dd[i + 1];
+        const R l = ddi / dli;
+        dd[i * K + t] = dli;
+        dl[i * K + t] = l;
+        const R tmp = du[i * K + t];
+        const R dd1 = dd[(i + 1) * K + t];
+        du[i * K + t] = dd1;
+        dd[(i + 1) * K + t] = tmp - l * dd1;
         if (i + 2 < n) {
-          du2[i] = du[i + 1];
-          du[i + 1] = -l * du[i + 1];
+          du2[i * K + t] = du[(i + 1) * K + t];
+          du[(i + 1) * K + t] = -l * du[(i + 1) * K + t];
         }
-        pv[i] = 1;
+        piv[i * K + t] = 1;
       }
     }
-    if (dd[n - 1] == R(0)) dd[n - 1] = pivmin;
+    if (dd[(n - 1) * K + t] == R(0)) dd[(n - 1) * K + t] = pivmin;
     for (int i = 0; i < n; ++i) y[i] = R(hash_unit(t, i));
   }
   // solve (T' - lam I) y_new = y
   for (int i = 0; i + 1 < n; ++i) {
-    if (pv[i]) {
-      R tmp = y[i];
+    if (piv[i * K + t]) {
+      const R tmp = y[i];
       y[i] = y[i + 1];
       y[i + 1] = tmp;
     }
-    y[i + 1] -= dl[i] * y[i];
+    y[i + 1] -= dl[i * K + t] * y[i];
   }
   // back substitution; the system is linear, so the whole vector may be
   // rescaled whenever a component grows large (near-singular shifts)
   for (int i = n - 1; i >= 0; --i) {
     R v = y[i];
-    if (i + 1 < n) v -= du[i] * y[i + 1];
-    if (i + 2 < n) v -= du2[i] * y[i + 2];
-    v /= dd[i];
+    if (i + 1 < n) v -= du[i * K + t] * y[i + 1];
+    if (i + 2 < n) v -= du2[i * K + t] * y[i + 2];
+    v /= dd[i * K + t];
     y[i] = v;
     if (fabs(v) > Eps<R>::big)
       for (int q = 0; q < n; ++q) y[q] *= R(1) / Eps<R>::big;

@@ -157,6 +157,9 @@ struct vb_mps {
   void *eigw32 = nullptr, *eigwS = nullptr;
   cd *skws = nullptr;  // split-K workspace of the Rayleigh-Ritz products
   long long skws_elems = 0;
+  // mixed form: environment updates in complex FP32
+  cf *envA32 = nullptr, *envE32 = nullptr, *envO32 = nullptr, *envT1 = nullptr, *envT2 = nullptr;
+  long long env_site_cap = 0, env_blk_cap = 0;
   std::vector<void *> owned;
   int center = 0;
 };
@@ -232,58 +235,60 @@ vb_status heff1_fp64(const vb_mpo *mpo, int j, int mL, int mR, const cd *L, cons
 }
 
 // ---- environment updates (the blocks of Eq. one-site Hamiltonian 1)
-vb_status env_left(const vb_mpo *mpo, int p, int mL, int mR, const cd *L, const cd *A, cd *Lnew,
-                   cd *T1, cd *T2, long long t_cap, cudaStream_t st) {
+template <class R>
+vb_status env_left(const vb_mpo *mpo, int p, int mL, int mR, const cplx<R> *L, const cplx<R> *A, cplx<R> *Lnew,
+                   cplx<R> *T1, cplx<R> *T2, long long t_cap, cudaStream_t st) {
   const MpoSite &S = mpo->sites[p];
   const long long d = S.d, wL = S.wl, wR = S.wr;
   // T1[(x w), (s y)] = L[(x w), z] A[z, (s y)]
-  GemmArgs g{};
+  GemmArgsT<R> g{};
   g.M = (int)(mL * wL); g.N = (int)(d * mR); g.K = mL; g.batch = 1;
   g.opA = OP_N; g.opB = OP_N;
   g.A = L; g.lda = mL; g.B = A; g.ldb = g.N; g.C = T1; g.ldc = g.N;
-  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
+  g.alpha = mkc<R>(1, 0); g.beta = mkc<R>(0, 0);
   g.a_size = mL * wL * mL; g.b_size = mL * d * mR; g.c_size = t_cap;
-  VB_TRY(zgemm(g, st));
+  VB_TRY(gemm<R>(g, st));
   // T2[x][s'][v][y] = W applied to T1[x][w][s][y]
-  VB_TRY(wapply(S, 0, T1, WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), t_cap, T2,
+  VB_TRY(wapply<R>(S, 0, T1, WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), t_cap, T2,
                 WS(/*p*/ d * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, mL, mR, st));
   // Lnew[y', (v y)] = sum_{(x s')} conj(A[(x s'), y']) T2[(x s'), (v y)]
-  GemmArgs h{};
+  GemmArgsT<R> h{};
   h.M = mR; h.N = (int)(wR * mR); h.K = (int)(mL * d); h.batch = 1;
   h.opA = OP_C; h.opB = OP_N;
   h.A = A; h.lda = mR; h.B = T2; h.ldb = h.N; h.C = Lnew; h.ldc = h.N;
-  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
+  h.alpha = mkc<R>(1, 0); h.beta = mkc<R>(0, 0);
   h.a_size = mL * d * mR; h.b_size = t_cap; h.c_size = (long long)mR * wR * mR;
-  return zgemm(h, st);
+  return gemm<R>(h, st);
 }
 
-vb_status env_right(const vb_mpo *mpo, int p, int mL, int mR, const cd *R, const cd *B, cd *Rnew,
-                    cd *T1, cd *T2, long long t_cap, cudaStream_t st) {
+template <class Rt>
+vb_status env_right(const vb_mpo *mpo, int p, int mL, int mR, const cplx<Rt> *R, const cplx<Rt> *B, cplx<Rt> *Rnew,
+                    cplx<Rt> *T1, cplx<Rt> *T2, long long t_cap, cudaStream_t st) {
   const MpoSite &S = mpo->sites[p];
   const long long d = S.d, wL = S.wl, wR = S.wr;
   // T1[(a t)][v][y] = sum_z B[(a t), z] R[y, v, z]   (batched over v)
-  GemmArgs g{};
+  GemmArgsT<Rt> g{};
   g.M = (int)(mL * d); g.N = mR; g.K = mR; g.batch = (int)wR;
   g.opA = OP_N; g.opB = OP_T;
   g.A = B; g.lda = mR; g.sA = 0;
   g.B = R; g.ldb = wR * mR; g.sB = mR;
   g.C = T1; g.ldc = wR * mR; g.sC = mR;
-  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
+  g.alpha = mkc<Rt>(1, 0); g.beta = mkc<Rt>(0, 0);
   g.a_size = mL * d * mR; g.b_size = (long long)mR * wR * mR; g.c_size = t_cap;
-  VB_TRY(zgemm(g, st));
+  VB_TRY(gemm<Rt>(g, st));
   // T2[a][w][t'][y] = sum_{t, v} W[w, t', t, v] T1[a][t][v][y]
-  VB_TRY(wapply(S, 1, T1, WS(/*p*/ d * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, T2,
+  VB_TRY(wapply<Rt>(S, 1, T1, WS(/*p*/ d * wR * mR, /*w*/ mR, /*s*/ wR * mR, /*q*/ 1), t_cap, T2,
                 WS(/*p*/ wL * d * mR, /*w*/ d * mR, /*s*/ mR, /*q*/ 1), t_cap, mL, mR, st));
   // Rnew[a', w, a] = sum_k conj(B[a', k]) T2[a, w, k]   (batched over w)
-  GemmArgs h{};
+  GemmArgsT<Rt> h{};
   h.M = mL; h.N = mL; h.K = (int)(d * mR); h.batch = (int)wL;
   h.opA = OP_R; h.opB = OP_T;
   h.A = B; h.lda = d * mR; h.sA = 0;
   h.B = T2; h.ldb = wL * d * mR; h.sB = d * mR;
   h.C = Rnew; h.ldc = wL * mL; h.sC = mL;
-  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
+  h.alpha = mkc<Rt>(1, 0); h.beta = mkc<Rt>(0, 0);
   h.a_size = mL * d * mR; h.b_size = t_cap; h.c_size = (long long)mL * wL * mL;
-  return zgemm(h, st);
+  return gemm<Rt>(h, st);
 }
 
 // ---- operator applied inside the Krylov loop
@@ -606,6 +611,31 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, cons
   return VB_OK;
 }
 
+// environment update of the sweep: FP64, or complex FP32 in the mixed form
+// (inputs converted from and the result converted back to the FP64 storage)
+vb_status env_update(vb_mps *s, bool left, int p, int mL, int mR, const cd *E, const cd *A, cd *Enew) {
+  const vb_mpo *mpo = s->mpo;
+  if (s->dtype != VB_MIXED) {
+    if (left) return env_left<double>(mpo, p, mL, mR, E, A, Enew, s->T1, s->T2, s->inter_cap, s->st);
+    return env_right<double>(mpo, p, mL, mR, E, A, Enew, s->T1, s->T2, s->inter_cap, s->st);
+  }
+  const MpoSite &S = mpo->sites[p];
+  const long long na = (long long)mL * S.d * mR;
+  const long long ne = left ? (long long)mL * S.wl * mL : (long long)mR * S.wr * mR;
+  const long long no = left ? (long long)mR * S.wr * mR : (long long)mL * S.wl * mL;
+  c64_to_c32<<<grid1(na), 256, 0, s->st>>>(A, s->envA32, na);
+  VB_CHECK_LAUNCH();
+  c64_to_c32<<<grid1(ne), 256, 0, s->st>>>(E, s->envE32, ne);
+  VB_CHECK_LAUNCH();
+  if (left)
+    VB_TRY(env_left<float>(mpo, p, mL, mR, s->envE32, s->envA32, s->envO32, s->envT1, s->envT2, s->inter_cap, s->st));
+  else
+    VB_TRY(env_right<float>(mpo, p, mL, mR, s->envE32, s->envA32, s->envO32, s->envT1, s->envT2, s->inter_cap, s->st));
+  c32_to_c64<<<grid1(no), 256, 0, s->st>>>(s->envO32, Enew, no);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
 vb_status merge(vb_mps *s, int i) {
   const int mL = s->bond[i], mM = s->bond[i + 1], mR = s->bond[i + 2];
   const int d1 = s->dims[i], d2 = s->dims[i + 1];
@@ -749,6 +779,17 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       A2(&s->eigwS, EigWork::bytes((int)rc, (int)rc, 8));
       s->skws_elems = 48LL * rc * nr2;
       A2((void **)&s->skws, (size_t)s->skws_elems * sizeof(cd));
+      for (int p = 0; p <= n; ++p) {
+        const int w = p < n ? mpo->sites[p].wl : 1;
+        s->env_blk_cap = std::max<long long>(s->env_blk_cap, (long long)s->bcap[p] * w * s->bcap[p]);
+        if (p < n)
+          s->env_site_cap = std::max<long long>(s->env_site_cap, (long long)s->bcap[p] * s->dims[p] * s->bcap[p + 1]);
+      }
+      A2((void **)&s->envA32, (size_t)s->env_site_cap * sizeof(cf));
+      A2((void **)&s->envE32, (size_t)s->env_blk_cap * sizeof(cf));
+      A2((void **)&s->envO32, (size_t)s->env_blk_cap * sizeof(cf));
+      A2((void **)&s->envT1, (size_t)s->inter_cap * sizeof(cf));
+      A2((void **)&s->envT2, (size_t)s->inter_cap * sizeof(cf));
       if (e != VB_OK) return fail_free(e);
     }
   }
@@ -773,8 +814,8 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
 // build R[p] for p = n-1 .. 1 from the right-canonical tensors
 vb_status build_right_envs(vb_mps *s) {
   for (int p = s->n - 1; p >= 1; --p)
-    VB_TRY(env_right(s->mpo, p, s->bond[p], s->bond[p + 1], s->R[p + 1], s->A[p], s->R[p], s->T1,
-                     s->T2, s->inter_cap, s->st));
+    VB_TRY(env_right<double>(s->mpo, p, s->bond[p], s->bond[p + 1], s->R[p + 1], s->A[p], s->R[p], s->T1,
+                             s->T2, s->inter_cap, s->st));
   return VB_OK;
 }
 
@@ -931,7 +972,7 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
     st.discarded_weight += disc;
     s->bond[i + 1] = k;
     prof_begin(PH_ENV, s->st);
-    VB_TRY(env_left(mpo, i, mL, k, s->L[i], s->A[i], s->L[i + 1], s->T1, s->T2, s->inter_cap, s->st));
+    VB_TRY(env_update(s, true, i, mL, k, s->L[i], s->A[i], s->L[i + 1]));
     prof_end(PH_ENV, s->st, 0.0);
     if (i + 2 < n) {
       HeffOp op1{0, i + 1, k, mR, s->L[i + 1], s->R[i + 2]};
@@ -954,8 +995,7 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
     st.discarded_weight += disc;
     s->bond[i + 1] = k;
     prof_begin(PH_ENV, s->st);
-    VB_TRY(env_right(mpo, i + 1, k, mR, s->R[i + 2], s->A[i + 1], s->R[i + 1], s->T1, s->T2, s->inter_cap,
-                     s->st));
+    VB_TRY(env_update(s, false, i + 1, k, mR, s->R[i + 2], s->A[i + 1], s->R[i + 1]));
     prof_end(PH_ENV, s->st, 0.0);
     if (i > 0) {
       HeffOp op1{0, i, mL, k, s->L[i], s->R[i + 1]};
@@ -1062,7 +1102,7 @@ vb_status vb_env_left_update(const vb_mpo *mpo, int p, int mL, int mR, const dou
     return fail(VB_EINVAL, "vb_env_left_update: bad argument");
   VB_TRY(mpo_upload(mpo));
   size_t half = vb_env_work_elems(mpo, p, mL, mR) / 2;
-  return env_left(mpo, p, mL, mR, (const cd *)L, (const cd *)A, (cd *)Lnew, (cd *)work, (cd *)work + half,
+  return env_left<double>(mpo, p, mL, mR, (const cd *)L, (const cd *)A, (cd *)Lnew, (cd *)work, (cd *)work + half,
                   (long long)half, (cudaStream_t)stream);
 }
 
@@ -1072,7 +1112,7 @@ vb_status vb_env_right_update(const vb_mpo *mpo, int p, int mL, int mR, const do
     return fail(VB_EINVAL, "vb_env_right_update: bad argument");
   VB_TRY(mpo_upload(mpo));
   size_t half = vb_env_work_elems(mpo, p, mL, mR) / 2;
-  return env_right(mpo, p, mL, mR, (const cd *)R, (const cd *)B, (cd *)Rnew, (cd *)work, (cd *)work + half,
+  return env_right<double>(mpo, p, mL, mR, (const cd *)R, (const cd *)B, (cd *)Rnew, (cd *)work, (cd *)work + half,
                    (long long)half, (cudaStream_t)stream);
 }
 
