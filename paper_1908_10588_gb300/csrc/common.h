@@ -144,7 +144,7 @@ inline vb_status zgemm(const GemmArgs &g, cudaStream_t st) { return gemm<double>
 struct MpoBlock {
   int win, wout;
   int ident;   // operator is the identity
-  int op_off;  // offset (in doubles) of the d x d operator [s_out][s_in]
+  int op_off;  // row-pointer base of the operator in csr_ptr (non-identity blocks)
 };
 
 struct MpoSite {
@@ -152,10 +152,17 @@ struct MpoSite {
   std::vector<double> dense;  // [wl][d][d][wr]
   std::vector<MpoBlock> blocks;
   std::vector<double> ops;  // concatenated non-identity operators
+  // the same operators row-compressed: for a block whose entry carries
+  // off = b, rows so have nonzeros csr_col/val[csr_ptr[b + so] .. csr_ptr[b + so + 1])
+  std::vector<int> csr_ptr, csr_col;
+  std::vector<double> csr_val;
   // device copies: operators, and for each direction a CSR over the produced
-  // bond index: entries (consumed index, ident, op_off)
+  // bond index: entries (consumed index, ident, operator row-pointer base)
   double *d_ops = nullptr;
   float *d_ops32 = nullptr;
+  int *d_csr_ptr = nullptr, *d_csr_col = nullptr;
+  double *d_csr_val = nullptr;
+  float *d_csr_val32 = nullptr;
   int *d_fwd_ptr = nullptr, *d_fwd_ent = nullptr;  // produce w_out from w_in
   int *d_bwd_ptr = nullptr, *d_bwd_ent = nullptr;  // produce w_in from w_out
   long long nnz_ops = 0;                           // non-identity blocks

@@ -122,7 +122,8 @@ __global__ void zero_cols(float *__restrict__ X, long long rows, long long ld, l
 // input column by the d outputs s' are served from L1. (Staging the inputs
 // in shared memory per block or per slab was measured slower on the largest
 // pair of the internal-conversion workload.)
-__global__ void wapply_planar_kernel(const float *__restrict__ ops, const int *__restrict__ ptr,
+__global__ void wapply_planar_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                     const float *__restrict__ val, const int *__restrict__ ptr,
                                      const int *__restrict__ ent, int d, int Wp, const float *__restrict__ X,
                                      long long xplane, WStrides xs, float *__restrict__ Y, long long yplane,
                                      WStrides ys, int P, int Q) {
@@ -144,13 +145,11 @@ __global__ void wapply_planar_kernel(const float *__restrict__ ops, const int *_
         ax += xw[so * xs.s];
         ay += xw[so * xs.s + xplane];
       } else {
-        const float *o = ops + off + so * d;
-        for (int s = 0; s < d; ++s) {
-          const float c = o[s];
-          if (c != 0.f) {
-            ax = fmaf(c, xw[s * xs.s], ax);
-            ay = fmaf(c, xw[s * xs.s + xplane], ay);
-          }
+        for (int k = rp[off + so]; k < rp[off + so + 1]; ++k) {
+          const float c = val[k];
+          const float *xs_ = xw + col[k] * xs.s;
+          ax = fmaf(c, xs_[0], ax);
+          ay = fmaf(c, xs_[xplane], ay);
         }
       }
     }
@@ -170,8 +169,8 @@ vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStr
   if (xmax >= x_size || ymax >= y_size) return fail(VB_EINVAL, "wapply_planar: view exceeds its buffer");
   long long blocks = (total + 255) / 256;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
-  wapply_planar_kernel<<<(int)blocks, 256, 0, st>>>(S.d_ops32, S.d_fwd_ptr, S.d_fwd_ent, d, Wp, X, xplane, xs, Y,
-                                                    yplane, ys, P, Q);
+  wapply_planar_kernel<<<(int)blocks, 256, 0, st>>>(S.d_csr_ptr, S.d_csr_col, S.d_csr_val32, S.d_fwd_ptr,
+                                                    S.d_fwd_ent, d, Wp, X, xplane, xs, Y, yplane, ys, P, Q);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

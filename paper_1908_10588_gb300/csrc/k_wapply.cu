@@ -1,4 +1,6 @@
 // Sparse application of one MPO site tensor (Eq. MPO) to a stacked tensor.
+// The operators of the nonzero blocks are themselves sparse (q tridiagonal,
+// b^+b diagonal, |i><j| a single entry) and are read row-compressed.
 //
 // The vibronic MPO is block sparse: most (w_in, w_out) blocks of a site are
 // zero and many of the rest are identities that only carry a channel
@@ -11,9 +13,10 @@ namespace vb {
 namespace {
 
 template <class R>
-__global__ void wapply_kernel(const R *__restrict__ ops, const int *__restrict__ ptr,
-                              const int *__restrict__ ent, int d, int Wp, const cplx<R> *__restrict__ X,
-                              WStrides xs, cplx<R> *__restrict__ Y, WStrides ys, int P, int Q) {
+__global__ void wapply_kernel(const int *__restrict__ rp, const int *__restrict__ col, const R *__restrict__ val,
+                              const int *__restrict__ ptr, const int *__restrict__ ent, int d, int Wp,
+                              const cplx<R> *__restrict__ X, WStrides xs, cplx<R> *__restrict__ Y, WStrides ys,
+                              int P, int Q) {
   long long total = (long long)P * d * Wp * Q;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -33,14 +36,11 @@ __global__ void wapply_kernel(const R *__restrict__ ops, const int *__restrict__
         ax += v.x;
         ay += v.y;
       } else {
-        const R *o = ops + off + so * d;
-        for (int s = 0; s < d; ++s) {
-          R c = o[s];
-          if (c != R(0)) {
-            cplx<R> v = xw[s * xs.s];
-            ax = fma(c, v.x, ax);
-            ay = fma(c, v.y, ay);
-          }
+        for (int k = rp[off + so]; k < rp[off + so + 1]; ++k) {
+          const R c = val[k];
+          const cplx<R> v = xw[col[k] * xs.s];
+          ax = fma(c, v.x, ax);
+          ay = fma(c, v.y, ay);
         }
       }
     }
@@ -70,12 +70,13 @@ vb_status wapply(const MpoSite &site, int dir, const cplx<R> *X, WStrides xs, lo
   int threads = 256;
   long long blocks = (total + threads - 1) / threads;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
-  const R *ops;
+  const R *vals;
   if constexpr (sizeof(R) == 8)
-    ops = reinterpret_cast<const R *>(site.d_ops);
+    vals = reinterpret_cast<const R *>(site.d_csr_val);
   else
-    ops = reinterpret_cast<const R *>(site.d_ops32);
-  wapply_kernel<R><<<(int)blocks, threads, 0, st>>>(ops, dir == 0 ? site.d_fwd_ptr : site.d_bwd_ptr,
+    vals = reinterpret_cast<const R *>(site.d_csr_val32);
+  wapply_kernel<R><<<(int)blocks, threads, 0, st>>>(site.d_csr_ptr, site.d_csr_col, vals,
+                                                 dir == 0 ? site.d_fwd_ptr : site.d_bwd_ptr,
                                                  dir == 0 ? site.d_fwd_ent : site.d_bwd_ent, d, Wp,
                                                  X, xs, Y, ys, P, Q);
   VB_CHECK_LAUNCH();

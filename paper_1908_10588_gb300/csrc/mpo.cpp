@@ -274,8 +274,19 @@ vb_status mpo_build(const vb_model *m, vb_mpo **out) {
       B.ident = ident ? 1 : 0;
       B.op_off = -1;
       if (!ident) {
-        B.op_off = (int)S.ops.size();
+        B.op_off = (int)S.csr_ptr.size();  // row-pointer base of this operator
         S.ops.insert(S.ops.end(), op.begin(), op.end());
+        for (int a = 0; a < d; ++a) {
+          S.csr_ptr.push_back((int)S.csr_col.size());
+          for (int b2 = 0; b2 < d; ++b2) {
+            const double v = op[(size_t)a * d + b2];
+            if (v != 0.0) {
+              S.csr_col.push_back(b2);
+              S.csr_val.push_back(v);
+            }
+          }
+        }
+        S.csr_ptr.push_back((int)S.csr_col.size());
         S.nnz_ops++;
       } else {
         S.n_ident++;
@@ -336,6 +347,11 @@ vb_status mpo_upload(const vb_mpo *cmpo) {
     VB_TRY(up(S.ops.data(), S.ops.size() * sizeof(double), (void **)&S.d_ops));
     std::vector<float> ops32(S.ops.begin(), S.ops.end());
     VB_TRY(up(ops32.data(), ops32.size() * sizeof(float), (void **)&S.d_ops32));
+    VB_TRY(up(S.csr_ptr.data(), S.csr_ptr.size() * sizeof(int), (void **)&S.d_csr_ptr));
+    VB_TRY(up(S.csr_col.data(), S.csr_col.size() * sizeof(int), (void **)&S.d_csr_col));
+    VB_TRY(up(S.csr_val.data(), S.csr_val.size() * sizeof(double), (void **)&S.d_csr_val));
+    std::vector<float> val32(S.csr_val.begin(), S.csr_val.end());
+    VB_TRY(up(val32.data(), val32.size() * sizeof(float), (void **)&S.d_csr_val32));
     for (int dir = 0; dir < 2; ++dir) {
       int np = dir == 0 ? S.wr : S.wl;
       std::vector<int> ptr(np + 1, 0), ent;
