@@ -7,11 +7,12 @@
 // 128-byte-swizzled shared memory (boxes of 32 K-elements x 128 rows) in a
 // STAGES-deep ring guarded by mbarriers; one elected thread issues
 // tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8 per instruction) into a
-// TMEM accumulator of 128 lanes x 128 columns; four epilogue warps read the
-// accumulator with tcgen05.ld and store it. Complex products use the real
+// TMEM accumulator of 128 lanes x 128 columns; eight epilogue warps (two per
+// TMEM lane quarter, one column half each) read the accumulator with
+// tcgen05.ld and store it. Complex products use the real
 // embedding prepared by the caller (k_mixed.cu).
 //
-// Split-TF32 (SPLIT = true): while the main loop runs, the four epilogue
+// Split-TF32 (SPLIT = true): while the main loop runs, the eight epilogue
 // warps split every landed stage x = hi + lo with hi = x truncated to tf32
 // (written back in place, so it is exact in tf32) and lo = x - hi (exact in
 // fp32) into a second buffer; the MMA thread then issues three products per
@@ -32,7 +33,8 @@ namespace vb {
 namespace {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;
-constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..5 epilogue
+constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 split + epilogue
+constexpr int TC_EPI_THREADS = TC_THREADS - 64;
 constexpr uint32_t TC_STAGE_A = TC_BM * TC_BK * 4, TC_STAGE_B = TC_BN * TC_BK * 4;
 constexpr uint32_t TC_TMEM_COLS = 128;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;  // polls before a wait is declared failed
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&ready[s], 4);
+      mbar_init(&ready[s], TC_EPI_THREADS / 32);
     }
     mbar_init(accum, 1);
     *abort_flag = 0;
@@ -216,13 +218,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mma_commit(accum);
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const int m = m0 + row;
     if constexpr (SPLIT) {
       // split every landed stage into hi (in place) and lo
-      const int t = threadIdx.x - 64;  // 0..127
+      const int t = threadIdx.x - 64;  // 0 .. TC_EPI_THREADS - 1
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % TC_STAGES;
         const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
@@ -235,13 +238,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t *b = reinterpret_cast<uint32_t *>(sB + s * TC_STAGE_B);
         uint32_t *bl = reinterpret_cast<uint32_t *>(sBlo + s * TC_STAGE_B);
 #pragma unroll 4
-        for (int j = t; j < (int)(TC_STAGE_A / 4); j += 128) {
+        for (int j = t; j < (int)(TC_STAGE_A / 4); j += TC_EPI_THREADS) {
           const uint32_t x = a[j], h = x & 0xFFFFE000u;
           al[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
           a[j] = h;
         }
 #pragma unroll 4
-        for (int j = t; j < (int)(TC_STAGE_B / 4); j += 128) {
+        for (int j = t; j < (int)(TC_STAGE_B / 4); j += TC_EPI_THREADS) {
           const uint32_t x = b[j], h = x & 0xFFFFE000u;
           bl[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
           b[j] = h;
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (ok && !*abort_flag) {
       float v[32];
 #pragma unroll 1
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      for (int c0 = half * (TC_BN / 2); c0 < (half + 1) * (TC_BN / 2); c0 += 32) {
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
         uint32_t r[32];
         asm volatile(
