@@ -267,14 +267,14 @@ __device__ __forceinline__ double hash_unit(int t, int i) {
 }
 
 template <class R>
-__global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *evals, R *Y, R *lu, int *piv, int round) {
-  // the LU factors of all vectors are interleaved (element i of vector t at
-  // i * k_vec + t) so that the threads of a warp touch consecutive addresses
+__global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *evals, R *Y, R *lu,
+                            int *piv, int round) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k_vec) return;
   R *y = Y + (long long)t * n;
-  const long long K = k_vec;
-  R *dl = lu, *dd = lu + (long long)n * K, *du = lu + 2LL * n * K, *du2 = lu + 3LL * n * K;
+  R *dl = lu + (long long)t * n * 4;
+  R *dd = dl + n, *du = dd + n, *du2 = du + n;
+  int *pv = piv + (long long)t * n;
   R tnorm = 0;
   for (int i = 0; i < n; ++i)
     tnorm = fmax(tnorm, fabs(dg[i]) + (i > 0 ? e[i - 1] : R(0)) + (i + 1 < n ? e[i] : R(0)));
@@ -283,57 +283,54 @@ __global__ void invit_round(const R *dg, const R *e, int n, int k_vec, const R *
   if (round == 0) {
     // factor T' - lam I = P L U once
     for (int i = 0; i < n; ++i) {
-      dd[i * K + t] = dg[i] - lam;
+      dd[i] = dg[i] - lam;
       if (i + 1 < n) {
-        dl[i * K + t] = e[i];
-        du[i * K + t] = e[i];
+        dl[i] = e[i];
+        du[i] = e[i];
       }
-      du2[i * K + t] = 0;
-      piv[i * K + t] = 0;
+      du2[i] = 0;
+      pv[i] = 0;
     }
     for (int i = 0; i + 1 < n; ++i) {
-      R ddi = dd[i * K + t], dli = dl[i * K + t];
-      if (fabs(ddi) >= fabs(dli)) {
-        if (ddi == R(0)) ddi = pivmin;
-        const R l = dli / ddi;
-        dd[i * K + t] = ddi;
-        dl[i * K + t] = l;
-        dd[(i + 1) * K + t] -= l * du[i * K + t];
-        piv[i * K + t] = 0;
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        if (dd[i] == R(0)) dd[i] = pivmin;
+        R l = dl[i] / dd[i];
+        dl[i] = l;
+        dd[i + 1] -= l * du[i];
+        pv[i] = 0;
       } else {
-        const R l = ddi / dli;
-        dd[i * K + t] = dli;
-        dl[i * K + t] = l;
-        const R tmp = du[i * K + t];
-        const R dd1 = dd[(i + 1) * K + t];
-        du[i * K + t] = dd1;
-        dd[(i + 1) * K + t] = tmp - l * dd1;
+        R l = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = l;
+        R tmp = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = tmp - l * dd[i + 1];
         if (i + 2 < n) {
-          du2[i * K + t] = du[(i + 1) * K + t];
-          du[(i + 1) * K + t] = -l * du[(i + 1) * K + t];
+          du2[i] = du[i + 1];
+          du[i + 1] = -l * du[i + 1];
         }
-        piv[i * K + t] = 1;
+        pv[i] = 1;
       }
     }
-    if (dd[(n - 1) * K + t] == R(0)) dd[(n - 1) * K + t] = pivmin;
+    if (dd[n - 1] == R(0)) dd[n - 1] = pivmin;
     for (int i = 0; i < n; ++i) y[i] = R(hash_unit(t, i));
   }
   // solve (T' - lam I) y_new = y
   for (int i = 0; i + 1 < n; ++i) {
-    if (piv[i * K + t]) {
-      const R tmp = y[i];
+    if (pv[i]) {
+      R tmp = y[i];
       y[i] = y[i + 1];
       y[i + 1] = tmp;
     }
-    y[i + 1] -= dl[i * K + t] * y[i];
+    y[i + 1] -= dl[i] * y[i];
   }
   // back substitution; the system is linear, so the whole vector may be
   // rescaled whenever a component grows large (near-singular shifts)
   for (int i = n - 1; i >= 0; --i) {
     R v = y[i];
-    if (i + 1 < n) v -= du[i * K + t] * y[i + 1];
-    if (i + 2 < n) v -= du2[i * K + t] * y[i + 2];
-    v /= dd[i * K + t];
+    if (i + 1 < n) v -= du[i] * y[i + 1];
+    if (i + 2 < n) v -= du2[i] * y[i + 2];
+    v /= dd[i];
     y[i] = v;
     if (fabs(v) > Eps<R>::big)
       for (int q = 0; q < n; ++q) y[q] *= R(1) / Eps<R>::big;
@@ -858,11 +855,12 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
   R *eabs = reinterpret_cast<R *>(w + lay.off_eabs);
   C_ *delta = reinterpret_cast<C_ *>(w + lay.off_delta);
   C_ *p = reinterpret_cast<C_ *>(w + lay.off_p);
-  if (n <= 64 || sizeof(R) == 8) {
-    // FP64 or small matrices: four launches per column. (In FP64 the reduction
-    // is bound by GB300's FP64 issue rate, where these per-column kernels
-    // spread the rank-2 update over every SM; the cooperative kernel wins in
-    // FP32, where barriers and launches dominate.)
+  if (n <= 64 || (sizeof(R) == 8 && n > 256)) {
+    // small matrices, and large FP64 ones: four launches per column. (A large
+    // FP64 reduction is bound by GB300's FP64 issue rate, where these
+    // per-column kernels spread the rank-2 update over every SM; the
+    // cooperative kernel wins in FP32 and for small FP64 matrices, where
+    // barriers and launches dominate.)
     VB_TRY_CUDA(cudaMemsetAsync(w + lay.off_bar, 0, 3 * sizeof(unsigned int), st));
     // small matrices: four launches per column are cheaper than a grid-wide launch
     for (int j = 0; j + 2 < n; ++j) {
@@ -887,7 +885,9 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
     VB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     VB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_tridiag_coop<R>, 512, 0));
     if (per_sm < 1) return fail(VB_ECUDA, "eig_values: cooperative kernel does not fit on an SM");
-    int nb = sms;  // one block per SM
+    // one block per SM at most; for small matrices fewer blocks (16 warps
+    // each) make the grid barrier cheaper without idling rows
+    int nb = std::min(sms, std::max(8, (n + 15) / 16));
     if (nb > 1024) nb = 1024;
     void *args[] = {(void *)&rho, (void *)&n, (void *)&vref, (void *)&tau, (void *)&dg, (void *)&ec,
                     (void *)&p, (void *)&part, (void *)&bar, (void *)&err};
