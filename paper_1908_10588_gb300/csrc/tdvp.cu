@@ -355,8 +355,17 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     cd *w = V + (k + 1) * ldv;
     VB_TRY(apply_heff(s, op, V + k * ldv, w));
     prof_begin(PH_KRYLOV, st);
-    VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st));
-    VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
+    if (s->dtype == VB_MIXED) {
+      // first pass against v_{k-1}, v_k only (the three-term recurrence),
+      // then one full pass: the full pass then removes components that are
+      // already small, so it loses no orthogonality to cancellation
+      const int j0 = k > 0 ? k - 1 : 0;
+      VB_TRY(vec_multi_dot(V + j0 * ldv, ldv, k + 1 - j0, w, N, s->d_c + j0, s->d_partc, np, st));
+      VB_TRY(vec_multi_axpy(V + j0 * ldv, ldv, k + 1 - j0, s->d_c + j0, -1.0, w, N, st));
+    } else {
+      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st));
+      VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
+    }
     VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st));
     VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c2, -1.0, w, N, st));
     set_alpha_kernel<<<1, 1, 0, st>>>(s->d_c, s->d_c2, k, s->d_alpha);
