@@ -40,7 +40,7 @@ void count_launch();
 
 // ---- per-phase event profiler (host side, single-threaded use)
 enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5, PH_RHO = 6, PH_EIGVAL = 7,
-       PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_EIG32VAL = 10, PH_EIG32VEC = 11, PH_INVIT = 12,
+       PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_SUBPROD = 10, PH_SUBORTH = 11, PH_INVIT = 12,
        PH_CGS = 13, PH_BACKT = 14, PH_COUNT = 16 };
 bool prof_on();
 void prof_begin(int phase, cudaStream_t st);
@@ -207,6 +207,26 @@ vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long lo
 // w -= sum_j c[j] V[j] (sign = -1) or w += ... (sign = +1); c on device; cscale applied
 vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
                          long long n, cudaStream_t st);
+// ------------------------------------------------------------ subspace iteration
+struct SubspaceWork {
+  cf *G, *W, *T;  // r x r Gram matrix, r x r transform, r x n scratch rows
+  int *flag;      // r + 1: rows refilled at random, then their count
+  cf *ws;         // split-K workspace of the Gram product
+  long long ws_elems;
+};
+size_t subspace_chol_smem(int r);
+// Q (r x n, FP32 rows): rows j < m_warm copied from the old bond tensor (left:
+// n x m_old, row j = column j; right: m_old x n, row j = row j), the others
+// drawn from a counter-based generator keyed by seed
+vb_status subspace_init(cf *Q, int r, int n, const cd *warm, int m_old, int m_warm, bool left,
+                        unsigned long long seed, cudaStream_t st);
+// orthonormalise the rows of Q (r <= 128) in place: row-scaled Cholesky QR,
+// twice; rows found dependent are refilled at random before the second pass
+vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned long long seed, cudaStream_t st);
+// *out = sum |x_i|^2 accumulated in FP64
+vb_status norm2_sq_f32(const cf *x, long long n, double *out, double *partial, int n_part, cudaStream_t st);
+// out[0] = *capt, out[1] = *cnt
+vb_status subspace_status(const double *capt, const int *cnt, double *out, cudaStream_t st);
 vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
                     cudaStream_t st);
 // x *= 1/ (*nrm)  (device scalar)

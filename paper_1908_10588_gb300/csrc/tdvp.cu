@@ -22,6 +22,10 @@ namespace vb {
 constexpr double HBAR_EV_FS = 0.6582119569;
 constexpr double MULTIPLET_RTOL = 1e-10;
 constexpr int MIXED_SPLIT_MIN_N = 192;
+// subspace iteration of the mixed split: at most this many applications of
+// rho; stop once the captured weight changes by less than this fraction
+constexpr int SUBSPACE_MAXIT = 30;
+constexpr double SUBSPACE_RTOL = 3e-7;
 
 // H_eff products in split-TF32 on the tensor cores (k_mixed.cu)
 vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
@@ -80,6 +84,14 @@ __global__ void lowdin_kernel(cd *G, int r) {
     const int i = e / r, j = e % r;
     cd g = G[e];
     G[e] = mkc((i == j ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
+  }
+}
+
+// FP64 copy of the FP32 basis rows, conjugated when conj != 0
+__global__ void subspace_rows_c64(const cf *__restrict__ q, cd *__restrict__ out, long long n, int conj) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cf a = q[i];
+    out[i] = mkc((double)a.x, conj ? -(double)a.y : (double)a.y);
   }
 }
 
@@ -149,12 +161,17 @@ struct vb_mps {
   cd *d_c = nullptr, *d_c2 = nullptr, *d_u = nullptr, *d_partc = nullptr;
   double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
   int *d_tcerr = nullptr;                        // raised by a tensor-core kernel whose wait ran out
+  // subspace iteration of the mixed split
+  cf *subZ = nullptr, *subT = nullptr, *subG = nullptr, *subW = nullptr, *skws32 = nullptr;
+  long long skws32_elems = 0;
+  int *subflag = nullptr;
+  double *d_capt = nullptr;
+  unsigned long long split_calls = 0;
   // mixed split: FP32 eigenvectors of rho, FP64 Rayleigh-Ritz
   int rcap = 0;
-  cf *M32 = nullptr, *rho32 = nullptr, *Q32 = nullptr;
+  cf *M32 = nullptr, *Q32 = nullptr;
   cd *Q64 = nullptr, *Qo = nullptr, *G = nullptr, *X = nullptr, *S = nullptr, *Zr = nullptr, *U = nullptr;
-  float *ev32 = nullptr;
-  void *eigw32 = nullptr, *eigwS = nullptr;
+  void *eigwS = nullptr;
   cd *skws = nullptr;  // split-K workspace of the Rayleigh-Ritz products
   long long skws_elems = 0;
   // mixed form: environment updates in complex FP32
@@ -433,10 +450,12 @@ int choose_rank(const std::vector<double> &lam, int n, double tot, int rank_boun
 
 // theta (mL d1 x d2 mR) -> left-orthonormal A_i (into dstA) and C (into dstC),
 // or (right) C (dstA) and right-orthonormal B (dstC). Returns the new bond.
-vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o, cd *dstA,
-                      cd *dstC, int *k_out, double *disc);
+vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old, const TruncOpts &o,
+                      cd *dstA, cd *dstC, int *k_out, double *disc);
 
-vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o,
+// m_old: the bond dimension between the two sites before this split; dstA
+// (left) or dstC (right) still holds the old tensor on entry
+vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old, const TruncOpts &o,
                 cd *dstA, cd *dstC, int *k_out, double *disc) {
   cudaStream_t st = s->st;
   const int n1 = mL * d1, n2 = d2 * mR;
@@ -444,7 +463,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
   // mixed form: FP32 eigenvectors + FP64 Rayleigh-Ritz once the matrix is
   // large enough for the FP64 reduction to matter
   if (s->dtype == VB_MIXED && n > MIXED_SPLIT_MIN_N && o.m_max + 1 + 8 <= s->rcap)
-    return split_mixed(s, left, mL, d1, d2, mR, o, dstA, dstC, k_out, disc);
+    return split_mixed(s, left, mL, d1, d2, mR, m_old, o, dstA, dstC, k_out, disc);
   const cd *M = s->theta;
   GemmArgs g{};
   g.M = n; g.N = n; g.batch = 1;
@@ -517,8 +536,8 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const Trun
 // products with theta and diagonalised in FP64, and the kept weights, the
 // discarded weight (against tr rho = |theta|^2) and the new tensors all come
 // from the FP64 Ritz pairs.
-vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, const TruncOpts &o, cd *dstA,
-                      cd *dstC, int *k_out, double *disc) {
+vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old, const TruncOpts &o,
+                      cd *dstA, cd *dstC, int *k_out, double *disc) {
   cudaStream_t st = s->st;
   const int n1 = mL * d1, n2 = d2 * mR;
   const int n = left ? n1 : n2;
@@ -536,36 +555,62 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, cons
     g.ws = s->skws; g.ws_elems = s->skws_elems;
     return zgemm(g, st);
   };
-  // ---- FP32 eigenvectors of rho
+  // ---- FP32 subspace iteration for the r leading eigenvectors of rho
   prof_begin(PH_RHO, st);
   c64_to_c32<<<grid1(nm), 256, 0, st>>>(M, s->M32, nm);
   VB_CHECK_LAUNCH();
-  {
-    GemmArgsF g{};
-    g.M = n; g.N = n; g.batch = 1;
-    g.alpha = mkc(1.f, 0.f); g.beta = mkc(0.f, 0.f);
-    g.A = s->M32; g.lda = n2; g.B = s->M32; g.ldb = n2;
-    if (left) {
-      g.K = n2; g.opA = OP_N; g.opB = OP_C;
-    } else {
-      g.K = n1; g.opA = OP_C; g.opB = OP_N;
-    }
-    g.C = s->rho32; g.ldc = n;
-    g.a_size = nm; g.b_size = nm; g.c_size = s->nrho_cap * s->nrho_cap;
-    VB_TRY(gemm<float>(g, st));
-  }
   VB_TRY(vec_norm2(M, nm, s->d_trace, s->d_part, reduce_parts(nm), st));
   prof_end(PH_RHO, st, 0.0);
   prof_begin(PH_EIGVAL, st);
-  prof_begin(PH_EIG32VAL, st);
-  VB_TRY(eig_values<float>(n, s->rho32, r, s->ev32, s->eigw32, st));
-  prof_end(PH_EIG32VAL, st, 0.0);
-  prof_begin(PH_EIG32VEC, st);
-  VB_TRY(eig_vectors<float>(n, s->rho32, r, r, s->ev32, s->Q32, s->eigw32, st));
-  prof_end(PH_EIG32VEC, st, 0.0);
-  VB_TRY(EigWork::check(n, r, 4, s->eigw32, st));
-  // ---- FP64 Rayleigh-Ritz on the span of the FP32 vectors (rows of Q)
-  c32_to_c64<<<grid1((long long)r * n), 256, 0, st>>>(s->Q32, s->Q64, (long long)r * n);
+  // rows of Q: left, u_j^T (rho = M M^+); right, conj(v_j)^T (rho = M^+ M).
+  // Z = conj(Q) op1(M) and Q <- conj(Z) op2(M) apply rho once (left: op1 = N,
+  // op2 = T; right: op1 = T, op2 = N); |Z|^2 is the weight the span captures
+  const int nother = left ? n2 : n1;
+  const unsigned long long seed = 0x243F6A8885A308D3ull + 0x9E3779B97F4A7C15ull * (++s->split_calls);
+  const SubspaceWork sw{s->subG, s->subW, s->subT, s->subflag, s->skws32, s->skws32_elems};
+  const int m_warm = std::min(std::max(m_old, 0), r);
+  prof_begin(PH_SUBORTH, st);
+  VB_TRY(subspace_init(s->Q32, r, n, left ? dstA : dstC, m_old, m_warm, left, seed, st));
+  VB_TRY(subspace_orth(s->Q32, r, n, sw, seed + 1, st));
+  prof_end(PH_SUBORTH, st, 0.0);
+  const cf onef = mkc(1.f, 0.f), zerof = mkc(0.f, 0.f);
+  double prev = -1.0;
+  for (int it = 0; it < SUBSPACE_MAXIT; ++it) {
+    prof_begin(PH_SUBPROD, st);
+    GemmArgsF g{};
+    g.M = r; g.N = nother; g.K = n; g.batch = 1;
+    g.opA = OP_R; g.A = s->Q32; g.lda = n;
+    g.opB = left ? OP_N : OP_T; g.B = s->M32; g.ldb = n2;
+    g.C = s->subZ; g.ldc = nother;
+    g.alpha = onef; g.beta = zerof;
+    g.a_size = (long long)r * n; g.b_size = nm; g.c_size = (long long)r * nother;
+    g.ws = s->skws32; g.ws_elems = s->skws32_elems;
+    VB_TRY(gemm<float>(g, st));
+    const long long nz = (long long)r * nother;
+    VB_TRY(norm2_sq_f32(s->subZ, nz, s->d_capt, s->d_part, reduce_parts(nz), st));
+    GemmArgsF h{};
+    h.M = r; h.N = n; h.K = nother; h.batch = 1;
+    h.opA = OP_R; h.A = s->subZ; h.lda = nother;
+    h.opB = left ? OP_T : OP_N; h.B = s->M32; h.ldb = n2;
+    h.C = s->Q32; h.ldc = n;
+    h.alpha = onef; h.beta = zerof;
+    h.a_size = nz; h.b_size = nm; h.c_size = (long long)r * n;
+    h.ws = s->skws32; h.ws_elems = s->skws32_elems;
+    VB_TRY(gemm<float>(h, st));
+    prof_end(PH_SUBPROD, st, 0.0);
+    prof_begin(PH_SUBORTH, st);
+    VB_TRY(subspace_orth(s->Q32, r, n, sw, seed + 2 + it, st));
+    VB_TRY(subspace_status(s->d_capt, s->subflag + r, s->d_flag + 2, st));
+    prof_end(PH_SUBORTH, st, 0.0);
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    const double capt = s->h_flag[2], nbad = s->h_flag[3];
+    if (!(capt == capt)) return fail(VB_ECUDA, "split: NaN in the subspace iteration");
+    if (nbad > 0.0) VB_TRY(subspace_orth(s->Q32, r, n, sw, seed + 0x1000 + it, st));
+    if (it >= 1 && std::fabs(capt - prev) <= SUBSPACE_RTOL * capt) break;
+    prev = capt;
+  }
+  // ---- FP64 Rayleigh-Ritz on the span of the rows of Q
+  subspace_rows_c64<<<grid1((long long)r * n), 256, 0, st>>>(s->Q32, s->Q64, (long long)r * n, left ? 0 : 1);
   VB_CHECK_LAUNCH();
   const long long rn = (long long)r * n, rr = (long long)r * r;
   VB_TRY(G64(r, r, n, OP_N, s->Q64, n, rn, OP_C, s->Q64, n, rn, s->G, r, rr));  // G = Q Q^+
@@ -774,7 +819,14 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       s->rcap = (int)std::min<long long>(nr2, std::min(opts->m_cap + 1 + 32, 128));
       const long long rc = std::max(s->rcap, 1);
       A2((void **)&s->M32, s->theta_cap * sizeof(cf));
-      A2((void **)&s->rho32, (size_t)nr2 * nr2 * sizeof(cf));
+      A2((void **)&s->subZ, (size_t)rc * nr2 * sizeof(cf));
+      A2((void **)&s->subT, (size_t)rc * nr2 * sizeof(cf));
+      A2((void **)&s->subG, (size_t)rc * rc * sizeof(cf));
+      A2((void **)&s->subW, (size_t)rc * rc * sizeof(cf));
+      A2((void **)&s->subflag, (size_t)(rc + 1) * sizeof(int));
+      A2((void **)&s->d_capt, 256);
+      s->skws32_elems = 48LL * rc * nr2;
+      A2((void **)&s->skws32, (size_t)s->skws32_elems * sizeof(cf));
       A2((void **)&s->Q32, (size_t)rc * nr2 * sizeof(cf));
       A2((void **)&s->Q64, (size_t)rc * nr2 * sizeof(cd));
       A2((void **)&s->Qo, (size_t)rc * nr2 * sizeof(cd));
@@ -783,8 +835,6 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       A2((void **)&s->G, (size_t)rc * rc * sizeof(cd));
       A2((void **)&s->S, (size_t)rc * rc * sizeof(cd));
       A2((void **)&s->Zr, (size_t)rc * rc * sizeof(cd));
-      A2((void **)&s->ev32, (size_t)rc * sizeof(float));
-      A2(&s->eigw32, EigWork::bytes((int)nr2, (int)rc, 4));
       A2(&s->eigwS, EigWork::bytes((int)rc, (int)rc, 8));
       s->skws_elems = 48LL * rc * nr2;
       A2((void **)&s->skws, (size_t)s->skws_elems * sizeof(cd));
@@ -976,7 +1026,7 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
     int k = 0;
     double disc = 0.0;
     prof_begin(PH_SPLIT, s->st);
-    VB_TRY(split(s, true, mL, d1, d2, mR, to, s->A[i], s->A[i + 1], &k, &disc));
+    VB_TRY(split(s, true, mL, d1, d2, mR, s->bond[i + 1], to, s->A[i], s->A[i + 1], &k, &disc));
     prof_end(PH_SPLIT, s->st, 0.0);
     st.discarded_weight += disc;
     s->bond[i + 1] = k;
@@ -999,7 +1049,7 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
     int k = 0;
     double disc = 0.0;
     prof_begin(PH_SPLIT, s->st);
-    VB_TRY(split(s, false, mL, d1, d2, mR, to, s->A[i], s->A[i + 1], &k, &disc));
+    VB_TRY(split(s, false, mL, d1, d2, mR, s->bond[i + 1], to, s->A[i], s->A[i + 1], &k, &disc));
     prof_end(PH_SPLIT, s->st, 0.0);
     st.discarded_weight += disc;
     s->bond[i + 1] = k;
