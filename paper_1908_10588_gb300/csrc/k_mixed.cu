@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include <climits>
 
 namespace vb {
 
@@ -116,46 +117,69 @@ __global__ void zero_cols(float *__restrict__ X, long long rows, long long ld, l
     X[(e / w) * ld + from + e % w] = 0.f;
 }
 
-// planar sparse MPO leg: like wapply (k_wapply.cu), with the real and the
-// imaginary parts in separate planes of X and Y. One thread per output
-// element; consecutive threads take consecutive q, so the re-reads of an
-// input column by the d outputs s' are served from L1. (Staging the inputs
-// in shared memory per block or per slab was measured slower on the largest
-// pair of the internal-conversion workload.)
-__global__ void wapply_planar_kernel(const int *__restrict__ rp, const int *__restrict__ col,
-                                     const float *__restrict__ val, const int *__restrict__ ptr,
-                                     const int *__restrict__ ent, int d, int Wp, const float *__restrict__ X,
-                                     long long xplane, WStrides xs, float *__restrict__ Y, long long yplane,
-                                     WStrides ys, int P, int Q) {
-  const long long total = (long long)P * d * Wp * Q;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(idx % Q);
-    long long r = idx / Q;
-    const int wo = (int)(r % Wp);
-    r /= Wp;
-    const int so = (int)(r % d);
-    const int p = (int)(r / d);
-    float ax = 0.f, ay = 0.f;
-    const float *xb = X + p * xs.p + q * xs.q;
-    for (int e = ptr[wo]; e < ptr[wo + 1]; ++e) {
+// Sparse MPO leg of the mixed-precision H_eff product (FP32, CUDA cores), real
+// and imaginary parts in separate planes of X and Y. A block covers RB output
+// rows (p, s', w') and TQ * QPT consecutive q of each; every warp stays inside
+// one row, so the loops over the row's nonzero blocks and operator entries are
+// uniform, and the q reads of a warp are coalesced. Index arithmetic is 32-bit
+// and done once per row.
+template <int QPT>
+__global__ void __launch_bounds__(128) wapply_planar_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                                            const float *__restrict__ val, const int *__restrict__ ptr,
+                                                            const int *__restrict__ ent, int d, int Wp, int rows,
+                                                            int TQ, const float *__restrict__ X, long long xplane,
+                                                            WStrides xs, float *__restrict__ Y, long long yplane,
+                                                            WStrides ys, int Q) {
+  const int RB = blockDim.x / TQ;
+  const int tq = threadIdx.x % TQ, rb = threadIdx.x / TQ;
+  const int q0 = blockIdx.x * TQ * QPT + tq;
+  const int xq = (int)xs.q, yq = (int)ys.q;
+  for (int row = blockIdx.y * RB + rb; row < rows; row += gridDim.y * RB) {
+    const int wo = row % Wp, t = row / Wp;
+    const int so = t % d, p = t / d;
+    float ax[QPT], ay[QPT];
+#pragma unroll
+    for (int j = 0; j < QPT; ++j) ax[j] = ay[j] = 0.f;
+    const float *xb = X + p * xs.p;
+    const int e1 = ptr[wo + 1];
+    for (int e = ptr[wo]; e < e1; ++e) {
       const int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
       const float *xw = xb + wi * xs.w;
       if (ident) {
-        ax += xw[so * xs.s];
-        ay += xw[so * xs.s + xplane];
+        const float *xr = xw + so * xs.s;
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+          const int q = q0 + j * TQ;
+          if (q < Q) {
+            ax[j] += xr[q * xq];
+            ay[j] += xr[q * xq + xplane];
+          }
+        }
       } else {
-        for (int k = rp[off + so]; k < rp[off + so + 1]; ++k) {
+        const int k1 = rp[off + so + 1];
+        for (int k = rp[off + so]; k < k1; ++k) {
           const float c = val[k];
-          const float *xs_ = xw + col[k] * xs.s;
-          ax = fmaf(c, xs_[0], ax);
-          ay = fmaf(c, xs_[xplane], ay);
+          const float *xr = xw + col[k] * xs.s;
+#pragma unroll
+          for (int j = 0; j < QPT; ++j) {
+            const int q = q0 + j * TQ;
+            if (q < Q) {
+              ax[j] = fmaf(c, xr[q * xq], ax[j]);
+              ay[j] = fmaf(c, xr[q * xq + xplane], ay[j]);
+            }
+          }
         }
       }
     }
-    const long long o = p * ys.p + so * ys.s + wo * ys.w + q * ys.q;
-    Y[o] = ax;
-    Y[o + yplane] = ay;
+    float *yr = Y + p * ys.p + so * ys.s + wo * ys.w;
+#pragma unroll
+    for (int j = 0; j < QPT; ++j) {
+      const int q = q0 + j * TQ;
+      if (q < Q) {
+        yr[q * yq] = ax[j];
+        yr[q * yq + yplane] = ay[j];
+      }
+    }
   }
 }
 
@@ -164,13 +188,36 @@ vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStr
   const int d = S.d, Wp = S.wr, Wc = S.wl;
   const long long total = (long long)P * d * Wp * Q;
   if (total == 0) return VB_OK;
+  if (P < 0 || Q < 0 || xs.q < 0 || ys.q < 0 || xs.q > INT_MAX / 4 || ys.q > INT_MAX / 4 ||
+      (long long)Q * std::max(xs.q, ys.q) > INT_MAX || (long long)P * d * Wp > INT_MAX)
+    return fail(VB_EINVAL, "wapply_planar: sizes or strides out of range");
   const long long xmax = (P - 1) * xs.p + (Wc - 1) * xs.w + (d - 1) * xs.s + (Q - 1) * xs.q + xplane;
   const long long ymax = (P - 1) * ys.p + (Wp - 1) * ys.w + (d - 1) * ys.s + (Q - 1) * ys.q + yplane;
   if (xmax >= x_size || ymax >= y_size) return fail(VB_EINVAL, "wapply_planar: view exceeds its buffer");
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152LL * 64) blocks = 152LL * 64;
-  wapply_planar_kernel<<<(int)blocks, 256, 0, st>>>(S.d_csr_ptr, S.d_csr_col, S.d_csr_val32, S.d_fwd_ptr,
-                                                    S.d_fwd_ent, d, Wp, X, xplane, xs, Y, yplane, ys, P, Q);
+  const int rows = P * d * Wp;
+  // q tiling: wide rows take 128 threads x 4 q each; narrow rows share a block
+  int TQ, qpt;
+  if (Q >= 512) {
+    TQ = 128; qpt = 4;
+  } else if (Q > 128) {
+    TQ = 128; qpt = (Q + 127) / 128;  // 2..4
+    if (qpt == 3) qpt = 4;
+  } else {
+    TQ = std::max(32, (Q + 31) / 32 * 32); qpt = 1;
+    if (TQ == 96) TQ = 128;
+  }
+  const int RB = 128 / TQ;
+  const long long gx = (Q + (long long)TQ * qpt - 1) / ((long long)TQ * qpt);
+  const long long gy = std::min<long long>((rows + RB - 1) / RB, 65535);
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  const int *rp = S.d_csr_ptr, *cl = S.d_csr_col, *pt = S.d_fwd_ptr, *en = S.d_fwd_ent;
+  const float *vl = S.d_csr_val32;
+  if (qpt == 4)
+    wapply_planar_kernel<4><<<grid, 128, 0, st>>>(rp, cl, vl, pt, en, d, Wp, rows, TQ, X, xplane, xs, Y, yplane, ys, Q);
+  else if (qpt == 2)
+    wapply_planar_kernel<2><<<grid, 128, 0, st>>>(rp, cl, vl, pt, en, d, Wp, rows, TQ, X, xplane, xs, Y, yplane, ys, Q);
+  else
+    wapply_planar_kernel<1><<<grid, 128, 0, st>>>(rp, cl, vl, pt, en, d, Wp, rows, TQ, X, xplane, xs, Y, yplane, ys, Q);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

@@ -8,43 +8,70 @@
 // of the environment updates therefore run here as a loop over the nonzero
 // blocks of the site instead of a dense GEMM over w x d.
 #include "common.h"
+#include <climits>
 
 namespace vb {
 namespace {
 
-template <class R>
-__global__ void wapply_kernel(const int *__restrict__ rp, const int *__restrict__ col, const R *__restrict__ val,
-                              const int *__restrict__ ptr, const int *__restrict__ ent, int d, int Wp,
-                              const cplx<R> *__restrict__ X, WStrides xs, cplx<R> *__restrict__ Y, WStrides ys,
-                              int P, int Q) {
-  long long total = (long long)P * d * Wp * Q;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int q = (int)(idx % Q);
-    long long r = idx / Q;
-    int wo = (int)(r % Wp);
-    r /= Wp;
-    int so = (int)(r % d);
-    int p = (int)(r / d);
-    R ax = 0, ay = 0;
-    const cplx<R> *xb = X + p * xs.p + q * xs.q;
-    for (int e = ptr[wo]; e < ptr[wo + 1]; ++e) {
-      int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
+// A block covers RB output rows (p, s', w') and TQ * QPT consecutive q of
+// each; every warp stays inside one row, so the loops over the row's nonzero
+// blocks and operator entries are uniform and the q accesses of a warp are
+// coalesced. Index arithmetic is 32-bit and done once per row.
+template <class R, int QPT>
+__global__ void __launch_bounds__(128) wapply_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                                     const R *__restrict__ val, const int *__restrict__ ptr,
+                                                     const int *__restrict__ ent, int d, int Wp, int rows, int TQ,
+                                                     const cplx<R> *__restrict__ X, WStrides xs,
+                                                     cplx<R> *__restrict__ Y, WStrides ys, int Q) {
+  const int RB = blockDim.x / TQ;
+  const int tq = threadIdx.x % TQ, rb = threadIdx.x / TQ;
+  const int q0 = blockIdx.x * TQ * QPT + tq;
+  const int xq = (int)xs.q, yq = (int)ys.q;
+  for (int row = blockIdx.y * RB + rb; row < rows; row += gridDim.y * RB) {
+    const int wo = row % Wp, t = row / Wp;
+    const int so = t % d, p = t / d;
+    R ax[QPT], ay[QPT];
+#pragma unroll
+    for (int j = 0; j < QPT; ++j) ax[j] = ay[j] = 0;
+    const cplx<R> *xb = X + p * xs.p;
+    const int e1 = ptr[wo + 1];
+    for (int e = ptr[wo]; e < e1; ++e) {
+      const int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
       const cplx<R> *xw = xb + wi * xs.w;
       if (ident) {
-        cplx<R> v = xw[so * xs.s];
-        ax += v.x;
-        ay += v.y;
+        const cplx<R> *xr = xw + so * xs.s;
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+          const int q = q0 + j * TQ;
+          if (q < Q) {
+            const cplx<R> v = xr[q * xq];
+            ax[j] += v.x;
+            ay[j] += v.y;
+          }
+        }
       } else {
-        for (int k = rp[off + so]; k < rp[off + so + 1]; ++k) {
+        const int k1 = rp[off + so + 1];
+        for (int k = rp[off + so]; k < k1; ++k) {
           const R c = val[k];
-          const cplx<R> v = xw[col[k] * xs.s];
-          ax = fma(c, v.x, ax);
-          ay = fma(c, v.y, ay);
+          const cplx<R> *xr = xw + col[k] * xs.s;
+#pragma unroll
+          for (int j = 0; j < QPT; ++j) {
+            const int q = q0 + j * TQ;
+            if (q < Q) {
+              const cplx<R> v = xr[q * xq];
+              ax[j] = fma(c, v.x, ax[j]);
+              ay[j] = fma(c, v.y, ay[j]);
+            }
+          }
         }
       }
     }
-    Y[p * ys.p + so * ys.s + wo * ys.w + q * ys.q] = mkc<R>(ax, ay);
+    cplx<R> *yr = Y + p * ys.p + so * ys.s + wo * ys.w;
+#pragma unroll
+    for (int j = 0; j < QPT; ++j) {
+      const int q = q0 + j * TQ;
+      if (q < Q) yr[q * yq] = mkc<R>(ax[j], ay[j]);
+    }
   }
 }
 
@@ -67,18 +94,40 @@ vb_status wapply(const MpoSite &site, int dir, const cplx<R> *X, WStrides xs, lo
     return fail(VB_EINVAL, "wapply: view exceeds its buffer (x " + std::to_string(xmax) + " >= " +
                                std::to_string(x_size) + " or y " + std::to_string(ymax) + " >= " +
                                std::to_string(y_size) + ")");
-  int threads = 256;
-  long long blocks = (total + threads - 1) / threads;
-  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  if (xs.q > INT_MAX / 4 || ys.q > INT_MAX / 4 || (long long)Q * std::max(xs.q, ys.q) > INT_MAX ||
+      (long long)P * d * Wp > INT_MAX)
+    return fail(VB_EINVAL, "wapply: sizes or strides out of range");
+  const int rows = P * d * Wp;
+  // q tiling: wide rows take 128 threads x 4 q each; narrow rows share a block
+  int TQ, qpt;
+  if (Q >= 512) {
+    TQ = 128; qpt = 4;
+  } else if (Q > 128) {
+    TQ = 128; qpt = (Q + 127) / 128;
+    if (qpt == 3) qpt = 4;
+  } else {
+    TQ = std::max(32, (Q + 31) / 32 * 32); qpt = 1;
+    if (TQ == 96) TQ = 128;
+  }
+  const int RB = 128 / TQ;
+  const long long gx = (Q + (long long)TQ * qpt - 1) / ((long long)TQ * qpt);
+  const long long gy = std::min<long long>((rows + RB - 1) / RB, 65535);
+  dim3 grid((unsigned)gx, (unsigned)gy);
   const R *vals;
   if constexpr (sizeof(R) == 8)
     vals = reinterpret_cast<const R *>(site.d_csr_val);
   else
     vals = reinterpret_cast<const R *>(site.d_csr_val32);
-  wapply_kernel<R><<<(int)blocks, threads, 0, st>>>(site.d_csr_ptr, site.d_csr_col, vals,
-                                                 dir == 0 ? site.d_fwd_ptr : site.d_bwd_ptr,
-                                                 dir == 0 ? site.d_fwd_ent : site.d_bwd_ent, d, Wp,
-                                                 X, xs, Y, ys, P, Q);
+  const int *pt = dir == 0 ? site.d_fwd_ptr : site.d_bwd_ptr, *en = dir == 0 ? site.d_fwd_ent : site.d_bwd_ent;
+  if (qpt == 4)
+    wapply_kernel<R, 4><<<grid, 128, 0, st>>>(site.d_csr_ptr, site.d_csr_col, vals, pt, en, d, Wp, rows, TQ, X, xs,
+                                              Y, ys, Q);
+  else if (qpt == 2)
+    wapply_kernel<R, 2><<<grid, 128, 0, st>>>(site.d_csr_ptr, site.d_csr_col, vals, pt, en, d, Wp, rows, TQ, X, xs,
+                                              Y, ys, Q);
+  else
+    wapply_kernel<R, 1><<<grid, 128, 0, st>>>(site.d_csr_ptr, site.d_csr_col, vals, pt, en, d, Wp, rows, TQ, X, xs,
+                                              Y, ys, Q);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
