@@ -21,6 +21,7 @@
 
 #include "common.h"
 #include <climits>
+#include <cstdint>
 
 namespace vb {
 
@@ -183,6 +184,75 @@ __global__ void __launch_bounds__(128) wapply_planar_kernel(const int *__restric
   }
 }
 
+// Vectorised form of the leg for unit q stride, Q % 4 == 0 and 16-byte
+// aligned rows: a block takes one output pair (s', w') and a chunk of
+// 128 * WV4_J consecutive (p, q/4) positions, so all its threads walk the same
+// nonzero blocks and operator entries; each thread moves four q per load.
+// Blocks are ordered with the chunk slowest, so the (s', w') blocks of one
+// chunk run together and share its input rows in L2.
+constexpr int WV4_J = 4;
+__global__ void __launch_bounds__(128) wapply_planar_v4_kernel(
+    const int *__restrict__ rp, const int *__restrict__ col, const float *__restrict__ val,
+    const int *__restrict__ ptr, const int *__restrict__ ent, int d, int Wp, int P, int Q4,
+    const float *__restrict__ X, long long xplane, WStrides xs, float *__restrict__ Y, long long yplane, WStrides ys) {
+  const int b = blockIdx.x;
+  const int wo = b % Wp, t = b / Wp;
+  const int so = t % d, chunk = t / d;
+  const int npair = P * Q4;
+  const float *xb[WV4_J];
+  float *yb[WV4_J];
+  bool ok[WV4_J];
+#pragma unroll
+  for (int j = 0; j < WV4_J; ++j) {
+    const int i = chunk * (128 * WV4_J) + threadIdx.x + 128 * j;
+    ok[j] = i < npair;
+    const int p = ok[j] ? i / Q4 : 0, q4 = ok[j] ? i % Q4 : 0;
+    xb[j] = X + p * xs.p + 4 * q4;
+    yb[j] = Y + p * ys.p + so * ys.s + wo * ys.w + 4 * q4;
+  }
+  float4 ar[WV4_J], ai[WV4_J];
+#pragma unroll
+  for (int j = 0; j < WV4_J; ++j) ar[j] = ai[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int e1 = ptr[wo + 1];
+  for (int e = ptr[wo]; e < e1; ++e) {
+    const int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
+    const long long ow = wi * xs.w;
+    if (ident) {
+      const long long o = ow + so * xs.s;
+#pragma unroll
+      for (int j = 0; j < WV4_J; ++j) {
+        if (!ok[j]) continue;
+        const float4 vr = *reinterpret_cast<const float4 *>(xb[j] + o);
+        const float4 vi = *reinterpret_cast<const float4 *>(xb[j] + o + xplane);
+        ar[j].x += vr.x; ar[j].y += vr.y; ar[j].z += vr.z; ar[j].w += vr.w;
+        ai[j].x += vi.x; ai[j].y += vi.y; ai[j].z += vi.z; ai[j].w += vi.w;
+      }
+    } else {
+      const int k1 = rp[off + so + 1];
+      for (int kk = rp[off + so]; kk < k1; ++kk) {
+        const float c = val[kk];
+        const long long o = ow + col[kk] * xs.s;
+#pragma unroll
+        for (int j = 0; j < WV4_J; ++j) {
+          if (!ok[j]) continue;
+          const float4 vr = *reinterpret_cast<const float4 *>(xb[j] + o);
+          const float4 vi = *reinterpret_cast<const float4 *>(xb[j] + o + xplane);
+          ar[j].x = fmaf(c, vr.x, ar[j].x); ar[j].y = fmaf(c, vr.y, ar[j].y);
+          ar[j].z = fmaf(c, vr.z, ar[j].z); ar[j].w = fmaf(c, vr.w, ar[j].w);
+          ai[j].x = fmaf(c, vi.x, ai[j].x); ai[j].y = fmaf(c, vi.y, ai[j].y);
+          ai[j].z = fmaf(c, vi.z, ai[j].z); ai[j].w = fmaf(c, vi.w, ai[j].w);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < WV4_J; ++j) {
+    if (!ok[j]) continue;
+    *reinterpret_cast<float4 *>(yb[j]) = ar[j];
+    *reinterpret_cast<float4 *>(yb[j] + yplane) = ai[j];
+  }
+}
+
 vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStrides xs, long long x_size,
                         float *Y, long long yplane, WStrides ys, long long y_size, int P, int Q, cudaStream_t st) {
   const int d = S.d, Wp = S.wr, Wc = S.wl;
@@ -194,6 +264,20 @@ vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStr
   const long long xmax = (P - 1) * xs.p + (Wc - 1) * xs.w + (d - 1) * xs.s + (Q - 1) * xs.q + xplane;
   const long long ymax = (P - 1) * ys.p + (Wp - 1) * ys.w + (d - 1) * ys.s + (Q - 1) * ys.q + yplane;
   if (xmax >= x_size || ymax >= y_size) return fail(VB_EINVAL, "wapply_planar: view exceeds its buffer");
+  auto al16 = [](long long v) { return (v & 3) == 0; };
+  if (xs.q == 1 && ys.q == 1 && Q % 4 == 0 && al16(xs.p) && al16(xs.w) && al16(xs.s) && al16(xplane) &&
+      al16(ys.p) && al16(ys.w) && al16(ys.s) && al16(yplane) && ((uintptr_t)X & 15) == 0 &&
+      ((uintptr_t)Y & 15) == 0 && (long long)P * (Q / 4) <= INT_MAX - 128 * WV4_J) {
+    const long long chunks = ((long long)P * (Q / 4) + 128 * WV4_J - 1) / (128 * WV4_J);
+    const long long blocks = chunks * d * Wp;
+    if (blocks <= INT_MAX) {
+      wapply_planar_v4_kernel<<<(unsigned)blocks, 128, 0, st>>>(S.d_csr_ptr, S.d_csr_col, S.d_csr_val32, S.d_fwd_ptr,
+                                                                S.d_fwd_ent, d, Wp, P, Q / 4, X, xplane, xs, Y,
+                                                                yplane, ys);
+      VB_CHECK_LAUNCH();
+      return VB_OK;
+    }
+  }
   const int rows = P * d * Wp;
   // q tiling: wide rows take 128 threads x 4 q each; narrow rows share a block
   int TQ, qpt;
