@@ -63,7 +63,7 @@ class vb_profile(C.Structure):
 
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
           "split_out", "split_subspace_products", "split_subspace_orth", "eigvec_invit", "eigvec_gram_schmidt",
-          "eigvec_backtransform"]
+          "eigvec_backtransform", "split_rayleigh_ritz_products"]
 
 
 class vb_sweep_stats(C.Structure):

@@ -41,7 +41,7 @@ void count_launch();
 // ---- per-phase event profiler (host side, single-threaded use)
 enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5, PH_RHO = 6, PH_EIGVAL = 7,
        PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_SUBPROD = 10, PH_SUBORTH = 11, PH_INVIT = 12,
-       PH_CGS = 13, PH_BACKT = 14, PH_COUNT = 16 };
+       PH_CGS = 13, PH_BACKT = 14, PH_RR = 15, PH_COUNT = 16 };
 bool prof_on();
 void prof_begin(int phase, cudaStream_t st);
 void prof_end(int phase, cudaStream_t st, double flops);
@@ -227,6 +227,9 @@ vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned lon
 vb_status norm2_sq_f32(const cf *x, long long n, double *out, double *partial, int n_part, cudaStream_t st);
 // out[0] = *capt, out[1] = *cnt
 vb_status subspace_status(const double *capt, const int *cnt, double *out, cudaStream_t st);
+// vec_multi_axpy, then *out = |w| (partial: at least 512 doubles)
+vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
+                              double *out, double *partial, cudaStream_t st);
 vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
                     cudaStream_t st);
 // x *= 1/ (*nrm)  (device scalar)

@@ -31,24 +31,63 @@ __device__ double block_sum(double v, double *sh) {
   return r;
 }
 
-// partial[b * nv + j] = sum over block b's chunk of conj(V_j[i]) w[i]
+// partial[b * nv + j] = sum over block b's chunk of conj(V_j[i]) w[i].
+// blockIdx.y picks a group of up to DOT_JB vectors; each thread keeps the
+// group's partial sums in registers (independent FMA chains) and reads w[i]
+// once per group. The group size is a template parameter, so a short last
+// group issues no predicated-off FP64 instructions.
+constexpr int DOT_JB = 8;
+template <int JB>
+__device__ __forceinline__ void dot_group(const cd *__restrict__ Vg, long long ldv, const cd *__restrict__ w,
+                                          long long i0, long long i1, double *sh, double *out2) {
+  double sx[JB], sy[JB];
+#pragma unroll
+  for (int j = 0; j < JB; ++j) sx[j] = sy[j] = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += RT) {
+    const cd b = w[i];
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+      const cd a = Vg[j * ldv + i];
+      sx[j] = fma(a.x, b.x, fma(a.y, b.y, sx[j]));
+      sy[j] = fma(a.x, b.y, fma(-a.y, b.x, sy[j]));
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < JB; ++j) {
+    const double rx = warp_sum(sx[j]), ry = warp_sum(sy[j]);
+    if (lane == 0) {
+      sh[wid * 2 * DOT_JB + 2 * j] = rx;
+      sh[wid * 2 * DOT_JB + 2 * j + 1] = ry;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * JB) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < RT / 32; ++w2) s += sh[w2 * 2 * DOT_JB + threadIdx.x];
+    out2[threadIdx.x] = s;
+  }
+}
+
 __global__ void __launch_bounds__(RT) multi_dot_part(const cd *__restrict__ V, long long ldv, int nv,
                                                      const cd *__restrict__ w, long long n,
                                                      cd *__restrict__ partial) {
-  __shared__ double sh[RT / 32];
-  long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
-  for (int j = 0; j < nv; ++j) {
-    const cd *v = V + j * ldv;
-    double sx = 0.0, sy = 0.0;
-    for (long long i = i0 + threadIdx.x; i < i1; i += RT) {
-      cd a = v[i], b = w[i];
-      sx = fma(a.x, b.x, fma(a.y, b.y, sx));
-      sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
-    }
-    double rx = block_sum(sx, sh);
-    double ry = block_sum(sy, sh);
-    if (threadIdx.x == 0) partial[(long long)blockIdx.x * nv + j] = mkc(rx, ry);
+  __shared__ double sh[(RT / 32) * 2 * DOT_JB];
+  const int j0 = blockIdx.y * DOT_JB;
+  const int jn = min(DOT_JB, nv - j0);
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  const cd *Vg = V + j0 * ldv;
+  double *out2 = reinterpret_cast<double *>(partial + (long long)blockIdx.x * nv + j0);
+  switch (jn) {
+    case 8: dot_group<8>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 7: dot_group<7>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 6: dot_group<6>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 5: dot_group<5>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 4: dot_group<4>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 3: dot_group<3>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 2: dot_group<2>(Vg, ldv, w, i0, i1, sh, out2); break;
+    default: dot_group<1>(Vg, ldv, w, i0, i1, sh, out2); break;
   }
 }
 
@@ -68,22 +107,53 @@ __global__ void reduce_parts_cd(const cd *__restrict__ partial, int n_part, int 
   if (lane == 0) out[j] = mkc(sx, sy);
 }
 
-__global__ void multi_axpy_kernel(const cd *__restrict__ V, long long ldv, int nv,
-                                  const cd *__restrict__ c, double sign, cd *__restrict__ w,
-                                  long long n) {
+// w[i] += sign * sum_j c[j] V_j[i], two elements per thread (four
+// independent FMA chains). With partial != nullptr each block also writes
+// the sum of |w_new[i]|^2 over its elements to partial[blockIdx.x].
+__global__ void __launch_bounds__(256) multi_axpy_kernel(const cd *__restrict__ V, long long ldv, int nv,
+                                                         const cd *__restrict__ c, double sign, cd *__restrict__ w,
+                                                         long long n, double *__restrict__ partial) {
   __shared__ cd cs[128];
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = c[j];
+  __shared__ double sh[8];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = cscale(c[j], sign);
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    double ax = 0.0, ay = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double nn = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    const long long i2 = i + stride;
+    const bool two = i2 < n;
+    double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
     for (int j = 0; j < nv; ++j) {
-      cd v = V[j * ldv + i];
-      ax = fma(cs[j].x, v.x, fma(-cs[j].y, v.y, ax));
-      ay = fma(cs[j].x, v.y, fma(cs[j].y, v.x, ay));
+      const cd cj = cs[j];
+      const cd v = V[j * ldv + i];
+      ax = fma(cj.x, v.x, fma(-cj.y, v.y, ax));
+      ay = fma(cj.x, v.y, fma(cj.y, v.x, ay));
+      if (two) {
+        const cd u = V[j * ldv + i2];
+        bx = fma(cj.x, u.x, fma(-cj.y, u.y, bx));
+        by = fma(cj.x, u.y, fma(cj.y, u.x, by));
+      }
     }
-    cd o = w[i];
-    w[i] = mkc(o.x + sign * ax, o.y + sign * ay);
+    const cd o = w[i];
+    const cd r = mkc(o.x + ax, o.y + ay);
+    w[i] = r;
+    nn = fma(r.x, r.x, fma(r.y, r.y, nn));
+    if (two) {
+      const cd o2 = w[i2];
+      const cd r2 = mkc(o2.x + bx, o2.y + by);
+      w[i2] = r2;
+      nn = fma(r2.x, r2.x, fma(r2.y, r2.y, nn));
+    }
+  }
+  if (partial) {
+    nn = warp_sum(nn);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sh[w2];
+      partial[blockIdx.x] = s;
+    }
   }
 }
 
@@ -244,7 +314,8 @@ int reduce_parts(long long n) {
 vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
                         cd *partial, int n_part, cudaStream_t st) {
   if (nv <= 0) return VB_OK;
-  multi_dot_part<<<n_part, RT, 0, st>>>(V, ldv, nv, w, n, partial);
+  if (nv > 128 || (long long)n_part * nv > 512LL * 128) return fail(VB_EINVAL, "multi_dot: too many vectors");
+  multi_dot_part<<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial);
   VB_CHECK_LAUNCH();
   reduce_parts_cd<<<(nv + 7) / 8, 256, 0, st>>>(partial, n_part, nv, out);
   VB_CHECK_LAUNCH();
@@ -255,7 +326,19 @@ vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double
                          long long n, cudaStream_t st) {
   if (nv <= 0 || n == 0) return VB_OK;
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
-  multi_axpy_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, ldv, nv, c, sign, w, n);
+  multi_axpy_kernel<<<grid_for((n + 1) / 2, 256), 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
+                              double *out, double *partial, cudaStream_t st) {
+  if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
+  if (nv <= 0 || n == 0) return vec_norm2(w, n, out, partial, reduce_parts(n), st);
+  const int blocks = (int)std::min<long long>(512, std::max<long long>(1, (n + 511) / 512));
+  multi_axpy_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial);
+  VB_CHECK_LAUNCH();
+  norm2_final<<<1, 32, 0, st>>>(partial, blocks, out);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

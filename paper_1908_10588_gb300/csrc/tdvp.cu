@@ -384,10 +384,9 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
     }
     VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st));
-    VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c2, -1.0, w, N, st));
+    VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st));
     set_alpha_kernel<<<1, 1, 0, st>>>(s->d_c, s->d_c2, k, s->d_alpha);
     VB_CHECK_LAUNCH();
-    VB_TRY(vec_norm2(w, N, s->d_bnext, s->d_part, np, st));
     VB_TRY(tridiag_expm(s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     VB_TRY_CUDA(cudaMemcpyAsync(s->d_flag + 1, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
     prof_end(PH_KRYLOV, st, 0.0);
@@ -610,6 +609,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     prev = capt;
   }
   // ---- FP64 Rayleigh-Ritz on the span of the rows of Q
+  prof_begin(PH_RR, st);
   subspace_rows_c64<<<grid1((long long)r * n), 256, 0, st>>>(s->Q32, s->Q64, (long long)r * n, left ? 0 : 1);
   VB_CHECK_LAUNCH();
   const long long rn = (long long)r * n, rr = (long long)r * r;
@@ -626,6 +626,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     VB_TRY(G64(n1, r, n2, OP_N, M, n2, nm, OP_T, s->Qo, n2, rn, s->X, r, (long long)n1 * r));
     VB_TRY(G64(r, r, n1, OP_C, s->X, r, (long long)n1 * r, OP_N, s->X, r, (long long)n1 * r, s->S, r, rr));
   }
+  prof_end(PH_RR, st, 0.0);
   const int kws = std::min(r, kw);
   VB_TRY(eig_values(r, s->S, kws, s->d_evals, s->eigwS, st));
   std::vector<double> lam(kws);
