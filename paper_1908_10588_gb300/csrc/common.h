@@ -255,9 +255,10 @@ template <class R>
 vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cudaStream_t st);
 // phase 2: eigenvectors for the first k_vec of those eigenvalues, written as
 // rows of evecs [k_vec][n] (device). Needs the same rho/work after phase 1.
+// rounds: inverse-iteration rounds (0: 3 in FP64, 2 in FP32)
 template <class R>
 vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R *evals,
-                      cplx<R> *evecs, void *work, cudaStream_t st);
+                      cplx<R> *evecs, void *work, cudaStream_t st, int rounds = 0);
 
 // Krylov tridiagonal exponential: from alpha[0..k], beta[0..k-1] (device),
 // u = exp(-i T tau) e_1 (k+1 complex) and err = bnext * |u_k| written to

@@ -886,15 +886,18 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
     VB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_tridiag_coop<R>, 512, 0));
     if (per_sm < 1) return fail(VB_ECUDA, "eig_values: cooperative kernel does not fit on an SM");
     // one block per SM at most; for small matrices fewer blocks (16 warps
-    // each) make the grid barrier cheaper without idling rows
-    int nb = std::min(sms, std::max(8, (n + 15) / 16));
+    // each) make the grid barrier cheaper without idling rows. FP64 runs at
+    // two FMA per clock and SM on this part, so there the blocks are 4 warps
+    // (one per scheduler) and each warp owns about one row.
+    const int bt = sizeof(R) == 8 ? 128 : 512;
+    int nb = sizeof(R) == 8 ? std::min(sms, std::max(8, (n + 3) / 4)) : std::min(sms, std::max(8, (n + 15) / 16));
     if (nb > 1024) nb = 1024;
     void *args[] = {(void *)&rho, (void *)&n, (void *)&vref, (void *)&tau, (void *)&dg, (void *)&ec,
                     (void *)&p, (void *)&part, (void *)&bar, (void *)&err};
     const size_t vsm = (size_t)3 * n * sizeof(C_);
     if (vsm <= 44 * 1024) {
       // one barrier per column; the reflectors stay in shared memory
-      VB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)hh_tridiag_fused<R>, dim3(nb), dim3(512), args, vsm, st));
+      VB_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)hh_tridiag_fused<R>, dim3(nb), dim3(bt), args, vsm, st));
       count_launch();
       tri_finish_fused<R><<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
       VB_CHECK_LAUNCH();
@@ -906,14 +909,19 @@ vb_status eig_values(int n, cplx<R> *rho, int k_want, R *evals, void *work, cuda
   tri_finish<R><<<1, 32, 0, st>>>(rho, n, tau, dg, ec, eabs, delta);
   VB_CHECK_LAUNCH();
 values:
-  multisect_kernel<R><<<(k_want * 32 + 255) / 256, 256, 0, st>>>(dg, eabs, n, k_want, evals);
+  {
+    // FP64: one warp per block, so the warps (one per eigenvalue) land on
+    // separate SMs and do not share an FP64 pipe
+    const int mt = sizeof(R) == 8 ? 32 : 256;
+    multisect_kernel<R><<<(k_want * 32 + mt - 1) / mt, mt, 0, st>>>(dg, eabs, n, k_want, evals);
+  }
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
 
 template <class R>
 vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R *evals, cplx<R> *evecs,
-                      void *work, cudaStream_t st) {
+                      void *work, cudaStream_t st, int rounds_in) {
   typedef cplx<R> C_;
   (void)rho;
   if (k_vec < 1 || k_vec > k_want) return fail(VB_EINVAL, "eig_vectors: bad k_vec");
@@ -929,7 +937,7 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
   R *lu = reinterpret_cast<R *>(w + lay.off_lu);
   int *piv = reinterpret_cast<int *>(lu + (size_t)k_want * n * 4);
   // FP32 vectors only seed an FP64 Rayleigh-Ritz step: two rounds suffice there
-  const int rounds = sizeof(R) == 8 ? INVIT_ROUNDS : 2;
+  const int rounds = rounds_in > 0 ? std::min(rounds_in, INVIT_ROUNDS) : (sizeof(R) == 8 ? INVIT_ROUNDS : 2);
   for (int r = 0; r < rounds; ++r) {
     prof_begin(PH_INVIT, st);
     invit_round<R><<<(k_vec + 31) / 32, 32, 0, st>>>(dg, eabs, n, k_vec, evals, Y, lu, piv, r);
@@ -968,8 +976,8 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
 
 template vb_status eig_values<double>(int, cd *, int, double *, void *, cudaStream_t);
 template vb_status eig_values<float>(int, cf *, int, float *, void *, cudaStream_t);
-template vb_status eig_vectors<double>(int, const cd *, int, int, const double *, cd *, void *, cudaStream_t);
-template vb_status eig_vectors<float>(int, const cf *, int, int, const float *, cf *, void *, cudaStream_t);
+template vb_status eig_vectors<double>(int, const cd *, int, int, const double *, cd *, void *, cudaStream_t, int);
+template vb_status eig_vectors<float>(int, const cf *, int, int, const float *, cf *, void *, cudaStream_t, int);
 
 }  // namespace vb
 

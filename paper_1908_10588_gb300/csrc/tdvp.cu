@@ -87,6 +87,49 @@ __global__ void lowdin_kernel(cd *G, int r) {
   }
 }
 
+// w[i] = |row i of X|^2 (rows: X is kws x len) or |column i|^2 (X is len x kws)
+__global__ void ritz_weights_kernel(const cd *__restrict__ X, int kws, int len, int rows, double *w) {
+  __shared__ double sh[8];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int x = threadIdx.x; x < len; x += blockDim.x) s += cabs2(rows ? X[(long long)i * len + x] : X[(long long)x * kws + i]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += sh[j];
+    w[i] = t;
+  }
+}
+
+// rows perm[0..k) of src (rows of length len): mode 0 writes them as the
+// columns of dst (len x k), mode 1 as rows (k x len), mode 2 as conjugated rows
+__global__ void ritz_gather_kernel(const cd *__restrict__ src, int len, const int *__restrict__ perm, int k, int mode,
+                                   cd *__restrict__ dst) {
+  const long long tot = (long long)k * len;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    if (mode == 0) {
+      const int x = (int)(e / k), j = (int)(e % k);
+      dst[e] = src[(long long)perm[j] * len + x];
+    } else {
+      const int j = (int)(e / len), x = (int)(e % len);
+      const cd v = src[(long long)perm[j] * len + x];
+      dst[e] = mode == 2 ? cconj(v) : v;
+    }
+  }
+}
+
+// dst[x][j] = X[x][perm[j]] (X is rows x kws, dst rows x k)
+__global__ void ritz_cols_kernel(const cd *__restrict__ X, int rows, int kws, const int *__restrict__ perm, int k,
+                                 cd *__restrict__ dst) {
+  const long long tot = (long long)rows * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(e / k), j = (int)(e % k);
+    dst[e] = X[(long long)x * kws + perm[j]];
+  }
+}
+
 // FP64 copy of the FP32 basis rows, conjugated when conj != 0
 __global__ void subspace_rows_c64(const cf *__restrict__ q, cd *__restrict__ out, long long n, int conj) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -164,14 +207,15 @@ struct vb_mps {
   // subspace iteration of the mixed split
   cf *subZ = nullptr, *subT = nullptr, *subG = nullptr, *subW = nullptr, *skws32 = nullptr;
   long long skws32_elems = 0;
-  int *subflag = nullptr;
+  int *subflag = nullptr, *d_perm = nullptr;
   double *d_capt = nullptr;
+  float *ev32 = nullptr;
+  void *eigw32 = nullptr;
   unsigned long long split_calls = 0;
   // mixed split: FP32 eigenvectors of rho, FP64 Rayleigh-Ritz
   int rcap = 0;
   cf *M32 = nullptr, *Q32 = nullptr;
-  cd *Q64 = nullptr, *Qo = nullptr, *G = nullptr, *X = nullptr, *S = nullptr, *Zr = nullptr, *U = nullptr;
-  void *eigwS = nullptr;
+  cd *Q64 = nullptr, *Qo = nullptr, *G = nullptr, *X = nullptr;
   cd *skws = nullptr;  // split-K workspace of the Rayleigh-Ritz products
   long long skws_elems = 0;
   // mixed form: environment updates in complex FP32
@@ -528,13 +572,15 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old,
   return VB_OK;
 }
 
-// Mixed form of the split: the r = min(n, m_max + 17, 128) leading
-// eigenvectors of rho come from the FP32 eigensolver; the truncation itself
-// is done in FP64 by a Rayleigh-Ritz step on their span: the basis is
-// re-orthonormalised (one Lowdin step), S = Q^+ rho Q is formed from FP64
-// products with theta and diagonalised in FP64, and the kept weights, the
-// discarded weight (against tr rho = |theta|^2) and the new tensors all come
-// from the FP64 Ritz pairs.
+// Mixed form of the split (Sec. 2.1.1 truncation). The kept Schmidt
+// directions are found in FP32: subspace iteration on theta for the
+// r = min(n, m_max + 17, 128) leading eigenvectors of rho, then a
+// Rayleigh-Ritz step on their span (S = Q^* rho Q^T diagonalised in FP32) for
+// the kws = min(r, m_max + 1) leading Ritz vectors. Everything that defines
+// the new tensors is FP64: the Ritz basis is re-orthonormalised (one Lowdin
+// step), theta is projected on it, and the weights that the truncation rule
+// sees are the FP64 Rayleigh quotients |X_i|^2, so the discarded weight
+// reported is exactly the weight the chosen tensors drop.
 vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old, const TruncOpts &o,
                       cd *dstA, cd *dstC, int *k_out, double *disc) {
   cudaStream_t st = s->st;
@@ -608,55 +654,89 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     if (it >= 1 && std::fabs(capt - prev) <= SUBSPACE_RTOL * capt) break;
     prev = capt;
   }
-  // ---- FP64 Rayleigh-Ritz on the span of the rows of Q
-  prof_begin(PH_RR, st);
-  subspace_rows_c64<<<grid1((long long)r * n), 256, 0, st>>>(s->Q32, s->Q64, (long long)r * n, left ? 0 : 1);
-  VB_CHECK_LAUNCH();
-  const long long rn = (long long)r * n, rr = (long long)r * r;
-  VB_TRY(G64(r, r, n, OP_N, s->Q64, n, rn, OP_C, s->Q64, n, rn, s->G, r, rr));  // G = Q Q^+
-  lowdin_kernel<<<grid1(rr), 256, 0, st>>>(s->G, r);
-  VB_CHECK_LAUNCH();
-  VB_TRY(G64(r, n, r, OP_N, s->G, r, rr, OP_N, s->Q64, n, rn, s->Qo, n, rn));  // Qo = (3I - G)/2 Q
-  if (left) {
-    // X = conj(Qo) M  (r x n2);  S = X X^+
-    VB_TRY(G64(r, n2, n1, OP_R, s->Qo, n1, rn, OP_N, M, n2, nm, s->X, n2, (long long)r * n2));
-    VB_TRY(G64(r, r, n2, OP_N, s->X, n2, (long long)r * n2, OP_C, s->X, n2, (long long)r * n2, s->S, r, rr));
-  } else {
-    // X = M Qo^T  (n1 x r);  S = X^+ X
-    VB_TRY(G64(n1, r, n2, OP_N, M, n2, nm, OP_T, s->Qo, n2, rn, s->X, r, (long long)n1 * r));
-    VB_TRY(G64(r, r, n1, OP_C, s->X, r, (long long)n1 * r, OP_N, s->X, r, (long long)n1 * r, s->S, r, rr));
-  }
-  prof_end(PH_RR, st, 0.0);
+  // ---- Rayleigh-Ritz in FP32: rotate the basis to the kws leading Ritz vectors
   const int kws = std::min(r, kw);
-  VB_TRY(eig_values(r, s->S, kws, s->d_evals, s->eigwS, st));
-  std::vector<double> lam(kws);
+  prof_begin(PH_RR, st);
+  {
+    GemmArgsF g{};
+    g.M = r; g.N = nother; g.K = n; g.batch = 1;
+    g.opA = OP_R; g.A = s->Q32; g.lda = n;
+    g.opB = left ? OP_N : OP_T; g.B = s->M32; g.ldb = n2;
+    g.C = s->subZ; g.ldc = nother;
+    g.alpha = onef; g.beta = zerof;
+    g.a_size = (long long)r * n; g.b_size = nm; g.c_size = (long long)r * nother;
+    g.ws = s->skws32; g.ws_elems = s->skws32_elems;
+    VB_TRY(gemm<float>(g, st));
+    GemmArgsF h{};  // S32 = Z Z^+ = conj(Q) rho Q^T
+    h.M = r; h.N = r; h.K = nother; h.batch = 1;
+    h.opA = OP_N; h.A = s->subZ; h.lda = nother;
+    h.opB = OP_C; h.B = s->subZ; h.ldb = nother;
+    h.C = s->subG; h.ldc = r;
+    h.alpha = onef; h.beta = zerof;
+    h.a_size = (long long)r * nother; h.b_size = (long long)r * nother; h.c_size = (long long)r * r;
+    h.ws = s->skws32; h.ws_elems = s->skws32_elems;
+    VB_TRY(gemm<float>(h, st));
+  }
+  VB_TRY(eig_values<float>(r, s->subG, kws, s->ev32, s->eigw32, st));
+  VB_TRY(eig_vectors<float>(r, s->subG, kws, kws, s->ev32, s->subW, s->eigw32, st));
+  {
+    GemmArgsF g{};  // Ritz basis: rows of W Q (kws x n)
+    g.M = kws; g.N = n; g.K = r; g.batch = 1;
+    g.opA = OP_N; g.A = s->subW; g.lda = r;
+    g.opB = OP_N; g.B = s->Q32; g.ldb = n;
+    g.C = s->subT; g.ldc = n;
+    g.alpha = onef; g.beta = zerof;
+    g.a_size = (long long)kws * r; g.b_size = (long long)r * n; g.c_size = (long long)kws * n;
+    VB_TRY(gemm<float>(g, st));
+  }
+  // ---- FP64: orthonormal Ritz basis Qo, X = theta projected on it, and the
+  // kept weights as FP64 Rayleigh quotients |X_i|^2
+  subspace_rows_c64<<<grid1((long long)kws * n), 256, 0, st>>>(s->subT, s->Q64, (long long)kws * n, left ? 0 : 1);
+  VB_CHECK_LAUNCH();
+  const long long rn = (long long)kws * n, rr = (long long)kws * kws;
+  VB_TRY(G64(kws, kws, n, OP_N, s->Q64, n, rn, OP_C, s->Q64, n, rn, s->G, kws, rr));  // G = Q Q^+
+  lowdin_kernel<<<grid1(rr), 256, 0, st>>>(s->G, kws);
+  VB_CHECK_LAUNCH();
+  VB_TRY(G64(kws, n, kws, OP_N, s->G, kws, rr, OP_N, s->Q64, n, rn, s->Qo, n, rn));  // Qo = (3I - G)/2 Q
+  if (left)  // X = conj(Qo) M  (kws x n2)
+    VB_TRY(G64(kws, n2, n1, OP_R, s->Qo, n1, rn, OP_N, M, n2, nm, s->X, n2, (long long)kws * n2));
+  else  // X = M Qo^T  (n1 x kws)
+    VB_TRY(G64(n1, kws, n2, OP_N, M, n2, nm, OP_T, s->Qo, n2, rn, s->X, kws, (long long)n1 * kws));
+  ritz_weights_kernel<<<kws, 256, 0, st>>>(s->X, kws, left ? n2 : n1, left ? 1 : 0, s->d_evals);
+  VB_CHECK_LAUNCH();
+  prof_end(PH_RR, st, 0.0);
+  std::vector<double> w(kws);
   double nrm = 0.0;
-  VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), s->d_evals, kws * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaMemcpyAsync(w.data(), s->d_evals, kws * sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaMemcpyAsync(&nrm, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaStreamSynchronize(st));
-  VB_TRY(EigWork::check(r, kws, sizeof(double), s->eigwS, st));
+  VB_TRY(EigWork::check(r, kws, 4, s->eigw32, st));
   prof_end(PH_EIGVAL, st, 0.0);
+  for (double v : w)
+    if (!(v == v)) return fail(VB_ECUDA, "split: NaN in the Ritz weights");
+  std::vector<int> perm(kws);
+  for (int i = 0; i < kws; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return w[a] > w[b]; });
+  std::vector<double> lam(kws);
+  for (int i = 0; i < kws; ++i) lam[i] = w[perm[i]];
   const int k = choose_rank(lam, n, nrm * nrm, std::min(n1, n2), o, disc);
-  prof_begin(PH_EIGVEC, st);
-  VB_TRY(eig_vectors(r, s->S, kws, k, s->d_evals, s->Zr, s->eigwS, st));
-  prof_end(PH_EIGVEC, st, 0.0);
   prof_begin(PH_SPLITOUT, st);
-  const long long kr = (long long)k * r;
+  VB_TRY_CUDA(cudaMemcpyAsync(s->d_perm, perm.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
   if (left) {
-    // Ritz vectors U = Z Qo (k x n1): A = U^T; C = conj(Z) X (k x n2)
-    VB_TRY(G64(k, n1, r, OP_N, s->Zr, r, kr, OP_N, s->Qo, n1, rn, s->U, n1, (long long)k * n1));
-    transpose_kernel<<<grid1((long long)k * n1), 256, 0, st>>>(s->U, k, n1, dstA);
+    // A[x][j] = Qo[perm_j][x];  C[j][y] = X[perm_j][y]
+    ritz_gather_kernel<<<grid1((long long)k * n1), 256, 0, st>>>(s->Qo, n1, s->d_perm, k, 0, dstA);
     VB_CHECK_LAUNCH();
-    VB_TRY(G64(k, n2, r, OP_R, s->Zr, r, kr, OP_N, s->X, n2, (long long)r * n2, dstC, n2, (long long)k * n2));
+    ritz_gather_kernel<<<grid1((long long)k * n2), 256, 0, st>>>(s->X, n2, s->d_perm, k, 1, dstC);
+    VB_CHECK_LAUNCH();
     const long long nc = (long long)k * n2;
     VB_TRY(vec_norm2(dstC, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
     VB_TRY(vec_scale_inv(dstC, nc, s->d_nrm, st));
   } else {
-    // Ritz vectors V = Z Qo (k x n2): B = conj(V); C = X Z^T (n1 x k)
-    VB_TRY(G64(k, n2, r, OP_N, s->Zr, r, kr, OP_N, s->Qo, n2, rn, s->U, n2, (long long)k * n2));
-    conj_copy_kernel<<<grid1((long long)k * n2), 256, 0, st>>>(s->U, (long long)k * n2, dstC);
+    // B[j][y] = conj(Qo[perm_j][y]);  C[x][j] = X[x][perm_j]
+    ritz_gather_kernel<<<grid1((long long)k * n2), 256, 0, st>>>(s->Qo, n2, s->d_perm, k, 2, dstC);
     VB_CHECK_LAUNCH();
-    VB_TRY(G64(n1, k, r, OP_N, s->X, r, (long long)n1 * r, OP_T, s->Zr, r, kr, dstA, k, (long long)n1 * k));
+    ritz_cols_kernel<<<grid1((long long)n1 * k), 256, 0, st>>>(s->X, n1, kws, s->d_perm, k, dstA);
+    VB_CHECK_LAUNCH();
     const long long nc = (long long)n1 * k;
     VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
     VB_TRY(vec_scale_inv(dstA, nc, s->d_nrm, st));
@@ -826,17 +906,16 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       A2((void **)&s->subW, (size_t)rc * rc * sizeof(cf));
       A2((void **)&s->subflag, (size_t)(rc + 1) * sizeof(int));
       A2((void **)&s->d_capt, 256);
+      A2((void **)&s->d_perm, (size_t)rc * sizeof(int));
+      A2((void **)&s->ev32, (size_t)rc * sizeof(float));
+      A2(&s->eigw32, EigWork::bytes((int)rc, (int)rc, 4));
       s->skws32_elems = 48LL * rc * nr2;
       A2((void **)&s->skws32, (size_t)s->skws32_elems * sizeof(cf));
       A2((void **)&s->Q32, (size_t)rc * nr2 * sizeof(cf));
       A2((void **)&s->Q64, (size_t)rc * nr2 * sizeof(cd));
       A2((void **)&s->Qo, (size_t)rc * nr2 * sizeof(cd));
-      A2((void **)&s->U, (size_t)rc * nr2 * sizeof(cd));
       A2((void **)&s->X, (size_t)rc * nr2 * sizeof(cd));
       A2((void **)&s->G, (size_t)rc * rc * sizeof(cd));
-      A2((void **)&s->S, (size_t)rc * rc * sizeof(cd));
-      A2((void **)&s->Zr, (size_t)rc * rc * sizeof(cd));
-      A2(&s->eigwS, EigWork::bytes((int)rc, (int)rc, 8));
       s->skws_elems = 48LL * rc * nr2;
       A2((void **)&s->skws, (size_t)s->skws_elems * sizeof(cd));
       for (int p = 0; p <= n; ++p) {
