@@ -61,6 +61,11 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = mkc<R>(0, 0);
+  // rows of this thread: i0 + ty + 16 r; a warp holds ty = 2w, 2w + 1, so
+  // the number of row groups r with a valid row is the same for the warp
+  const int wrow = i0 + 2 * (tid >> 5);
+  const int rwarp = max(0, min(4, (g.M - wrow + 15) / 16));
+  const bool rfull = i0 + BM <= g.M;
 
   for (int k0 = 0; k0 < Kb; k0 += BK) {
 #pragma unroll
@@ -89,22 +94,44 @@ __global__ void __launch_bounds__(NT) zgemm_kernel(GemmArgsT<R> g) {
       Bs[kk][jj] = (gj < g.N && gk < Kb) ? ldB<R>(B, g.opB, g.ldb, gk, gj) : mkc<R>(0, 0);
     }
     __syncthreads();
+    if (rfull) {
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      C_ a[4], bb[4];
+      for (int kk = 0; kk < BK; ++kk) {
+        C_ a[4], bb[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bb[c] = Bs[kk][tx + 16 * c];
+        for (int c = 0; c < 4; ++c) bb[c] = Bs[kk][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          acc[r][c].x = fma(a[r].x, bb[c].x, acc[r][c].x);
-          acc[r][c].x = fma(-a[r].y, bb[c].y, acc[r][c].x);
-          acc[r][c].y = fma(a[r].x, bb[c].y, acc[r][c].y);
-          acc[r][c].y = fma(a[r].y, bb[c].x, acc[r][c].y);
+          for (int c = 0; c < 4; ++c) {
+            acc[r][c].x = fma(a[r].x, bb[c].x, acc[r][c].x);
+            acc[r][c].x = fma(-a[r].y, bb[c].y, acc[r][c].x);
+            acc[r][c].y = fma(a[r].x, bb[c].y, acc[r][c].y);
+            acc[r][c].y = fma(a[r].y, bb[c].x, acc[r][c].y);
+          }
+      }
+    } else if (rwarp > 0) {
+      // ragged last row tile: only the warp-uniform row groups that hold
+      // valid rows do arithmetic (FP64 issue slots are the scarce resource)
+      for (int kk = 0; kk < BK; ++kk) {
+        C_ bb[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bb[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (r >= rwarp) break;
+          const C_ a = As[kk][ty + 16 * r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            acc[r][c].x = fma(a.x, bb[c].x, acc[r][c].x);
+            acc[r][c].x = fma(-a.y, bb[c].y, acc[r][c].x);
+            acc[r][c].y = fma(a.x, bb[c].y, acc[r][c].y);
+            acc[r][c].y = fma(a.y, bb[c].x, acc[r][c].y);
+          }
         }
+      }
     }
     __syncthreads();
   }

@@ -87,7 +87,7 @@ __global__ void lowdin_kernel(cd *G, int r) {
   }
 }
 
-// w[i] = |row i of X|^2 (rows: X is kws x len) or |column i|^2 (X is len x kws)
+// w[i] = |row i of X|^2 (X is kws x len, or len x kws when rows == 0: columns)
 __global__ void ritz_weights_kernel(const cd *__restrict__ X, int kws, int len, int rows, double *w) {
   __shared__ double sh[8];
   const int i = blockIdx.x;
@@ -117,16 +117,6 @@ __global__ void ritz_gather_kernel(const cd *__restrict__ src, int len, const in
       const cd v = src[(long long)perm[j] * len + x];
       dst[e] = mode == 2 ? cconj(v) : v;
     }
-  }
-}
-
-// dst[x][j] = X[x][perm[j]] (X is rows x kws, dst rows x k)
-__global__ void ritz_cols_kernel(const cd *__restrict__ X, int rows, int kws, const int *__restrict__ perm, int k,
-                                 cd *__restrict__ dst) {
-  const long long tot = (long long)rows * k;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(e / k), j = (int)(e % k);
-    dst[e] = X[(long long)x * kws + perm[j]];
   }
 }
 
@@ -700,9 +690,9 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
   VB_TRY(G64(kws, n, kws, OP_N, s->G, kws, rr, OP_N, s->Q64, n, rn, s->Qo, n, rn));  // Qo = (3I - G)/2 Q
   if (left)  // X = conj(Qo) M  (kws x n2)
     VB_TRY(G64(kws, n2, n1, OP_R, s->Qo, n1, rn, OP_N, M, n2, nm, s->X, n2, (long long)kws * n2));
-  else  // X = M Qo^T  (n1 x kws)
-    VB_TRY(G64(n1, kws, n2, OP_N, M, n2, nm, OP_T, s->Qo, n2, rn, s->X, kws, (long long)n1 * kws));
-  ritz_weights_kernel<<<kws, 256, 0, st>>>(s->X, kws, left ? n2 : n1, left ? 1 : 0, s->d_evals);
+  else  // X^T = Qo M^T  (kws x n1), rows for the GEMM's sake
+    VB_TRY(G64(kws, n1, n2, OP_N, s->Qo, n2, rn, OP_T, M, n2, nm, s->X, n1, (long long)kws * n1));
+  ritz_weights_kernel<<<kws, 256, 0, st>>>(s->X, kws, left ? n2 : n1, 1, s->d_evals);
   VB_CHECK_LAUNCH();
   prof_end(PH_RR, st, 0.0);
   std::vector<double> w(kws);
@@ -732,10 +722,10 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     VB_TRY(vec_norm2(dstC, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
     VB_TRY(vec_scale_inv(dstC, nc, s->d_nrm, st));
   } else {
-    // B[j][y] = conj(Qo[perm_j][y]);  C[x][j] = X[x][perm_j]
+    // B[j][y] = conj(Qo[perm_j][y]);  C[x][j] = X^T[perm_j][x]
     ritz_gather_kernel<<<grid1((long long)k * n2), 256, 0, st>>>(s->Qo, n2, s->d_perm, k, 2, dstC);
     VB_CHECK_LAUNCH();
-    ritz_cols_kernel<<<grid1((long long)n1 * k), 256, 0, st>>>(s->X, n1, kws, s->d_perm, k, dstA);
+    ritz_gather_kernel<<<grid1((long long)n1 * k), 256, 0, st>>>(s->X, n1, s->d_perm, k, 0, dstA);
     VB_CHECK_LAUNCH();
     const long long nc = (long long)n1 * k;
     VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
