@@ -210,14 +210,17 @@ unsigned long long vb_kernel_launches(void);
  * updates, 5 = merge of two sites; sub-phases of 3: 6 = reduced density
  * matrix, 7 = tridiagonal reduction and eigenvalues, 8 = eigenvectors,
  * 9 = new tensors and normalisation; in the mixed form 10 and 11 are the
- * FP32 eigenvalue and eigenvector stages inside 7; 12, 13, 14 are the
+ * products and the orthonormalisations of the subspace iteration inside 7,
+ * 15 its Rayleigh-Ritz step, split into 16 (FP32 Ritz vectors) and 17 (FP64
+ * basis, projection and weights), and 18 / 19 the Cholesky kernels and the
+ * Gram and transform products of the orthonormalisations; 12, 13, 14 are the
  * inverse iteration, Gram-Schmidt and back-transformation parts of every
  * eigenvector stage). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
  * multiply-add is 8, real-times-complex 4, an identity-block add 2). */
 typedef struct {
-  double ms[16];
-  long long calls[16];
+  double ms[24];
+  long long calls[24];
   double heff_flops[2];
 } vb_profile;
 vb_status vb_profile_enable(int on);

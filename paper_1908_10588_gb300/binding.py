@@ -58,12 +58,13 @@ class vb_tdvp_opts(C.Structure):
 
 
 class vb_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 16), ("calls", C.c_longlong * 16), ("heff_flops", C.c_double * 2)]
+    _fields_ = [("ms", C.c_double * 24), ("calls", C.c_longlong * 24), ("heff_flops", C.c_double * 2)]
 
 
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
           "split_out", "split_subspace_products", "split_subspace_orth", "eigvec_invit", "eigvec_gram_schmidt",
-          "eigvec_backtransform", "split_rayleigh_ritz_products"]
+          "eigvec_backtransform", "split_rayleigh_ritz", "split_ritz_fp32", "split_ritz_fp64",
+          "split_orth_cholesky", "split_orth_products"]
 
 
 class vb_sweep_stats(C.Structure):

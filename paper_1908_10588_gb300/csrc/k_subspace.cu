@@ -51,25 +51,28 @@ __global__ void fill_flagged_kernel(cf *__restrict__ Q, int r, int n, const int 
   }
 }
 
-// One CTA. G = A A^+ (r x r). With D = diag(G)^(-1/2), factor D G D = L L^+
-// (lower) and write W = L^-1 D (r x r), so that W A has orthonormal rows. A
-// row whose scaled pivot is <= tau (its part orthogonal to the rows before it
-// is below sqrt(tau) of its length) gets a zero row in W and flag 1;
-// flag[r] counts them. Shared memory: r*r complex + 2 r words; the strictly
-// upper triangle of L holds the strictly lower triangle of L^-1, transposed.
-constexpr int CHOL_THREADS = 512;
+// One CTA. G = A A^+ (r x r). With D = diag(G)^(-1/2), factor
+// D G D = L P L^+ (L unit lower triangular, P = diag(p_j)) and write
+// W = P^(-1/2) L^-1 D, so that W A has orthonormal rows. A row whose pivot
+// p_j is <= tau (its part orthogonal to the rows before it is below
+// sqrt(tau) of its length) gets a zero row in W and flag 1; flag[r] counts
+// them.
+// Step j eliminates column j and at the same time applies the same row
+// operation to M = L^-1 (M_ic -= l_ij M_jc for c < j, M_ij = -l_ij), so each
+// step needs a single barrier. The lower triangle holds the elimination,
+// the strictly upper triangle holds M transposed.
+constexpr int CHOL_THREADS = 1024;
 __global__ void __launch_bounds__(CHOL_THREADS) chol_rows_kernel(const cf *__restrict__ G, int r, float tau,
                                                                  cf *__restrict__ W, int *__restrict__ flag) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
-  cf *L = reinterpret_cast<cf *>(chol_smem);
-  float *dsc = reinterpret_cast<float *>(L + (size_t)r * r);
-  int *bad = reinterpret_cast<int *>(dsc + r);
-  __shared__ float dinv[128];
+  cf *S = reinterpret_cast<cf *>(chol_smem);
+  float *dsc = reinterpret_cast<float *>(S + (size_t)r * r);
+  float *piv = dsc + r;  // p_j, 0 for a rejected row
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int i = tid; i < r; i += nt) {
     const float g = G[(long long)i * r + i].x;
     dsc[i] = g > 0.f ? 1.0f / sqrtf(g) : 0.f;
-    bad[i] = 0;
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += nt) {
@@ -77,79 +80,55 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_rows_kernel(const cf *__res
     if (j <= i) {
       const cf g = G[e];
       const float s = dsc[i] * dsc[j];
-      L[e] = mkc(g.x * s, g.y * s);
+      S[e] = mkc(g.x * s, g.y * s);
     }
   }
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    const float p = L[j * r + j].x;
-    const bool fail = !(p > tau);
-    __syncthreads();
-    if (fail) {
-      for (int i = j + tid; i < r; i += nt) L[i * r + j] = mkc(0.f, 0.f);
-      if (tid == 0) bad[j] = 1;
-      __syncthreads();
-      continue;
-    }
-    const float ljj = sqrtf(p), inv = 1.0f / ljj;
-    for (int i = j + 1 + tid; i < r; i += nt) {
-      const cf v = L[i * r + j];
-      L[i * r + j] = mkc(v.x * inv, v.y * inv);
-    }
-    if (tid == 0) L[j * r + j] = mkc(ljj, 0.f);
-    __syncthreads();
-    const int m = r - j - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      const int ii = e / m, cc = e % m;
-      if (cc > ii) continue;
-      const int i = j + 1 + ii, c = j + 1 + cc;
-      const cf a = L[i * r + j], b = L[c * r + j];
-      const cf cur = L[i * r + c];
-      L[i * r + c] = mkc(cur.x - (a.x * b.x + a.y * b.y), cur.y - (a.y * b.x - a.x * b.y));
-    }
-    __syncthreads();
-  }
-  // inverse by forward substitution, one thread per column c:
-  // x_i = (delta_ic - sum_{c<=k<i} L_ik x_k) / L_ii, x_c kept in dinv[c]
-  for (int c = tid; c < r; c += nt) {
-    const float xc = bad[c] ? 0.f : 1.0f / L[c * r + c].x;
-    dinv[c] = xc;
-    for (int i = c + 1; i < r; ++i) {
-      cf s = mkc(0.f, 0.f);
-      if (!bad[i]) {
-        {
-          const cf a = L[i * r + c];
-          s = mkc(-a.x * xc, -a.y * xc);
+    const float p = S[j * r + j].x;
+    const bool ok = p > tau;
+    const float inv = ok ? 1.0f / p : 0.f;
+    // warps take rows i > j, lanes the columns c <= i
+    for (int i = j + 1 + wid; i < r; i += nw) {
+      const cf a = S[i * r + j];
+      const float lx = a.x * inv, ly = a.y * inv;
+      for (int c = lane; c <= i; c += 32) {
+        if (!ok) {
+          if (c == j) S[j * r + i] = mkc(0.f, 0.f);
+          continue;
         }
-        for (int k = c + 1; k < i; ++k) {
-          const cf a = L[i * r + k], x = L[c * r + k];
-          s.x -= a.x * x.x - a.y * x.y;
-          s.y -= a.x * x.y + a.y * x.x;
+        if (c > j) {  // trailing update of the lower triangle
+          const cf b = S[c * r + j];
+          const cf cur = S[i * r + c];
+          S[i * r + c] = mkc(cur.x - (lx * b.x + ly * b.y), cur.y - (ly * b.x - lx * b.y));
+        } else if (c < j) {  // M_ic -= l_ij M_jc
+          const cf mj = S[c * r + j];
+          const cf cur = S[c * r + i];
+          S[c * r + i] = mkc(cur.x - (lx * mj.x - ly * mj.y), cur.y - (lx * mj.y + ly * mj.x));
+        } else {  // M_ij = -l_ij
+          S[j * r + i] = mkc(-lx, -ly);
         }
-        const float li = 1.0f / L[i * r + i].x;
-        s = mkc(s.x * li, s.y * li);
       }
-      L[c * r + i] = s;
     }
+    if (tid == 0) piv[j] = ok ? p : 0.f;
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < r * r; e += nt) {
     const int i = e / r, c = e % r;
     cf w = mkc(0.f, 0.f);
-    if (i == c)
-      w = mkc(dinv[c], 0.f);
-    else if (i > c)
-      w = L[c * r + i];
-    if (bad[i]) w = mkc(0.f, 0.f);
-    const float s = dsc[c];
-    W[e] = mkc(w.x * s, w.y * s);
+    if (piv[i] > 0.f && c <= i) {
+      const cf mv = c == i ? mkc(1.f, 0.f) : S[c * r + i];
+      const float s = dsc[c] / sqrtf(piv[i]);
+      w = mkc(mv.x * s, mv.y * s);
+    }
+    W[e] = w;
   }
   if (tid == 0) {
     int cnt = 0;
-    for (int i = 0; i < r; ++i) cnt += bad[i];
+    for (int i = 0; i < r; ++i) cnt += piv[i] > 0.f ? 0 : 1;
     flag[r] = cnt;
   }
-  for (int i = tid; i < r; i += nt) flag[i] = bad[i];
+  for (int i = tid; i < r; i += nt) flag[i] = piv[i] > 0.f ? 0 : 1;
 }
 
 __global__ void __launch_bounds__(256) norm2_f32_part(const cf *__restrict__ x, long long n,
@@ -210,16 +189,22 @@ static vb_status orth_pass(const cf *A, cf *T, int r, int n, const SubspaceWork 
   g.alpha = mkc(1.f, 0.f); g.beta = mkc(0.f, 0.f);
   g.a_size = (long long)r * n; g.b_size = (long long)r * n; g.c_size = (long long)r * r;
   g.ws = w.ws; g.ws_elems = w.ws_elems;
+  prof_begin(PH_ORTHGEMM, st);
   VB_TRY(gemm<float>(g, st));
+  prof_end(PH_ORTHGEMM, st, 0.0);
+  prof_begin(PH_CHOL, st);
   chol_rows_kernel<<<1, CHOL_THREADS, subspace_chol_smem(r), st>>>(w.G, r, 1e-4f, w.W, w.flag);
   VB_CHECK_LAUNCH();
+  prof_end(PH_CHOL, st, 0.0);
   GemmArgsF h{};
   h.M = r; h.N = n; h.K = r; h.batch = 1;
   h.opA = OP_N; h.opB = OP_N;
   h.A = w.W; h.lda = r; h.B = A; h.ldb = n; h.C = T; h.ldc = n;
   h.alpha = mkc(1.f, 0.f); h.beta = mkc(0.f, 0.f);
   h.a_size = (long long)r * r; h.b_size = (long long)r * n; h.c_size = (long long)r * n;
+  prof_begin(PH_ORTHGEMM, st);
   VB_TRY(gemm<float>(h, st));
+  prof_end(PH_ORTHGEMM, st, 0.0);
   fill_flagged_kernel<<<grid_of((long long)r * n), 256, 0, st>>>(T, r, n, w.flag, seed);
   VB_CHECK_LAUNCH();
   return VB_OK;

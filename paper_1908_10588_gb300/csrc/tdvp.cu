@@ -647,6 +647,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
   // ---- Rayleigh-Ritz in FP32: rotate the basis to the kws leading Ritz vectors
   const int kws = std::min(r, kw);
   prof_begin(PH_RR, st);
+  prof_begin(PH_RR32, st);
   {
     GemmArgsF g{};
     g.M = r; g.N = nother; g.K = n; g.batch = 1;
@@ -679,8 +680,10 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     g.a_size = (long long)kws * r; g.b_size = (long long)r * n; g.c_size = (long long)kws * n;
     VB_TRY(gemm<float>(g, st));
   }
+  prof_end(PH_RR32, st, 0.0);
   // ---- FP64: orthonormal Ritz basis Qo, X = theta projected on it, and the
   // kept weights as FP64 Rayleigh quotients |X_i|^2
+  prof_begin(PH_RR64, st);
   subspace_rows_c64<<<grid1((long long)kws * n), 256, 0, st>>>(s->subT, s->Q64, (long long)kws * n, left ? 0 : 1);
   VB_CHECK_LAUNCH();
   const long long rn = (long long)kws * n, rr = (long long)kws * kws;
@@ -694,6 +697,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     VB_TRY(G64(kws, n1, n2, OP_N, s->Qo, n2, rn, OP_T, M, n2, nm, s->X, n1, (long long)kws * n1));
   ritz_weights_kernel<<<kws, 256, 0, st>>>(s->X, kws, left ? n2 : n1, 1, s->d_evals);
   VB_CHECK_LAUNCH();
+  prof_end(PH_RR64, st, 0.0);
   prof_end(PH_RR, st, 0.0);
   std::vector<double> w(kws);
   double nrm = 0.0;
