@@ -85,7 +85,8 @@ def test_mixed_sweeps_dbss(P):
 
 def test_mixed_sweeps_large_split_rayleigh_ritz(P):
     # bonds up to 32 with d = 12..16: reduced density matrices of dimension
-    # > 192 go through the FP32-eigenvector + FP64 Rayleigh-Ritz split
+    # > 192 go through the subspace-iteration split (FP32 directions, FP64
+    # basis, projection and weights)
     m = vm.model_internal_conversion(seed=41, n_modes=5, level_range=(12, 16), n_offdiag=2, n_bilinear=4)
     dims = vm.local_dims(m)
     ts = vm.random_right_canonical_mps(77, dims, 32)
