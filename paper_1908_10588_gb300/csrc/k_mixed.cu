@@ -191,24 +191,28 @@ __global__ void __launch_bounds__(128) wapply_planar_kernel(const int *__restric
 // Blocks are ordered with the chunk slowest, so the (s', w') blocks of one
 // chunk run together and share its input rows in L2.
 constexpr int WV4_J = 4;
-__global__ void __launch_bounds__(128) wapply_planar_v4_kernel(
+// 32-bit element offsets (both buffers are below 2^31 elements; checked on
+// the host), so the per-thread row offsets take one register each
+struct V4Strides {
+  int xp, xw, xs, xplane, yp, yw, ys, yplane;
+};
+__global__ void __launch_bounds__(128, 8) wapply_planar_v4_kernel(
     const int *__restrict__ rp, const int *__restrict__ col, const float *__restrict__ val,
     const int *__restrict__ ptr, const int *__restrict__ ent, int d, int Wp, int P, int Q4,
-    const float *__restrict__ X, long long xplane, WStrides xs, float *__restrict__ Y, long long yplane, WStrides ys) {
+    const float *__restrict__ X, float *__restrict__ Y, V4Strides s) {
   const int b = blockIdx.x;
   const int wo = b % Wp, t = b / Wp;
   const int so = t % d, chunk = t / d;
   const int npair = P * Q4;
-  const float *xb[WV4_J];
-  float *yb[WV4_J];
+  int xo[WV4_J], yo[WV4_J];
   bool ok[WV4_J];
 #pragma unroll
   for (int j = 0; j < WV4_J; ++j) {
     const int i = chunk * (128 * WV4_J) + threadIdx.x + 128 * j;
     ok[j] = i < npair;
     const int p = ok[j] ? i / Q4 : 0, q4 = ok[j] ? i % Q4 : 0;
-    xb[j] = X + p * xs.p + 4 * q4;
-    yb[j] = Y + p * ys.p + so * ys.s + wo * ys.w + 4 * q4;
+    xo[j] = p * s.xp + 4 * q4;
+    yo[j] = p * s.yp + so * s.ys + wo * s.yw + 4 * q4;
   }
   float4 ar[WV4_J], ai[WV4_J];
 #pragma unroll
@@ -216,14 +220,14 @@ __global__ void __launch_bounds__(128) wapply_planar_v4_kernel(
   const int e1 = ptr[wo + 1];
   for (int e = ptr[wo]; e < e1; ++e) {
     const int wi = ent[3 * e], ident = ent[3 * e + 1], off = ent[3 * e + 2];
-    const long long ow = wi * xs.w;
+    const int ow = wi * s.xw;
     if (ident) {
-      const long long o = ow + so * xs.s;
+      const float *xr = X + (ow + so * s.xs);
 #pragma unroll
       for (int j = 0; j < WV4_J; ++j) {
         if (!ok[j]) continue;
-        const float4 vr = *reinterpret_cast<const float4 *>(xb[j] + o);
-        const float4 vi = *reinterpret_cast<const float4 *>(xb[j] + o + xplane);
+        const float4 vr = *reinterpret_cast<const float4 *>(xr + xo[j]);
+        const float4 vi = *reinterpret_cast<const float4 *>(xr + xo[j] + s.xplane);
         ar[j].x += vr.x; ar[j].y += vr.y; ar[j].z += vr.z; ar[j].w += vr.w;
         ai[j].x += vi.x; ai[j].y += vi.y; ai[j].z += vi.z; ai[j].w += vi.w;
       }
@@ -231,12 +235,12 @@ __global__ void __launch_bounds__(128) wapply_planar_v4_kernel(
       const int k1 = rp[off + so + 1];
       for (int kk = rp[off + so]; kk < k1; ++kk) {
         const float c = val[kk];
-        const long long o = ow + col[kk] * xs.s;
+        const float *xr = X + (ow + col[kk] * s.xs);
 #pragma unroll
         for (int j = 0; j < WV4_J; ++j) {
           if (!ok[j]) continue;
-          const float4 vr = *reinterpret_cast<const float4 *>(xb[j] + o);
-          const float4 vi = *reinterpret_cast<const float4 *>(xb[j] + o + xplane);
+          const float4 vr = *reinterpret_cast<const float4 *>(xr + xo[j]);
+          const float4 vi = *reinterpret_cast<const float4 *>(xr + xo[j] + s.xplane);
           ar[j].x = fmaf(c, vr.x, ar[j].x); ar[j].y = fmaf(c, vr.y, ar[j].y);
           ar[j].z = fmaf(c, vr.z, ar[j].z); ar[j].w = fmaf(c, vr.w, ar[j].w);
           ai[j].x = fmaf(c, vi.x, ai[j].x); ai[j].y = fmaf(c, vi.y, ai[j].y);
@@ -248,8 +252,8 @@ __global__ void __launch_bounds__(128) wapply_planar_v4_kernel(
 #pragma unroll
   for (int j = 0; j < WV4_J; ++j) {
     if (!ok[j]) continue;
-    *reinterpret_cast<float4 *>(yb[j]) = ar[j];
-    *reinterpret_cast<float4 *>(yb[j] + yplane) = ai[j];
+    *reinterpret_cast<float4 *>(Y + yo[j]) = ar[j];
+    *reinterpret_cast<float4 *>(Y + yo[j] + s.yplane) = ai[j];
   }
 }
 
@@ -267,13 +271,13 @@ vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStr
   auto al16 = [](long long v) { return (v & 3) == 0; };
   if (xs.q == 1 && ys.q == 1 && Q % 4 == 0 && al16(xs.p) && al16(xs.w) && al16(xs.s) && al16(xplane) &&
       al16(ys.p) && al16(ys.w) && al16(ys.s) && al16(yplane) && ((uintptr_t)X & 15) == 0 &&
-      ((uintptr_t)Y & 15) == 0 && (long long)P * (Q / 4) <= INT_MAX - 128 * WV4_J) {
+      ((uintptr_t)Y & 15) == 0 && x_size <= INT_MAX && y_size <= INT_MAX) {
     const long long chunks = ((long long)P * (Q / 4) + 128 * WV4_J - 1) / (128 * WV4_J);
     const long long blocks = chunks * d * Wp;
     if (blocks <= INT_MAX) {
+      const V4Strides sv{(int)xs.p, (int)xs.w, (int)xs.s, (int)xplane, (int)ys.p, (int)ys.w, (int)ys.s, (int)yplane};
       wapply_planar_v4_kernel<<<(unsigned)blocks, 128, 0, st>>>(S.d_csr_ptr, S.d_csr_col, S.d_csr_val32, S.d_fwd_ptr,
-                                                                S.d_fwd_ent, d, Wp, P, Q / 4, X, xplane, xs, Y,
-                                                                yplane, ys);
+                                                                S.d_fwd_ent, d, Wp, P, Q / 4, X, Y, sv);
       VB_CHECK_LAUNCH();
       return VB_OK;
     }
