@@ -3,17 +3,20 @@
 //
 //   D[m, n] = sum_k A[m, k] * B[n, k]      (A: M x K, B: N x K, both K-major fp32)
 //
-// One CTA computes a 128 x 128 tile of D. Operands are staged by TMA into
-// 128-byte-swizzled shared memory (boxes of 32 K-elements x 128 rows) in a
-// STAGES-deep ring guarded by mbarriers; one elected thread issues
-// tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8 per instruction) into a
-// TMEM accumulator of 128 lanes x 128 columns; eight epilogue warps (two per
-// TMEM lane quarter, one column half each) read the accumulator with
-// tcgen05.ld and store it. Complex products use the real
-// embedding prepared by the caller (k_mixed.cu).
+// Persistent kernel: one CTA per SM walks the 128 x 128 tiles of D
+// (t = blockIdx.x, blockIdx.x + gridDim.x, ..., M tiles fastest, so that
+// consecutive tiles share their B rows in L2). Operands are staged by TMA
+// into 128-byte-swizzled shared memory (boxes of 32 K-elements x 128 rows) in
+// a STAGES-deep ring guarded by mbarriers that runs on across tiles; one
+// elected thread issues tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8 per
+// instruction) into one of two TMEM accumulators of 128 lanes x 128 columns,
+// so that four epilogue warps (one per TMEM lane quarter) read and store
+// tile t with tcgen05.ld while the tensor core already works on tile t + 1.
+// Complex products use the real embedding prepared by the caller
+// (k_mixed.cu).
 //
-// Split-TF32 (SPLIT = true): while the main loop runs, the eight epilogue
-// warps split every landed stage x = hi + lo with hi = x truncated to tf32
+// Split-TF32 (SPLIT = true): while the main loop runs, eight split warps
+// split every landed stage x = hi + lo with hi = x truncated to tf32
 // (written back in place, so it is exact in tf32) and lo = x - hi (exact in
 // fp32) into a second buffer; the MMA thread then issues three products per
 // k-step, A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated in FP32. The lo*lo
@@ -25,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <mutex>
 
 #include "common.h"
@@ -33,10 +37,12 @@ namespace vb {
 namespace {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;
-constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 split + epilogue
-constexpr int TC_EPI_THREADS = TC_THREADS - 64;
+constexpr int TC_SPLIT_WARPS = 8, TC_EPI_WARPS = 4;
+// warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 split, warps 10..13 epilogue
+constexpr int TC_THREADS = 32 * (2 + TC_SPLIT_WARPS + TC_EPI_WARPS);
+constexpr int TC_SPLIT_THREADS = 32 * TC_SPLIT_WARPS;
 constexpr uint32_t TC_STAGE_A = TC_BM * TC_BK * 4, TC_STAGE_B = TC_BN * TC_BK * 4;
-constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr uint32_t TC_TMEM_COLS = 256;  // two accumulators of 128 columns
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;  // polls before a wait is declared failed
 template <bool SPLIT>
 struct TcCfg {
@@ -127,7 +133,7 @@ struct Epi {
 template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M,
-                        int N, int K, Epi epi, int *err) {
+                        int N, int K, int tiles_m, int tiles, Epi epi, int *err) {
   constexpr int TC_STAGES = TcCfg<SPLIT>::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -138,21 +144,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(sBlo + (SPLIT ? TC_STAGES * TC_STAGE_B : 0));
   uint64_t *empty = full + TC_STAGES;
   uint64_t *ready = empty + TC_STAGES;  // SPLIT: stage split into hi / lo
-  uint64_t *accum = ready + TC_STAGES;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+  uint64_t *tfull = ready + TC_STAGES;  // accumulator b complete
+  uint64_t *tempty = tfull + 2;         // accumulator b read out
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
   const int nkb = K / TC_BK;
+  const int my_tiles = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&ready[s], TC_EPI_THREADS / 32);
+      mbar_init(&ready[s], TC_SPLIT_WARPS);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], TC_EPI_WARPS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -169,99 +179,124 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // TMA producer
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
-        if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
-          *abort_flag = 1;
-          break;
+      // TMA producer; g counts k-blocks over all tiles of this CTA
+      long long g = 0;
+      for (int lt = 0; lt < my_tiles && !*abort_flag; ++lt) {
+        const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+        const int m0 = (t % tiles_m) * TC_BM, n0 = (t / tiles_m) * TC_BN;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % TC_STAGES);
+          const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
+          if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&full[s], TC_STAGE_A + TC_STAGE_B);
+          tma_load_2d(sA + s * TC_STAGE_A, &ta, &full[s], kb * TC_BK, m0);
+          tma_load_2d(sB + s * TC_STAGE_B, &tb, &full[s], kb * TC_BK, n0);
         }
-        mbar_expect_tx(&full[s], TC_STAGE_A + TC_STAGE_B);
-        tma_load_2d(sA + s * TC_STAGE_A, &ta, &full[s], kb * TC_BK, m0);
-        tma_load_2d(sB + s * TC_STAGE_B, &tb, &full[s], kb * TC_BK, n0);
-        issued = kb + 1;
       }
       if (*abort_flag) {
         // let the copies already issued land before the CTA's shared memory goes away
-        for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
-          mbar_wait(&full[kb % TC_STAGES], (uint32_t)((kb / TC_STAGES) & 1));
+        for (long long q = (g > TC_STAGES ? g - TC_STAGES : 0); q < g; ++q)
+          mbar_wait(&full[q % TC_STAGES], (uint32_t)((q / TC_STAGES) & 1));
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
       const uint32_t idesc = tc_idesc();
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
-        if (*abort_flag || !mbar_wait(SPLIT ? &ready[s] : &full[s], ph)) {
+      long long g = 0;
+      for (int lt = 0; lt < my_tiles && !*abort_flag; ++lt) {
+        const int b = lt & 1;
+        const uint32_t use = (uint32_t)((lt >> 1) & 1);
+        if (!mbar_wait(&tempty[b], use ^ 1u)) {
           *abort_flag = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ad = smem_desc(smem_u32(sA + s * TC_STAGE_A));
-        const uint64_t bd = smem_desc(smem_u32(sB + s * TC_STAGE_B));
-#pragma unroll
-        for (int kk = 0; kk < TC_BK / 8; ++kk) {  // 8 tf32 = 32 bytes per instruction
-          mma_tf32(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb | kk) != 0);
-          if constexpr (SPLIT) {
-            const uint64_t adl = smem_desc(smem_u32(sAlo + s * TC_STAGE_A));
-            const uint64_t bdl = smem_desc(smem_u32(sBlo + s * TC_STAGE_B));
-            mma_tf32(tmem, ad + (uint64_t)(2 * kk), bdl + (uint64_t)(2 * kk), idesc, 1);
-            mma_tf32(tmem, adl + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, 1);
+        const uint32_t dt = tmem + (uint32_t)(b * TC_BN);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % TC_STAGES);
+          const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
+          if (*abort_flag || !mbar_wait(SPLIT ? &ready[s] : &full[s], ph)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ad = smem_desc(smem_u32(sA + s * TC_STAGE_A));
+          const uint64_t bd = smem_desc(smem_u32(sB + s * TC_STAGE_B));
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 8; ++kk) {  // 8 tf32 = 32 bytes per instruction
+            mma_tf32(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb | kk) != 0);
+            if constexpr (SPLIT) {
+              const uint64_t adl = smem_desc(smem_u32(sAlo + s * TC_STAGE_A));
+              const uint64_t bdl = smem_desc(smem_u32(sBlo + s * TC_STAGE_B));
+              mma_tf32(dt, ad + (uint64_t)(2 * kk), bdl + (uint64_t)(2 * kk), idesc, 1);
+              mma_tf32(dt, adl + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, 1);
+            }
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        if (!ok) break;
+        mma_commit(&tfull[b]);
       }
-      mma_commit(accum);
     }
-  } else {
-    // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
-    const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
-    const int row = q * 32 + lane;
-    const int m = m0 + row;
+  } else if (warp < 2 + TC_SPLIT_WARPS) {
     if constexpr (SPLIT) {
       // split every landed stage into hi (in place) and lo
-      const int t = threadIdx.x - 64;  // 0 .. TC_EPI_THREADS - 1
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+      const int t = threadIdx.x - 64;  // 0 .. TC_SPLIT_THREADS - 1
+      long long g = 0;
+      const long long gend = (long long)my_tiles * nkb;
+      for (; g < gend; ++g) {
+        const int s = (int)(g % TC_STAGES);
+        const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
         if (*abort_flag || !mbar_wait(&full[s], ph)) {
           *abort_flag = 1;
           break;
         }
         uint32_t *a = reinterpret_cast<uint32_t *>(sA + s * TC_STAGE_A);
         uint32_t *al = reinterpret_cast<uint32_t *>(sAlo + s * TC_STAGE_A);
-        uint32_t *b = reinterpret_cast<uint32_t *>(sB + s * TC_STAGE_B);
+        uint32_t *bb = reinterpret_cast<uint32_t *>(sB + s * TC_STAGE_B);
         uint32_t *bl = reinterpret_cast<uint32_t *>(sBlo + s * TC_STAGE_B);
 #pragma unroll 4
-        for (int j = t; j < (int)(TC_STAGE_A / 4); j += TC_EPI_THREADS) {
+        for (int j = t; j < (int)(TC_STAGE_A / 4); j += TC_SPLIT_THREADS) {
           const uint32_t x = a[j], h = x & 0xFFFFE000u;
           al[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
           a[j] = h;
         }
 #pragma unroll 4
-        for (int j = t; j < (int)(TC_STAGE_B / 4); j += TC_EPI_THREADS) {
-          const uint32_t x = b[j], h = x & 0xFFFFE000u;
+        for (int j = t; j < (int)(TC_STAGE_B / 4); j += TC_SPLIT_THREADS) {
+          const uint32_t x = bb[j], h = x & 0xFFFFE000u;
           bl[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
-          b[j] = h;
+          bb[j] = h;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ready[s])) : "memory");
       }
     }
-    bool ok = mbar_wait(accum, 0);
-    if (!ok) *abort_flag = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && !*abort_flag) {
+  } else {
+    // epilogue warps: TMEM lane quarter = warp % 4, all 128 columns
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    for (int lt = 0; lt < my_tiles; ++lt) {
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)((lt >> 1) & 1);
+      const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+      const int m0 = (t % tiles_m) * TC_BM, n0 = (t / tiles_m) * TC_BN;
+      const int m = m0 + row;
+      if (*abort_flag || !mbar_wait(&tfull[b], use)) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float v[32];
 #pragma unroll 1
-      for (int c0 = half * (TC_BN / 2); c0 < (half + 1) * (TC_BN / 2); c0 += 32) {
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN + c0);
         uint32_t r[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -298,6 +333,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      // accumulator b is read out: the MMA thread may reuse it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -371,12 +410,16 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
     g_attr_set[1][dev] = true;
   }
   Epi e{mode, D, ldd, Y, nh};
-  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
-  if (grid.y > 65535) return fail(VB_EINVAL, "tc_gemm: M too large");
+  const long long tm = (M + TC_BM - 1) / TC_BM, tn = (N + TC_BN - 1) / TC_BN;
+  if (tm * tn > INT_MAX / 2) return fail(VB_EINVAL, "tc_gemm: too many tiles");
+  static int sm_count[64] = {0};
+  if (!sm_count[dev]) VB_TRY_CUDA(cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev));
+  const int tiles = (int)(tm * tn);
+  const int grid = std::min(tiles, sm_count[dev]);
   if (split)
-    tc_gemm_tf32_kernel<true><<<grid, TC_THREADS, TcCfg<true>::SMEM, st>>>(ta, tb, M, N, K, e, err);
+    tc_gemm_tf32_kernel<true><<<grid, TC_THREADS, TcCfg<true>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, e, err);
   else
-    tc_gemm_tf32_kernel<false><<<grid, TC_THREADS, TcCfg<false>::SMEM, st>>>(ta, tb, M, N, K, e, err);
+    tc_gemm_tf32_kernel<false><<<grid, TC_THREADS, TcCfg<false>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, e, err);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
