@@ -48,7 +48,7 @@ template <bool SPLIT>
 struct TcCfg {
   static constexpr int STAGES = SPLIT ? 3 : 4;
   static constexpr uint32_t STAGE_BYTES = (SPLIT ? 2 : 1) * (TC_STAGE_A + TC_STAGE_B);
-  static constexpr size_t SMEM = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 512;
+  static constexpr size_t SMEM = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 4 * 32 * 33 * 4 /*epilogue*/ + 512;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -121,6 +121,22 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// 32 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // D element (m, n) sink
 struct Epi {
   int mode;        // 0: fp32 row-major D[m*ldd + n]; 1: complex double y[m*nh + j] = (D[m,j], D[m,nh+j])
@@ -141,7 +157,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t *sB = smem + TC_STAGES * TC_STAGE_A;
   uint8_t *sAlo = sB + TC_STAGES * TC_STAGE_B;                     // SPLIT only
   uint8_t *sBlo = sAlo + (SPLIT ? TC_STAGES * TC_STAGE_A : 0);     // SPLIT only
-  uint64_t *full = reinterpret_cast<uint64_t *>(sBlo + (SPLIT ? TC_STAGES * TC_STAGE_B : 0));
+  float *ebuf = reinterpret_cast<float *>(sBlo + (SPLIT ? TC_STAGES * TC_STAGE_B : 0));  // 4 x 32 x 33
+  uint64_t *full = reinterpret_cast<uint64_t *>(ebuf + TC_EPI_WARPS * 32 * 33);
   uint64_t *empty = full + TC_STAGES;
   uint64_t *ready = empty + TC_STAGES;  // SPLIT: stage split into hi / lo
   uint64_t *tfull = ready + TC_STAGES;  // accumulator b complete
@@ -293,36 +310,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN);
+      // each 32 x 32 block goes through shared memory (transposed) so that a
+      // warp store covers one contiguous row segment
+      float *wb = ebuf + (warp - 2 - TC_SPLIT_WARPS) * 32 * 33;
       float v[32];
+      if (epi.mode == 0) {
 #pragma unroll 1
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN + c0);
-        uint32_t r[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          tmem_ld32(tbase + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-        if (m < M) {
-          if (epi.mode == 0) {
-            float *drow = epi.D + (long long)m * epi.ldd + n0 + c0;
-            if (n0 + c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(drow) & 15) == 0)) {
-#pragma unroll
-              for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<float4 *>(drow + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            } else {
-              for (int j = 0; j < 32; ++j)
-                if (n0 + c0 + j < N) drow[j] = v[j];
+          for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
+          __syncwarp();
+          const int col = n0 + c0 + lane;
+          if (col < N) {
+            for (int rr = 0; rr < 32; ++rr) {
+              const int mr = m0 + q * 32 + rr;
+              if (mr < M) epi.D[(long long)mr * epi.ldd + col] = wb[rr * 33 + lane];
             }
-          } else {
-            // complex output: columns [0, nh) real, [nh, 2 nh) imaginary parts
+          }
+          __syncwarp();
+        }
+      } else if (n0 == 0 && epi.nh % 32 == 0 && 2 * epi.nh <= TC_BN) {
+        // complex output, real parts in columns [0, nh), imaginary in [nh, 2 nh):
+        // chunk c0 and chunk c0 + nh give 32 complex values of each row
+#pragma unroll 1
+        for (int c0 = 0; c0 < epi.nh; c0 += 32) {
+          float re[32];
+          tmem_ld32(tbase + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
+          __syncwarp();
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) re[rr] = wb[rr * 33 + lane];
+          __syncwarp();
+          tmem_ld32(tbase + (uint32_t)(c0 + epi.nh), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
+          __syncwarp();
+          const int col = c0 + lane;
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int mr = m0 + q * 32 + rr;
+            if (mr < M)
+              *reinterpret_cast<double2 *>(epi.Y + ((long long)mr * epi.nh + col) * 2) =
+                  make_double2((double)re[rr], (double)wb[rr * 33 + lane]);
+          }
+          __syncwarp();
+        }
+      } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          tmem_ld32(tbase + (uint32_t)c0, v);
+          if (m < M) {
             for (int j = 0; j < 32; ++j) {
               const int col = n0 + c0 + j;
               if (col < epi.nh)
