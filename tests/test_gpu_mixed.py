@@ -1,6 +1,7 @@
-"""Mixed-precision form (H_eff products in complex FP32, everything else in
-FP64) against the FP64 oracle: single products within FP32 accuracy and
-whole 2TDVP runs with populations within 1e-4."""
+"""Mixed-precision form (H_eff products and environments in complex FP32,
+kept directions of the split found in FP32; Lanczos, exponential, split
+tensors and weights in FP64) against the FP64 oracle: single products within
+FP32 accuracy and whole 2TDVP runs with populations within 1e-4."""
 import numpy as np
 import pytest
 
@@ -99,3 +100,15 @@ def test_mixed_sweeps_large_split_rayleigh_ritz(P):
         ref.step(0.5)
         assert st.noconv == 0
         assert np.max(np.abs(mps.populations() - otdvp.populations(ref.mps))) < POP_TOL_MIXED
+
+
+def test_mixed_sweeps_product_state_rank_deficient_splits(P):
+    # d = 20..24 from a product state with no discarded-weight threshold:
+    # splits of dimension up to ~480 (> 192, subspace iteration) while the
+    # Schmidt rank (<= 20) is below the subspace size, so the orthonormalisation
+    # meets dependent rows and refills them
+    m = vm.model_internal_conversion(seed=43, n_modes=4, level_range=(20, 24), n_offdiag=2, n_bilinear=3)
+    dims = vm.local_dims(m)
+    assert max(24 * d for d in dims) > 192
+    errs = _run(P, m, 8, 0.5, 24, eps=0.0)
+    assert max(errs) < POP_TOL_MIXED
