@@ -27,7 +27,10 @@ namespace vb {
 
 vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long ldb, int M, int N, int K,
                        int mode, float *D, long long ldd, double *Y, int nh, int *err, cudaStream_t st,
-                       bool split);
+                       bool split, float *ws = nullptr, long long ws_elems = 0);
+// split-K workspace of the tensor-core legs (floats): enough for every slice
+// count the GEMM picks (fewer than 76 tiles, at most 2 x 152 + 76 items)
+constexpr long long TC_WS_ELEMS = 380LL * 128 * 128;
 
 namespace {
 
@@ -314,7 +317,7 @@ struct TcLayout {
   long long ML, KL, ldL, NL;  // L leg: (2 ML) x ldL times NL x ldL
   long long MR, KR, ld3;      // R leg: MR x ld3 times (2 mR) x ld3
   long long nT1, nT2;
-  size_t oAL, oBX, oT1, oT2, oT3, oBR, oErr, total;
+  size_t oAL, oBX, oT1, oT2, oT3, oBR, oWs, oErr, total;
   TcLayout(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
     const MpoSite &S = mpo->sites[site];
     const MpoSite &S2 = two_site ? mpo->sites[site + 1] : S;
@@ -341,6 +344,7 @@ struct TcLayout {
     oT2 = take((size_t)std::max<long long>(nT2, 1) * 4);
     oT3 = take((size_t)MR * ld3 * 4);
     oBR = take((size_t)2 * mR * ld3 * 4);
+    oWs = take((size_t)TC_WS_ELEMS * 4);
     oErr = take(256);
     total = o;
   }
@@ -412,7 +416,8 @@ vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, in
   }
   // R leg: y (complex double) = T3 BR^T
   VB_TRY(tc_gemm_tf32(T3, lay.ld3, BR, lay.ld3, (int)lay.MR, 2 * mR, (int)lay.ld3, 1, nullptr, 0,
-                      reinterpret_cast<double *>(y), mR, err, st, true));
+                      reinterpret_cast<double *>(y), mR, err, st, true, reinterpret_cast<float *>(w + lay.oWs),
+                      TC_WS_ELEMS));
   return VB_OK;
 }
 

@@ -144,12 +144,13 @@ struct Epi {
   long long ldd;
   double *Y;       // mode 1
   int nh;          // mode 1: number of complex columns (2*nh <= TC_BN)
+  long long ws_stride;  // split-K: elements between the partial products of consecutive K slices
 };
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M,
-                        int N, int K, int tiles_m, int tiles, Epi epi, int *err) {
+                        int N, int K, int tiles_m, int tiles, int kslices, int kb_per, Epi epi, int *err) {
   constexpr int TC_STAGES = TcCfg<SPLIT>::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -168,7 +169,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = K / TC_BK;
-  const int my_tiles = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // work items: (tile, K slice); item t covers tile t % tiles and k-blocks
+  // [kb_per * (t / tiles), min(nkb, kb_per * (t / tiles + 1)))
+  const int items = tiles * kslices;
+  const int my_tiles = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto item_of = [&](int lt, int &m0, int &n0, int &kb0, int &kb1, int &slice) {
+    const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+    const int tile = t % tiles;
+    slice = t / tiles;
+    m0 = (tile % tiles_m) * TC_BM;
+    n0 = (tile / tiles_m) * TC_BN;
+    kb0 = slice * kb_per;
+    kb1 = min(nkb, kb0 + kb_per);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -199,9 +212,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // TMA producer; g counts k-blocks over all tiles of this CTA
       long long g = 0;
       for (int lt = 0; lt < my_tiles && !*abort_flag; ++lt) {
-        const int t = (int)blockIdx.x + lt * (int)gridDim.x;
-        const int m0 = (t % tiles_m) * TC_BM, n0 = (t / tiles_m) * TC_BN;
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
+        int m0, n0, kb0, kb1, slice;
+        item_of(lt, m0, n0, kb0, kb1, slice);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = (int)(g % TC_STAGES);
           const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
           if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
@@ -233,8 +246,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dt = tmem + (uint32_t)(b * TC_BN);
+        int m0, n0, kb0, kb1, slice;
+        item_of(lt, m0, n0, kb0, kb1, slice);
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = (int)(g % TC_STAGES);
           const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
           if (*abort_flag || !mbar_wait(SPLIT ? &ready[s] : &full[s], ph)) {
@@ -247,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint64_t bd = smem_desc(smem_u32(sB + s * TC_STAGE_B));
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 8; ++kk) {  // 8 tf32 = 32 bytes per instruction
-            mma_tf32(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb | kk) != 0);
+            mma_tf32(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
             if constexpr (SPLIT) {
               const uint64_t adl = smem_desc(smem_u32(sAlo + s * TC_STAGE_A));
               const uint64_t bdl = smem_desc(smem_u32(sBlo + s * TC_STAGE_B));
@@ -265,9 +280,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if constexpr (SPLIT) {
       // split every landed stage into hi (in place) and lo
       const int t = threadIdx.x - 64;  // 0 .. TC_SPLIT_THREADS - 1
-      long long g = 0;
-      const long long gend = (long long)my_tiles * nkb;
-      for (; g < gend; ++g) {
+      long long gend = 0;
+      for (int lt = 0; lt < my_tiles; ++lt) {
+        int m0, n0, kb0, kb1, slice;
+        item_of(lt, m0, n0, kb0, kb1, slice);
+        gend += kb1 - kb0;
+      }
+      for (long long g = 0; g < gend; ++g) {
         const int s = (int)(g % TC_STAGES);
         const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
         if (*abort_flag || !mbar_wait(&full[s], ph)) {
@@ -302,9 +321,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int lt = 0; lt < my_tiles; ++lt) {
       const int b = lt & 1;
       const uint32_t use = (uint32_t)((lt >> 1) & 1);
-      const int t = (int)blockIdx.x + lt * (int)gridDim.x;
-      const int m0 = (t % tiles_m) * TC_BM, n0 = (t / tiles_m) * TC_BN;
+      int m0, n0, kb0, kb1, slice;
+      item_of(lt, m0, n0, kb0, kb1, slice);
       const int m = m0 + row;
+      float *Dout = epi.D + (long long)slice * epi.ws_stride;
       if (*abort_flag || !mbar_wait(&tfull[b], use)) {
         *abort_flag = 1;
         break;
@@ -326,7 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (col < N) {
             for (int rr = 0; rr < 32; ++rr) {
               const int mr = m0 + q * 32 + rr;
-              if (mr < M) epi.D[(long long)mr * epi.ldd + col] = wb[rr * 33 + lane];
+              if (mr < M) Dout[(long long)mr * epi.ldd + col] = wb[rr * 33 + lane];
             }
           }
           __syncwarp();
@@ -388,6 +408,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
 }
 
+// sum of the K-slice partial products, in slice order: mode 0 writes D
+// (fp32, pitch ldd), mode 1 the complex double y[m][j] = (P[m][j], P[m][nh + j])
+__global__ void tc_splitk_reduce(const float *__restrict__ ws, int ks, int M, int N, int mode, float *D,
+                                 long long ldd, double *Y, int nh) {
+  const long long MN = (long long)M * N;
+  const long long tot = mode == 0 ? MN : (long long)M * nh;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    if (mode == 0) {
+      float s = 0.f;
+      for (int q = 0; q < ks; ++q) s += ws[q * MN + e];
+      D[(e / N) * ldd + e % N] = s;
+    } else {
+      const long long m = e / nh, j = e % nh;
+      float re = 0.f, im = 0.f;
+      for (int q = 0; q < ks; ++q) {
+        re += ws[q * MN + m * N + j];
+        im += ws[q * MN + m * N + nh + j];
+      }
+      reinterpret_cast<double2 *>(Y)[e] = make_double2((double)re, (double)im);
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 
@@ -427,9 +470,12 @@ bool g_attr_set[2][64] = {{false}};
 // D (M x N) = A (M x K) B (N x K)^T in TF32 with FP32 accumulation.
 // mode 0: D fp32 row-major with pitch ldd; mode 1: complex double output
 // Y[m][j] = (D[m, j], D[m, nh + j]) for j < nh (needs N = 2 nh).
+// ws (optional, ws_elems floats): when there are few tiles and a long K
+// loop, K is cut into slices whose partial products go to ws and are summed
+// in slice order by a second kernel.
 vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long ldb, int M, int N, int K,
                        int mode, float *D, long long ldd, double *Y, int nh, int *err, cudaStream_t st,
-                       bool split) {
+                       bool split, float *ws, long long ws_elems) {
   if (M <= 0 || N <= 0 || K <= 0) return VB_OK;
   if (mode == 1 && N != 2 * nh) return fail(VB_EINVAL, "tc_gemm: complex output needs N = 2 nh");
   VB_TRY(get_encode());
@@ -449,17 +495,38 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
                                      (int)TcCfg<true>::SMEM));
     g_attr_set[1][dev] = true;
   }
-  Epi e{mode, D, ldd, Y, nh};
   const long long tm = (M + TC_BM - 1) / TC_BM, tn = (N + TC_BN - 1) / TC_BN;
-  if (tm * tn > INT_MAX / 2) return fail(VB_EINVAL, "tc_gemm: too many tiles");
+  if (tm * tn > INT_MAX / 64) return fail(VB_EINVAL, "tc_gemm: too many tiles");
   static int sm_count[64] = {0};
   if (!sm_count[dev]) VB_TRY_CUDA(cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev));
+  const int sms = sm_count[dev];
   const int tiles = (int)(tm * tn);
-  const int grid = std::min(tiles, sm_count[dev]);
+  const int nkb = K / TC_BK;
+  // split-K when the tiles alone leave most SMs idle over a long K loop
+  int ks = 1, kb_per = nkb;
+  if (ws && tiles < sms / 2 && nkb >= 16) {
+    ks = std::min(nkb / 8, (2 * sms + tiles - 1) / tiles);
+    while (ks > 1 && (long long)ks * M * N > ws_elems) --ks;
+    if (ks > 1) {
+      kb_per = (nkb + ks - 1) / ks;
+      ks = (nkb + kb_per - 1) / kb_per;
+    }
+  }
+  Epi e = ks > 1 ? Epi{0, ws, N, nullptr, 0, (long long)M * N} : Epi{mode, D, ldd, Y, nh, 0};
+  const int items = tiles * ks;
+  const int grid = std::min(items, sms);
   if (split)
-    tc_gemm_tf32_kernel<true><<<grid, TC_THREADS, TcCfg<true>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, e, err);
+    tc_gemm_tf32_kernel<true><<<grid, TC_THREADS, TcCfg<true>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, ks, kb_per,
+                                                                           e, err);
   else
-    tc_gemm_tf32_kernel<false><<<grid, TC_THREADS, TcCfg<false>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, e, err);
+    tc_gemm_tf32_kernel<false><<<grid, TC_THREADS, TcCfg<false>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, ks,
+                                                                             kb_per, e, err);
+  VB_CHECK_LAUNCH();
+  if (ks > 1) {
+    const long long tot = mode == 0 ? (long long)M * N : (long long)M * nh;
+    tc_splitk_reduce<<<(int)std::min<long long>((tot + 255) / 256, 4096), 256, 0, st>>>(ws, ks, M, N, mode, D, ldd, Y,
+                                                                                        nh);
+  }
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
