@@ -224,6 +224,10 @@ vb_status subspace_init(cf *Q, int r, int n, const cd *warm, int m_old, int m_wa
 // orthonormalise the rows of Q (r <= 128) in place: row-scaled Cholesky QR,
 // twice; rows found dependent are refilled at random before the second pass
 vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned long long seed, cudaStream_t st);
+// k largest eigenpairs of a small Hermitian S (2 <= n <= 112) by a one-CTA
+// Jacobi solver: evals descending, eigenvectors as rows W[k][n]; info[0] =
+// sweeps used. VB_EINVAL for larger n (use eig_values / eig_vectors)
+vb_status ritz_eig_small(const cf *S, int n, int k, float *evals, cf *W, int *info, cudaStream_t st);
 // *out = sum |x_i|^2 accumulated in FP64
 vb_status norm2_sq_f32(const cf *x, long long n, double *out, double *partial, int n_part, cudaStream_t st);
 // out[0] = *capt, out[1] = *cnt

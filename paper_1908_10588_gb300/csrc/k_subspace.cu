@@ -131,6 +131,153 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_rows_kernel(const cf *__res
   for (int i = tid; i < r; i += nt) flag[i] = piv[i] > 0.f ? 0 : 1;
 }
 
+// One-CTA Jacobi eigensolver for the small Hermitian Rayleigh-Ritz matrix
+// S (n x n, n <= JAC_MAX_N), all in shared memory: parallel (round-robin)
+// ordering, n/2 disjoint rotations per round; every 2 x 2 block of A and
+// every row pair of V is updated independently, so a round costs two
+// barriers. A rotation U = diag(1, e^{-i phi}) R(theta) zeroes |A_pq| (phase
+// phi of A_pq; theta from the real Jacobi rule tan 2 theta = 2|A_pq|/(A_pp - A_qq),
+// smaller root). Sweeps stop when no off-diagonal element exceeds
+// 1e-7 sqrt(A_pp A_qq) + 1e-12 tr A. Writes the k largest eigenvalues
+// (descending) and their eigenvectors as rows W[t][0..n).
+constexpr int JAC_THREADS = 1024;
+constexpr int JAC_MAX_N = 112;
+constexpr int JAC_SWEEPS = 20;
+__global__ void __launch_bounds__(JAC_THREADS) ritz_jacobi_kernel(const cf *__restrict__ S, int n, int k,
+                                                                  float *__restrict__ evals, cf *__restrict__ W,
+                                                                  int *__restrict__ info) {
+  extern __shared__ __align__(16) unsigned char jsm[];
+  const int np = n + (n & 1), h = np / 2;
+  cf *A = reinterpret_cast<cf *>(jsm);
+  cf *V = A + np * np;
+  cf *ph = V + np * np;  // e^{-i phi} per pair
+  float *cs = reinterpret_cast<float *>(ph + h);
+  float *sn = cs + h;
+  int *pp = reinterpret_cast<int *>(sn + h);
+  int *qq = pp + h;
+  __shared__ int s_any;
+  __shared__ float s_scale;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < np * np; e += nt) {
+    const int i = e / np, j = e % np;
+    cf a = mkc(0.f, 0.f);
+    if (i < n && j < n) {
+      const cf u = S[(long long)i * n + j], v = S[(long long)j * n + i];
+      a = mkc(0.5f * (u.x + v.x), 0.5f * (u.y - v.y));  // Hermitian part
+    }
+    A[e] = a;
+    V[e] = mkc(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += fabsf(A[i * np + i].x);
+    s_scale = s;
+  }
+  __syncthreads();
+  const float floor_abs = 1e-12f * s_scale;
+  int sweep = 0;
+  for (; sweep < JAC_SWEEPS; ++sweep) {
+    if (tid == 0) s_any = 0;
+    __syncthreads();
+    for (int rd = 0; rd < np - 1; ++rd) {
+      for (int t = tid; t < h; t += nt) {
+        // circle method: slot 0 fixed, slots 1..np-1 rotate by rd
+        const int s0 = t, s1 = np - 1 - t;
+        int p = s0 == 0 ? 0 : 1 + (s0 - 1 + rd) % (np - 1);
+        int q = 1 + (s1 - 1 + rd) % (np - 1);
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        pp[t] = p;
+        qq[t] = q;
+        float c_ = 1.f, s_ = 0.f;
+        cf e = mkc(1.f, 0.f);
+        if (q < n) {
+          const float a = A[p * np + p].x, b = A[q * np + q].x;
+          const cf c = A[p * np + q];
+          const float ac = sqrtf(c.x * c.x + c.y * c.y);
+          if (ac > 1e-7f * sqrtf(fabsf(a * b)) + floor_abs) {
+            const float tau = (b - a) / (2.f * ac);
+            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c_ = 1.f / sqrtf(1.f + tt * tt);
+            s_ = tt * c_;
+            e = mkc(c.x / ac, -c.y / ac);
+            s_any = 1;
+          }
+        }
+        cs[t] = c_;
+        sn[t] = s_;
+        ph[t] = e;
+      }
+      __syncthreads();
+      // A <- U^H A U, block by block; V <- V U
+      for (int e2 = tid; e2 < h * h; e2 += nt) {
+        const int bi = e2 / h, bj = e2 % h;
+        const int pi = pp[bi], qi = qq[bi], pj = pp[bj], qj = qq[bj];
+        const float ci = cs[bi], si = sn[bi], cj = cs[bj], sj = sn[bj];
+        const cf ei = ph[bi], ej = ph[bj];
+        const cf b00 = A[pi * np + pj], b01 = A[pi * np + qj], b10 = A[qi * np + pj], b11 = A[qi * np + qj];
+        // left: rows (pi, qi) by U_i^H = [[c, -s conj(e)], [s, c conj(e)]]
+        const cf ce = mkc(ei.x, -ei.y);
+        const cf t10 = mkc(ce.x * b10.x - ce.y * b10.y, ce.x * b10.y + ce.y * b10.x);
+        const cf t11 = mkc(ce.x * b11.x - ce.y * b11.y, ce.x * b11.y + ce.y * b11.x);
+        const cf l00 = mkc(ci * b00.x - si * t10.x, ci * b00.y - si * t10.y);
+        const cf l01 = mkc(ci * b01.x - si * t11.x, ci * b01.y - si * t11.y);
+        const cf l10 = mkc(si * b00.x + ci * t10.x, si * b00.y + ci * t10.y);
+        const cf l11 = mkc(si * b01.x + ci * t11.x, si * b01.y + ci * t11.y);
+        // right: columns (pj, qj) by U_j = [[c, s], [-s e, c e]]
+        const cf u01 = mkc(ej.x * l01.x - ej.y * l01.y, ej.x * l01.y + ej.y * l01.x);
+        const cf u11 = mkc(ej.x * l11.x - ej.y * l11.y, ej.x * l11.y + ej.y * l11.x);
+        cf r00 = mkc(cj * l00.x - sj * u01.x, cj * l00.y - sj * u01.y);
+        cf r01 = mkc(sj * l00.x + cj * u01.x, sj * l00.y + cj * u01.y);
+        cf r10 = mkc(cj * l10.x - sj * u11.x, cj * l10.y - sj * u11.y);
+        cf r11 = mkc(sj * l10.x + cj * u11.x, sj * l10.y + cj * u11.y);
+        if (bi == bj) {
+          // diagonal block: real diagonal, the rotated coupling is zero
+          r00.y = 0.f;
+          r11.y = 0.f;
+          if (si != 0.f) r01 = r10 = mkc(0.f, 0.f);
+        }
+        A[pi * np + pj] = r00;
+        A[pi * np + qj] = r01;
+        A[qi * np + pj] = r10;
+        A[qi * np + qj] = r11;
+      }
+      for (int e2 = tid; e2 < np * h; e2 += nt) {
+        const int x = e2 / h, bj = e2 % h;
+        const int pj = pp[bj], qj = qq[bj];
+        const float cj = cs[bj], sj = sn[bj];
+        const cf ej = ph[bj];
+        const cf v0 = V[x * np + pj], v1 = V[x * np + qj];
+        const cf w1 = mkc(ej.x * v1.x - ej.y * v1.y, ej.x * v1.y + ej.y * v1.x);
+        V[x * np + pj] = mkc(cj * v0.x - sj * w1.x, cj * v0.y - sj * w1.y);
+        V[x * np + qj] = mkc(sj * v0.x + cj * w1.x, sj * v0.y + cj * w1.y);
+      }
+      __syncthreads();
+    }
+    const int any = s_any;
+    __syncthreads();
+    if (!any) break;
+  }
+  // k largest eigenvalues, descending (ties by index), and their vectors
+  for (int i = tid; i < n; i += nt) {
+    const float di = A[i * np + i].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float dj = A[j * np + j].x;
+      rank += (dj > di || (dj == di && j < i)) ? 1 : 0;
+    }
+    if (rank < k) {
+      evals[rank] = di;
+      for (int x = 0; x < n; ++x) W[(long long)rank * n + x] = V[x * np + i];
+    }
+  }
+  if (tid == 0) info[0] = sweep;
+}
+
 __global__ void __launch_bounds__(256) norm2_f32_part(const cf *__restrict__ x, long long n,
                                                       double *__restrict__ partial) {
   __shared__ double sh[8];
@@ -227,6 +374,27 @@ vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned lon
 
 vb_status subspace_status(const double *capt, const int *cnt, double *out, cudaStream_t st) {
   status_kernel<<<1, 1, 0, st>>>(capt, cnt, out);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+size_t ritz_jacobi_smem(int n) {
+  const size_t np = n + (n & 1), h = np / 2;
+  return 2 * np * np * sizeof(cf) + h * (sizeof(cf) + 2 * sizeof(float) + 2 * sizeof(int));
+}
+
+vb_status ritz_eig_small(const cf *S, int n, int k, float *evals, cf *W, int *info, cudaStream_t st) {
+  if (n < 2 || n > JAC_MAX_N || k < 1 || k > n) return fail(VB_EINVAL, "ritz_eig_small: needs 2 <= n <= 112");
+  static int smem_set[64] = {0};
+  int dev = 0;
+  VB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "ritz_eig_small: device ordinal out of range");
+  if (!smem_set[dev]) {
+    VB_TRY_CUDA(cudaFuncSetAttribute(ritz_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ritz_jacobi_smem(JAC_MAX_N)));
+    smem_set[dev] = 1;
+  }
+  ritz_jacobi_kernel<<<1, JAC_THREADS, ritz_jacobi_smem(n), st>>>(S, n, k, evals, W, info);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
