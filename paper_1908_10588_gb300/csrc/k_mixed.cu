@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(128) wapply_planar_kernel(const int *__restric
 // nonzero blocks and operator entries; each thread moves four q per load.
 // Blocks are ordered with the chunk slowest, so the (s', w') blocks of one
 // chunk run together and share its input rows in L2.
-constexpr int WV4_J = 4;
+constexpr int WV4_J = 2;
 // 32-bit element offsets (both buffers are below 2^31 elements; checked on
 // the host), so the per-thread row offsets take one register each
 struct V4Strides {
   int xp, xw, xs, xplane, yp, yw, ys, yplane;
 };
-__global__ void __launch_bounds__(128, 8) wapply_planar_v4_kernel(
+__global__ void __launch_bounds__(128, 12) wapply_planar_v4_kernel(
     const int *__restrict__ rp, const int *__restrict__ col, const float *__restrict__ val,
     const int *__restrict__ ptr, const int *__restrict__ ent, int d, int Wp, int P, int Q4,
     const float *__restrict__ X, float *__restrict__ Y, V4Strides s) {
