@@ -217,11 +217,15 @@ unsigned long long vb_kernel_launches(void);
  * inverse iteration, Gram-Schmidt and back-transformation parts of every
  * eigenvector stage). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
- * multiply-add is 8, real-times-complex 4, an identity-block add 2). */
+ * multiply-add is 8, real-times-complex 4, an identity-block add 2);
+ * krylov_flops counts the FP64 operations of the Krylov vector work (phase
+ * 2: inner products, updates, norms, scaling, the final combination) the same
+ * way. */
 typedef struct {
   double ms[24];
   long long calls[24];
   double heff_flops[2];
+  double krylov_flops;
 } vb_profile;
 vb_status vb_profile_enable(int on);
 vb_status vb_profile_read(vb_profile *out, int reset);

@@ -58,7 +58,8 @@ class vb_tdvp_opts(C.Structure):
 
 
 class vb_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 24), ("calls", C.c_longlong * 24), ("heff_flops", C.c_double * 2)]
+    _fields_ = [("ms", C.c_double * 24), ("calls", C.c_longlong * 24), ("heff_flops", C.c_double * 2),
+                ("krylov_flops", C.c_double)]
 
 
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
@@ -346,6 +347,7 @@ def vb_profile_read(reset: bool = True) -> dict:
     out = {name: {"ms": p.ms[k], "calls": int(p.calls[k])} for k, name in enumerate(PHASES)}
     out["heff2"]["flops"] = p.heff_flops[0]
     out["heff1"]["flops"] = p.heff_flops[1]
+    out["krylov"]["flops"] = p.krylov_flops
     return out
 
 

@@ -21,6 +21,7 @@ struct Prof {
   double ms[PH_COUNT] = {0};
   long long calls[PH_COUNT] = {0};
   double flops[2] = {0, 0};
+  double krylov_flops = 0;
 } g_prof;
 
 cudaEvent_t take_event() {
@@ -69,6 +70,7 @@ void prof_collect() {
     g_prof.ms[p.phase] += ms;
     g_prof.calls[p.phase] += 1;
     if (p.phase < 2) g_prof.flops[p.phase] += p.flops;
+    if (p.phase == PH_KRYLOV) g_prof.krylov_flops += p.flops;
     g_prof.pool.push_back(p.a);
     g_prof.pool.push_back(p.b);
   }
@@ -96,12 +98,14 @@ vb_status vb_profile_read(vb_profile *out, int reset) {
   }
   out->heff_flops[0] = vb::g_prof.flops[0];
   out->heff_flops[1] = vb::g_prof.flops[1];
+  out->krylov_flops = vb::g_prof.krylov_flops;
   if (reset) {
     for (int i = 0; i < vb::PH_COUNT; ++i) {
       vb::g_prof.ms[i] = 0;
       vb::g_prof.calls[i] = 0;
     }
     vb::g_prof.flops[0] = vb::g_prof.flops[1] = 0;
+    vb::g_prof.krylov_flops = 0;
   }
   return VB_OK;
 }

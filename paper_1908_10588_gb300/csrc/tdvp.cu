@@ -399,7 +399,9 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
   VB_TRY(vec_norm2(x, N, s->d_nrm, s->d_part, np, st));
   VB_TRY(vec_copy_scaled(x, V, N, st));
   VB_TRY(vec_scale_inv(V, N, s->d_nrm, st));
-  prof_end(PH_KRYLOV, st, 0.0);
+  // algorithmic FP64 flops: a complex multiply-add counts 8, |z|^2 counts 4
+  const double Nd = (double)N;
+  prof_end(PH_KRYLOV, st, 4.0 * Nd + 2.0 * Nd);
   int kdim = 0;
   *converged = 0;
   for (int k = 0; k < kmax; ++k) {
@@ -423,7 +425,10 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     VB_CHECK_LAUNCH();
     VB_TRY(tridiag_expm(s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     VB_TRY_CUDA(cudaMemcpyAsync(s->d_flag + 1, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    prof_end(PH_KRYLOV, st, 0.0);
+    {
+      const double nv1 = s->dtype == VB_MIXED ? (double)(k > 0 ? 2 : 1) : (double)(k + 1);
+      prof_end(PH_KRYLOV, st, Nd * (16.0 * (nv1 + k + 1) + 4.0));
+    }
     VB_TRY_CUDA(cudaStreamSynchronize(st));
     const double err = s->h_flag[0], b = s->h_flag[1];
     kdim = k + 1;
@@ -435,12 +440,12 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     prof_begin(PH_KRYLOV, st);
     VB_TRY_CUDA(cudaMemcpyAsync(s->d_beta + k, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
     VB_TRY(vec_scale_inv(w, N, s->d_bnext, st));
-    prof_end(PH_KRYLOV, st, 0.0);
+    prof_end(PH_KRYLOV, st, 2.0 * Nd);
   }
   *iters = kdim;
   prof_begin(PH_KRYLOV, st);
   VB_TRY(vec_combine(V, ldv, kdim, s->d_u, s->d_nrm, x, N, st));
-  prof_end(PH_KRYLOV, st, 0.0);
+  prof_end(PH_KRYLOV, st, 8.0 * Nd * kdim);
   return VB_OK;
 }
 
