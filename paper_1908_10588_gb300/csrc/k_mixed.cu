@@ -27,7 +27,8 @@ namespace vb {
 
 vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long ldb, int M, int N, int K,
                        int mode, float *D, long long ldd, double *Y, int nh, int *err, cudaStream_t st,
-                       bool split, float *ws = nullptr, long long ws_elems = 0);
+                       bool split, float *ws = nullptr, long long ws_elems = 0, const float *Alo = nullptr,
+                       const float *Blo = nullptr);
 // split-K workspace of the tensor-core legs (floats): enough for every slice
 // count the GEMM picks (fewer than 76 tiles, at most 2 x 152 + 76 items)
 constexpr long long TC_WS_ELEMS = 380LL * 128 * 128;
@@ -43,7 +44,17 @@ int grid_for(long long n) {
 }
 
 // AL[i][k]: rows i < M: [Re L[i,:], -Im L[i,:], 0...]; rows M + i: [Im L, Re L, 0...]
-__global__ void prep_left_env(const cd *__restrict__ L, long long M, int K, long long ld, float *__restrict__ AL) {
+// x = hi + lo with hi = x truncated to tf32 (low 13 mantissa bits cleared,
+// exact in tf32) and lo = x - hi (exact in fp32): the operand split of the
+// three-product TF32 GEMM, done where the operand is produced
+__device__ __forceinline__ void tf32_split_store(float v, float *hi, float *lo, long long e) {
+  const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+  hi[e] = h;
+  lo[e] = v - h;
+}
+
+__global__ void prep_left_env(const cd *__restrict__ L, long long M, int K, long long ld, float *__restrict__ AL,
+                              float *__restrict__ ALlo) {
   const long long total = 2 * M * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -60,12 +71,13 @@ __global__ void prep_left_env(const cd *__restrict__ L, long long M, int K, long
       else
         v = col < K ? (float)z.y : (float)z.x;
     }
-    AL[e] = v;
+    tf32_split_store(v, AL, ALlo, e);
   }
 }
 
 // BR[n][k]: rows n < N: [Re R[n,:], -Im R[n,:], 0...]; rows N + n: [Im R, Re R, 0...]
-__global__ void prep_right_env(const cd *__restrict__ R, int N, long long K, long long ld, float *__restrict__ BR) {
+__global__ void prep_right_env(const cd *__restrict__ R, int N, long long K, long long ld, float *__restrict__ BR,
+                               float *__restrict__ BRlo) {
   const long long total = 2LL * N * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -82,13 +94,14 @@ __global__ void prep_right_env(const cd *__restrict__ R, int N, long long K, lon
       else
         v = col < K ? (float)z.y : (float)z.x;
     }
-    BR[e] = v;
+    tf32_split_store(v, BR, BRlo, e);
   }
 }
 
 // BX[n][k] = [Re x[k][n] (k < K), Im x[k-K][n] (K <= k < 2K), 0...]: a tiled
 // transpose of x (K x Ncols complex double) into K-major fp32 rows
-__global__ void prep_vector_T(const cd *__restrict__ x, int K, long long Ncols, long long ld, float *__restrict__ BX) {
+__global__ void prep_vector_T(const cd *__restrict__ x, int K, long long Ncols, long long ld, float *__restrict__ BX,
+                              float *__restrict__ BXlo) {
   __shared__ float tr[32][33], ti[32][33];
   const long long n0 = (long long)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
@@ -106,8 +119,8 @@ __global__ void prep_vector_T(const cd *__restrict__ x, int K, long long Ncols, 
     const long long n = n0 + r;
     const int k = k0 + tx;
     if (n < Ncols && k < K) {
-      BX[n * ld + k] = tr[tx][r];
-      BX[n * ld + K + k] = ti[tx][r];
+      tf32_split_store(tr[tx][r], BX, BXlo, n * ld + k);
+      tf32_split_store(ti[tx][r], BX, BXlo, n * ld + K + k);
     }
   }
 }
@@ -317,7 +330,7 @@ struct TcLayout {
   long long ML, KL, ldL, NL;  // L leg: (2 ML) x ldL times NL x ldL
   long long MR, KR, ld3;      // R leg: MR x ld3 times (2 mR) x ld3
   long long nT1, nT2;
-  size_t oAL, oBX, oT1, oT2, oT3, oBR, oWs, oErr, total;
+  size_t oAL, oBX, oT1, oT2, oT3, oBR, oWs, oALlo, oBXlo, oBRlo, oErr, total;
   TcLayout(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
     const MpoSite &S = mpo->sites[site];
     const MpoSite &S2 = two_site ? mpo->sites[site + 1] : S;
@@ -345,6 +358,9 @@ struct TcLayout {
     oT3 = take((size_t)MR * ld3 * 4);
     oBR = take((size_t)2 * mR * ld3 * 4);
     oWs = take((size_t)TC_WS_ELEMS * 4);
+    oALlo = take((size_t)2 * ML * ldL * 4);
+    oBXlo = take((size_t)NL * ldL * 4);
+    oBRlo = take((size_t)2 * mR * ld3 * 4);
     oErr = take(256);
     total = o;
   }
@@ -375,24 +391,30 @@ vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, in
   float *T2 = reinterpret_cast<float *>(w + lay.oT2);
   float *T3 = reinterpret_cast<float *>(w + lay.oT3);
   float *BR = reinterpret_cast<float *>(w + lay.oBR);
+  float *ALlo = reinterpret_cast<float *>(w + lay.oALlo);
+  float *BXlo = reinterpret_cast<float *>(w + lay.oBXlo);
+  float *BRlo = reinterpret_cast<float *>(w + lay.oBRlo);
   const MpoSite &S = mpo->sites[site];
   // operands of the L leg
-  prep_left_env<<<grid_for(2 * lay.ML * lay.ldL), 256, 0, st>>>(L, lay.ML, (int)lay.KL, lay.ldL, AL);
+  prep_left_env<<<grid_for(2 * lay.ML * lay.ldL), 256, 0, st>>>(L, lay.ML, (int)lay.KL, lay.ldL, AL, ALlo);
   VB_CHECK_LAUNCH();
   {
     dim3 g((unsigned)((lay.NL + 31) / 32), (unsigned)((lay.KL + 31) / 32));
-    prep_vector_T<<<g, 256, 0, st>>>(x, (int)lay.KL, lay.NL, lay.ldL, BX);
+    prep_vector_T<<<g, 256, 0, st>>>(x, (int)lay.KL, lay.NL, lay.ldL, BX, BXlo);
     VB_CHECK_LAUNCH();
     if (lay.ldL > 2 * lay.KL) {
       zero_cols<<<grid_for(lay.NL * (lay.ldL - 2 * lay.KL)), 256, 0, st>>>(BX, lay.NL, lay.ldL, 2 * lay.KL);
       VB_CHECK_LAUNCH();
+      zero_cols<<<grid_for(lay.NL * (lay.ldL - 2 * lay.KL)), 256, 0, st>>>(BXlo, lay.NL, lay.ldL, 2 * lay.KL);
+      VB_CHECK_LAUNCH();
     }
   }
-  prep_right_env<<<grid_for(2LL * mR * lay.ld3), 256, 0, st>>>(R, mR, lay.KR, lay.ld3, BR);
+  prep_right_env<<<grid_for(2LL * mR * lay.ld3), 256, 0, st>>>(R, mR, lay.KR, lay.ld3, BR, BRlo);
   VB_CHECK_LAUNCH();
   // L leg: T1 planar (2 ML) x NL
+  // both operands were split by the prep kernels
   VB_TRY(tc_gemm_tf32(AL, lay.ldL, BX, lay.ldL, (int)(2 * lay.ML), (int)lay.NL, (int)lay.ldL, 0, T1, lay.NL,
-                      nullptr, 0, err, st, true));
+                      nullptr, 0, err, st, true, nullptr, 0, ALlo, BXlo));
   const long long P1 = lay.ML * lay.NL;  // plane offset of T1
   if (two_site) {
     const MpoSite &S2 = mpo->sites[site + 1];
@@ -417,7 +439,7 @@ vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, in
   // R leg: y (complex double) = T3 BR^T
   VB_TRY(tc_gemm_tf32(T3, lay.ld3, BR, lay.ld3, (int)lay.MR, 2 * mR, (int)lay.ld3, 1, nullptr, 0,
                       reinterpret_cast<double *>(y), mR, err, st, true, reinterpret_cast<float *>(w + lay.oWs),
-                      TC_WS_ELEMS));
+                      TC_WS_ELEMS, nullptr, BRlo));
   return VB_OK;
 }
 

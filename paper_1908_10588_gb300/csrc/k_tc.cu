@@ -147,10 +147,19 @@ struct Epi {
   long long ws_stride;  // split-K: elements between the partial products of consecutive K slices
 };
 
-template <bool SPLIT>
+// SA, SB: how each operand enters the product. 0: one tf32 product (no
+// split); 1: split into hi / lo in shared memory as it lands; 2: split
+// beforehand, hi and lo arrive by TMA from separate arrays (talo / tblo).
+// Either both operands are split (3 products) or neither.
+template <int SA, int SB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M,
+    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                        const __grid_constant__ CUtensorMap talo, const __grid_constant__ CUtensorMap tblo, int M,
                         int N, int K, int tiles_m, int tiles, int kslices, int kb_per, Epi epi, int *err) {
+  constexpr bool SPLIT = SA != 0;
+  constexpr bool SMEM_SPLIT = SA == 1 || SB == 1;
+  static_assert((SA == 0) == (SB == 0), "both operands split or neither");
+  constexpr uint32_t TX_BYTES = TC_STAGE_A + TC_STAGE_B + (SA == 2 ? TC_STAGE_A : 0) + (SB == 2 ? TC_STAGE_B : 0);
   constexpr int TC_STAGES = TcCfg<SPLIT>::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -221,9 +230,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             *abort_flag = 1;
             break;
           }
-          mbar_expect_tx(&full[s], TC_STAGE_A + TC_STAGE_B);
+          mbar_expect_tx(&full[s], TX_BYTES);
           tma_load_2d(sA + s * TC_STAGE_A, &ta, &full[s], kb * TC_BK, m0);
           tma_load_2d(sB + s * TC_STAGE_B, &tb, &full[s], kb * TC_BK, n0);
+          if constexpr (SA == 2) tma_load_2d(sAlo + s * TC_STAGE_A, &talo, &full[s], kb * TC_BK, m0);
+          if constexpr (SB == 2) tma_load_2d(sBlo + s * TC_STAGE_B, &tblo, &full[s], kb * TC_BK, n0);
         }
       }
       if (*abort_flag) {
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = (int)(g % TC_STAGES);
           const uint32_t ph = (uint32_t)((g / TC_STAGES) & 1);
-          if (*abort_flag || !mbar_wait(SPLIT ? &ready[s] : &full[s], ph)) {
+          if (*abort_flag || !mbar_wait(SMEM_SPLIT ? &ready[s] : &full[s], ph)) {
             *abort_flag = 1;
             ok = false;
             break;
@@ -277,7 +288,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else if (warp < 2 + TC_SPLIT_WARPS) {
-    if constexpr (SPLIT) {
+    if constexpr (SMEM_SPLIT) {
       // split every landed stage into hi (in place) and lo
       const int t = threadIdx.x - 64;  // 0 .. TC_SPLIT_THREADS - 1
       long long gend = 0;
@@ -297,17 +308,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t *al = reinterpret_cast<uint32_t *>(sAlo + s * TC_STAGE_A);
         uint32_t *bb = reinterpret_cast<uint32_t *>(sB + s * TC_STAGE_B);
         uint32_t *bl = reinterpret_cast<uint32_t *>(sBlo + s * TC_STAGE_B);
+        if constexpr (SA == 1) {
 #pragma unroll 4
-        for (int j = t; j < (int)(TC_STAGE_A / 4); j += TC_SPLIT_THREADS) {
-          const uint32_t x = a[j], h = x & 0xFFFFE000u;
-          al[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
-          a[j] = h;
+          for (int j = t; j < (int)(TC_STAGE_A / 4); j += TC_SPLIT_THREADS) {
+            const uint32_t x = a[j], h = x & 0xFFFFE000u;
+            al[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+            a[j] = h;
+          }
         }
+        if constexpr (SB == 1) {
 #pragma unroll 4
-        for (int j = t; j < (int)(TC_STAGE_B / 4); j += TC_SPLIT_THREADS) {
-          const uint32_t x = bb[j], h = x & 0xFFFFE000u;
-          bl[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
-          bb[j] = h;
+          for (int j = t; j < (int)(TC_STAGE_B / 4); j += TC_SPLIT_THREADS) {
+            const uint32_t x = bb[j], h = x & 0xFFFFE000u;
+            bl[j] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+            bb[j] = h;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -463,7 +478,17 @@ vb_status make_map(CUtensorMap *map, const float *base, long long rows, long lon
   return VB_OK;
 }
 
-bool g_attr_set[2][64] = {{false}};
+
+template <int SA, int SB>
+vb_status tc_prepare(int dev) {
+  static bool set[64] = {false};
+  if (!set[dev]) {
+    VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tf32_kernel<SA, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TcCfg<SA != 0>::SMEM));
+    set[dev] = true;
+  }
+  return VB_OK;
+}
 
 }  // namespace
 
@@ -473,28 +498,34 @@ bool g_attr_set[2][64] = {{false}};
 // ws (optional, ws_elems floats): when there are few tiles and a long K
 // loop, K is cut into slices whose partial products go to ws and are summed
 // in slice order by a second kernel.
+// split: three tf32 products (hi*hi + hi*lo + lo*hi); Alo / Blo (optional,
+// same pitch as A / B): the operand is already split, A holding the hi part
+// (x with its low 13 mantissa bits cleared) and Alo x - hi.
 vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long ldb, int M, int N, int K,
                        int mode, float *D, long long ldd, double *Y, int nh, int *err, cudaStream_t st,
-                       bool split, float *ws, long long ws_elems) {
+                       bool split, float *ws, long long ws_elems, const float *Alo, const float *Blo) {
   if (M <= 0 || N <= 0 || K <= 0) return VB_OK;
   if (mode == 1 && N != 2 * nh) return fail(VB_EINVAL, "tc_gemm: complex output needs N = 2 nh");
+  if (!split && (Alo || Blo)) return fail(VB_EINVAL, "tc_gemm: split operands need the split product");
   VB_TRY(get_encode());
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, talo, tblo;
   VB_TRY(make_map(&ta, A, M, K, lda));
   VB_TRY(make_map(&tb, B, N, K, ldb));
+  talo = ta;
+  tblo = tb;
+  if (Alo) VB_TRY(make_map(&talo, Alo, M, K, lda));
+  if (Blo) VB_TRY(make_map(&tblo, Blo, N, K, ldb));
   int dev = 0;
   VB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "tc_gemm: device ordinal out of range");
-  if (!g_attr_set[0][dev]) {
-    VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TcCfg<false>::SMEM));
-    g_attr_set[0][dev] = true;
-  }
-  if (!g_attr_set[1][dev]) {
-    VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TcCfg<true>::SMEM));
-    g_attr_set[1][dev] = true;
-  }
+  const int sa = split ? (Alo ? 2 : 1) : 0, sb = split ? (Blo ? 2 : 1) : 0;
+  vb_status ps;
+  if (sa == 0) ps = tc_prepare<0, 0>(dev);
+  else if (sa == 1 && sb == 1) ps = tc_prepare<1, 1>(dev);
+  else if (sa == 1) ps = tc_prepare<1, 2>(dev);
+  else if (sb == 1) ps = tc_prepare<2, 1>(dev);
+  else ps = tc_prepare<2, 2>(dev);
+  if (ps != VB_OK) return ps;
   const long long tm = (M + TC_BM - 1) / TC_BM, tn = (N + TC_BN - 1) / TC_BN;
   if (tm * tn > INT_MAX / 64) return fail(VB_EINVAL, "tc_gemm: too many tiles");
   static int sm_count[64] = {0};
@@ -515,12 +546,16 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
   Epi e = ks > 1 ? Epi{0, ws, N, nullptr, 0, (long long)M * N} : Epi{mode, D, ldd, Y, nh, 0};
   const int items = tiles * ks;
   const int grid = std::min(items, sms);
-  if (split)
-    tc_gemm_tf32_kernel<true><<<grid, TC_THREADS, TcCfg<true>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, ks, kb_per,
-                                                                           e, err);
-  else
-    tc_gemm_tf32_kernel<false><<<grid, TC_THREADS, TcCfg<false>::SMEM, st>>>(ta, tb, M, N, K, (int)tm, tiles, ks,
-                                                                             kb_per, e, err);
+  const size_t smem = split ? TcCfg<true>::SMEM : TcCfg<false>::SMEM;
+#define VB_TC_LAUNCH(SA_, SB_)                                                                                       \
+  tc_gemm_tf32_kernel<SA_, SB_><<<grid, TC_THREADS, smem, st>>>(ta, tb, talo, tblo, M, N, K, (int)tm, tiles, ks, \
+                                                                kb_per, e, err)
+  if (sa == 0) VB_TC_LAUNCH(0, 0);
+  else if (sa == 1 && sb == 1) VB_TC_LAUNCH(1, 1);
+  else if (sa == 1) VB_TC_LAUNCH(1, 2);
+  else if (sb == 1) VB_TC_LAUNCH(2, 1);
+  else VB_TC_LAUNCH(2, 2);
+#undef VB_TC_LAUNCH
   VB_CHECK_LAUNCH();
   if (ks > 1) {
     const long long tot = mode == 0 ? (long long)M * N : (long long)M * nh;
