@@ -569,7 +569,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old,
 
 // Mixed form of the split (Sec. 2.1.1 truncation). The kept Schmidt
 // directions are found in FP32: subspace iteration on theta for the
-// r = min(n, m_max + 17, 128) leading eigenvectors of rho, then a
+// r = min(n, m_max + 9, 128) leading eigenvectors of rho, then a
 // Rayleigh-Ritz step on their span (S = Q^* rho Q^T diagonalised in FP32) for
 // the kws = min(r, m_max + 1) leading Ritz vectors. Everything that defines
 // the new tensors is FP64: the Ritz basis is re-orthonormalised (one Lowdin
@@ -584,7 +584,7 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
   const long long nm = (long long)n1 * n2;
   const cd *M = s->theta;
   const int kw = std::min(n, o.m_max + 1);
-  const int r = std::min(n, std::min(kw + 16, s->rcap));
+  const int r = std::min(n, std::min(kw + 8, s->rcap));
   const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
   auto G64 = [&](int Mm, int Nn, int Kk, int opA, const cd *A, long long lda, long long asz, int opB, const cd *B,
                  long long ldb, long long bsz, cd *C, long long ldc, long long csz) {
