@@ -214,83 +214,143 @@ __global__ void combine_kernel(const cd *__restrict__ V, long long ldv, int nv,
 
 // ---------------------------------------------------------------------------
 // u = exp(-i T tau) e_1 for the symmetric tridiagonal Lanczos matrix T
-// (alpha on the diagonal, beta off it), kdim <= 64, one warp. T is shifted by
-// the midpoint mu of its diagonal; exp(-i (T - mu) tau) e_1 is built from s
-// substeps, each the degree-18 Taylor polynomial of A = -i (T - mu) tau / s
-// applied to the current vector, with s chosen so that ||A||_inf <= 1/2
-// (Taylor remainder < 2^-19 / 19! per substep). Row r of the vector lives in
-// lane r % 32, slot r / 32.
-__global__ void tridiag_expm_kernel(const double *__restrict__ alpha,
-                                    const double *__restrict__ beta, int kdim, double tau,
-                                    const double *bnext, cd *u, double *out_err) {
+// (alpha on the diagonal, beta off it), kdim <= 64, one warp; row r lives in
+// lane r % 32, slot r / 32. Chebyshev expansion (Jacobi-Anger identity):
+// with T's Gershgorin interval [mu - D, mu + D] and H = (T - mu) / D,
+//   exp(-i z H) = J_0(z) + 2 sum_{n >= 1} (-i)^n J_n(z) T_n(H),   z = D tau,
+// T_n(H) v from the three-term recurrence v_{n+1} = 2 H v_n - v_{n-1}, and
+// exp(-i T tau) = exp(-i mu tau) exp(-i z H). The Bessel values come from
+// Miller's backward recurrence normalised by J_0 + 2 sum_k J_2k = 1; terms
+// stop at n = |z| + 30 (J_n(z) < 1e-17 beyond for |z| <= 40); larger |z|
+// is cut into substeps of |z| <= 40. Also writes
+// out_err = bnext |u_{kdim-1}|, the Lanczos error estimate.
+constexpr int TRI_ZMAX = 40;                 // largest |z| per substep
+constexpr int TRI_NMAX = TRI_ZMAX + 30;      // terms per substep
+constexpr int TRI_MILLER = TRI_NMAX + 40;    // start of the backward recurrence (even)
+
+__device__ __forceinline__ void tri_matvec(const double *d, const double *bl, const double *br, const cd *v, cd *w,
+                                           int lane) {
+  // neighbours row - 1 and row + 1 of both slots
+  double u0x = __shfl_up_sync(0xffffffffu, v[0].x, 1), u0y = __shfl_up_sync(0xffffffffu, v[0].y, 1);
+  double u1x = __shfl_up_sync(0xffffffffu, v[1].x, 1), u1y = __shfl_up_sync(0xffffffffu, v[1].y, 1);
+  const double c0x = __shfl_sync(0xffffffffu, v[0].x, 31), c0y = __shfl_sync(0xffffffffu, v[0].y, 31);
+  double d0x = __shfl_down_sync(0xffffffffu, v[0].x, 1), d0y = __shfl_down_sync(0xffffffffu, v[0].y, 1);
+  double d1x = __shfl_down_sync(0xffffffffu, v[1].x, 1), d1y = __shfl_down_sync(0xffffffffu, v[1].y, 1);
+  const double c1x = __shfl_sync(0xffffffffu, v[1].x, 0), c1y = __shfl_sync(0xffffffffu, v[1].y, 0);
+  if (lane == 0) {
+    u0x = u0y = 0.0;
+    u1x = c0x;
+    u1y = c0y;
+  }
+  if (lane == 31) {
+    d0x = c1x;
+    d0y = c1y;
+    d1x = d1y = 0.0;
+  }
+  w[0] = mkc(d[0] * v[0].x + bl[0] * u0x + br[0] * d0x, d[0] * v[0].y + bl[0] * u0y + br[0] * d0y);
+  w[1] = mkc(d[1] * v[1].x + bl[1] * u1x + br[1] * d1x, d[1] * v[1].y + bl[1] * u1y + br[1] * d1y);
+}
+
+__global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const double *__restrict__ beta, int kdim,
+                                    double tau, const double *bnext, cd *u, double *out_err) {
+  __shared__ double jn[TRI_NMAX + 1];
   const int lane = threadIdx.x;
-  double a[2], bl[2], br[2];  // diagonal, coupling to row-1, coupling to row+1
-  double amin = 1e300, amax = -1e300;
-  for (int r = 0; r < kdim; ++r) {
-    amin = fmin(amin, alpha[r]);
-    amax = fmax(amax, alpha[r]);
+  double lo = 1e300, hi = -1e300;
+  for (int r = lane; r < kdim; r += 32) {
+    const double rad = (r > 0 ? fabs(beta[r - 1]) : 0.0) + (r + 1 < kdim ? fabs(beta[r]) : 0.0);
+    lo = fmin(lo, alpha[r] - rad);
+    hi = fmax(hi, alpha[r] + rad);
   }
-  const double mu = 0.5 * (amin + amax);
-  double nrm = 0.0;
-  for (int r = 0; r < kdim; ++r) {
-    double s = fabs(alpha[r] - mu);
-    if (r > 0) s += fabs(beta[r - 1]);
-    if (r + 1 < kdim) s += fabs(beta[r]);
-    nrm = fmax(nrm, s);
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
-  nrm *= fabs(tau);
-  int steps = (int)ceil(nrm / 0.5);
+  const double mu = 0.5 * (lo + hi);
+  const double D = 0.5 * (hi - lo);
+  const double ztot = D * fabs(tau);
+  int steps = (int)ceil(ztot / TRI_ZMAX);
   if (steps < 1) steps = 1;
-  const double h = tau / steps;
-  cd x[2];
-  for (int sl = 0; sl < 2; ++sl) {
-    int r = lane + 32 * sl;
-    bool ok = r < kdim;
-    a[sl] = ok ? (alpha[r] - mu) * h : 0.0;
-    bl[sl] = (ok && r > 0) ? beta[r - 1] * h : 0.0;
-    br[sl] = (ok && r + 1 < kdim) ? beta[r] * h : 0.0;
-    x[sl] = mkc(r == 0 ? 1.0 : 0.0, 0.0);
+  const double ts = tau / steps;
+  const double z = D * fabs(ts);
+  // Bessel values J_n(z), n <= nt (lane 0)
+  const int nt = z > 0.0 ? min(TRI_NMAX, (int)ceil(z) + 30) : 0;
+  if (lane == 0) {
+    for (int n = 0; n <= TRI_NMAX; ++n) jn[n] = 0.0;
+    if (z > 0.0) {
+      double fp = 0.0, f = 1e-280, norm = 0.0;  // f_{n+1}, f_n
+      for (int n = TRI_MILLER; n >= 0; --n) {
+        if (n <= nt) jn[n] = f;
+        if (n % 2 == 0) norm += (n == 0 ? 1.0 : 2.0) * f;
+        if (n > 0) {
+          const double fm = (2.0 * n / z) * f - fp;
+          fp = f;
+          f = fm;
+        }
+        if (fabs(f) > 1e250) {  // rescale everything computed so far
+          f *= 1e-250;
+          fp *= 1e-250;
+          norm *= 1e-250;
+          for (int q = n; q <= nt; ++q) jn[q] *= 1e-250;
+        }
+      }
+      const double s = 1.0 / norm;
+      for (int n = 0; n <= nt; ++n) jn[n] *= s;
+    } else {
+      jn[0] = 1.0;
+    }
   }
+  __syncwarp();
+  // H = (T - mu) / D for this lane's rows; the zero rows beyond kdim stay zero
+  double d[2], bl[2], br[2];
+  const double inv = D > 0.0 ? 1.0 / D : 0.0;
+  for (int sl = 0; sl < 2; ++sl) {
+    const int r = lane + 32 * sl;
+    const bool ok = r < kdim;
+    d[sl] = ok ? (alpha[r] - mu) * inv : 0.0;
+    bl[sl] = (ok && r > 0) ? beta[r - 1] * inv : 0.0;
+    br[sl] = (ok && r + 1 < kdim) ? beta[r] * inv : 0.0;
+  }
+  // (-i)^n for ts >= 0, (+i)^n for ts < 0 (J_n(-z) = (-1)^n J_n(z))
+  const double sg = ts >= 0.0 ? -1.0 : 1.0;
+  double ps, pc;
+  sincos(-mu * ts, &ps, &pc);
+  cd x[2] = {mkc(lane == 0 ? 1.0 : 0.0, 0.0), mkc(0.0, 0.0)};
   for (int st = 0; st < steps; ++st) {
-    cd term[2] = {x[0], x[1]};
-    cd acc[2] = {x[0], x[1]};
-    for (int n = 1; n <= 18; ++n) {
-      // neighbours of each row: row-1 and row+1
-      cd up0, up1, dn0, dn1;  // up = row-1, dn = row+1
-      double t0x = term[0].x, t0y = term[0].y, t1x = term[1].x, t1y = term[1].y;
-      double p0x = __shfl_up_sync(0xffffffffu, t0x, 1), p0y = __shfl_up_sync(0xffffffffu, t0y, 1);
-      double p1x = __shfl_up_sync(0xffffffffu, t1x, 1), p1y = __shfl_up_sync(0xffffffffu, t1y, 1);
-      double q0x = __shfl_down_sync(0xffffffffu, t0x, 1), q0y = __shfl_down_sync(0xffffffffu, t0y, 1);
-      double q1x = __shfl_down_sync(0xffffffffu, t1x, 1), q1y = __shfl_down_sync(0xffffffffu, t1y, 1);
-      double w31x = __shfl_sync(0xffffffffu, t0x, 31), w31y = __shfl_sync(0xffffffffu, t0y, 31);
-      double l0x = __shfl_sync(0xffffffffu, t1x, 0), l0y = __shfl_sync(0xffffffffu, t1y, 0);
-      up0 = lane > 0 ? mkc(p0x, p0y) : mkc(0.0, 0.0);
-      up1 = lane > 0 ? mkc(p1x, p1y) : mkc(w31x, w31y);
-      dn0 = lane < 31 ? mkc(q0x, q0y) : mkc(l0x, l0y);
-      dn1 = lane < 31 ? mkc(q1x, q1y) : mkc(0.0, 0.0);
-      cd nb[2][2] = {{up0, dn0}, {up1, dn1}};
+    cd v0[2] = {x[0], x[1]}, v1[2], acc[2];
+    tri_matvec(d, bl, br, v0, v1, lane);
+    // n = 0 and n = 1 terms: J_0 v0 + 2 (sg i) J_1 v1
+    const double j0 = jn[0], j1 = 2.0 * jn[1] * sg;
+    for (int sl = 0; sl < 2; ++sl)
+      acc[sl] = mkc(j0 * v0[sl].x - j1 * v1[sl].y, j0 * v0[sl].y + j1 * v1[sl].x);
+    for (int n = 2; n <= nt; ++n) {
+      cd v2[2];
+      tri_matvec(d, bl, br, v1, v2, lane);
+      // c_n = 2 (sg i)^n J_n: n % 4 = 0 -> 2J, 1 -> 2 sg i J, 2 -> -2J, 3 -> -2 sg i J
+      const double cj = 2.0 * jn[n];
+      const int m = n & 3;
       for (int sl = 0; sl < 2; ++sl) {
-        // y = (T - mu) h * term ; new term = -i y / n
-        double yx = a[sl] * term[sl].x + bl[sl] * nb[sl][0].x + br[sl] * nb[sl][1].x;
-        double yy = a[sl] * term[sl].y + bl[sl] * nb[sl][0].y + br[sl] * nb[sl][1].y;
-        term[sl] = mkc(yy / n, -yx / n);
-        acc[sl] = cadd(acc[sl], term[sl]);
+        v2[sl] = mkc(2.0 * v2[sl].x - v0[sl].x, 2.0 * v2[sl].y - v0[sl].y);
+        if (m == 0)
+          acc[sl] = mkc(acc[sl].x + cj * v2[sl].x, acc[sl].y + cj * v2[sl].y);
+        else if (m == 2)
+          acc[sl] = mkc(acc[sl].x - cj * v2[sl].x, acc[sl].y - cj * v2[sl].y);
+        else {
+          const double c = (m == 1 ? cj : -cj) * sg;  // times i
+          acc[sl] = mkc(acc[sl].x - c * v2[sl].y, acc[sl].y + c * v2[sl].x);
+        }
+        v0[sl] = v1[sl];
+        v1[sl] = v2[sl];
       }
     }
-    x[0] = acc[0];
-    x[1] = acc[1];
+    for (int sl = 0; sl < 2; ++sl) x[sl] = mkc(pc * acc[sl].x - ps * acc[sl].y, pc * acc[sl].y + ps * acc[sl].x);
   }
-  // phase exp(-i mu tau)
-  double sn, cs;
-  sincos(-mu * tau, &sn, &cs);
-  cd ph = mkc(cs, sn);
   for (int sl = 0; sl < 2; ++sl) {
-    int r = lane + 32 * sl;
-    if (r < kdim) u[r] = cmul(ph, x[sl]);
+    const int r = lane + 32 * sl;
+    if (r < kdim) u[r] = x[sl];
   }
   __syncwarp();
   if (lane == 0) {
-    cd last = u[kdim - 1];
+    const cd last = u[kdim - 1];
     out_err[0] = bnext[0] * sqrt(cabs2(last));
   }
 }
