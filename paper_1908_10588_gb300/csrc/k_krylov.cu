@@ -221,8 +221,9 @@ __global__ void combine_kernel(const cd *__restrict__ V, long long ldv, int nv,
 // T_n(H) v from the three-term recurrence v_{n+1} = 2 H v_n - v_{n-1}, and
 // exp(-i T tau) = exp(-i mu tau) exp(-i z H). The Bessel values come from
 // Miller's backward recurrence normalised by J_0 + 2 sum_k J_2k = 1; terms
-// stop at n = |z| + 30 (J_n(z) < 1e-17 beyond for |z| <= 40); larger |z|
-// is cut into substeps of |z| <= 40. Also writes
+// stop at the last n > |z| with |J_n(z)| >= 1e-18 (at most |z| + 30; J_n
+// falls super-exponentially beyond |z|); larger |z| is cut into substeps of
+// |z| <= 40. Also writes
 // out_err = bnext |u_{kdim-1}|, the Lanczos error estimate.
 constexpr int TRI_ZMAX = 40;                 // largest |z| per substep
 constexpr int TRI_NMAX = TRI_ZMAX + 30;      // terms per substep
@@ -251,9 +252,19 @@ __device__ __forceinline__ void tri_matvec(const double *d, const double *bl, co
   w[1] = mkc(d[1] * v[1].x + bl[1] * u1x + br[1] * d1x, d[1] * v[1].y + bl[1] * u1y + br[1] * d1y);
 }
 
+// one-slot form (kdim <= 32)
+__device__ __forceinline__ void tri_matvec1(double d, double bl, double br, cd v, cd &w, int lane) {
+  double ux = __shfl_up_sync(0xffffffffu, v.x, 1), uy = __shfl_up_sync(0xffffffffu, v.y, 1);
+  double dx = __shfl_down_sync(0xffffffffu, v.x, 1), dy = __shfl_down_sync(0xffffffffu, v.y, 1);
+  if (lane == 0) ux = uy = 0.0;
+  if (lane == 31) dx = dy = 0.0;
+  w = mkc(d * v.x + bl * ux + br * dx, d * v.y + bl * uy + br * dy);
+}
+
 __global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const double *__restrict__ beta, int kdim,
                                     double tau, const double *bnext, cd *u, double *out_err) {
   __shared__ double jn[TRI_NMAX + 1];
+  __shared__ int s_nt;
   const int lane = threadIdx.x;
   double lo = 1e300, hi = -1e300;
   for (int r = lane; r < kdim; r += 32) {
@@ -295,11 +306,17 @@ __global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const doub
       }
       const double s = 1.0 / norm;
       for (int n = 0; n <= nt; ++n) jn[n] *= s;
+      // last term needed: beyond z the values fall super-exponentially
+      int last = nt;
+      while (last > 1 && last > z + 1.0 && fabs(jn[last]) < 1e-18) --last;
+      s_nt = last;
     } else {
       jn[0] = 1.0;
+      s_nt = 0;
     }
   }
   __syncwarp();
+  const int nu = s_nt;
   // H = (T - mu) / D for this lane's rows; the zero rows beyond kdim stay zero
   double d[2], bl[2], br[2];
   const double inv = D > 0.0 ? 1.0 / D : 0.0;
@@ -315,20 +332,27 @@ __global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const doub
   double ps, pc;
   sincos(-mu * ts, &ps, &pc);
   cd x[2] = {mkc(lane == 0 ? 1.0 : 0.0, 0.0), mkc(0.0, 0.0)};
+  const int ns = kdim > 32 ? 2 : 1;  // row slots in use
   for (int st = 0; st < steps; ++st) {
     cd v0[2] = {x[0], x[1]}, v1[2], acc[2];
-    tri_matvec(d, bl, br, v0, v1, lane);
+    if (ns == 2)
+      tri_matvec(d, bl, br, v0, v1, lane);
+    else
+      tri_matvec1(d[0], bl[0], br[0], v0[0], v1[0], lane), v1[1] = mkc(0.0, 0.0);
     // n = 0 and n = 1 terms: J_0 v0 + 2 (sg i) J_1 v1
     const double j0 = jn[0], j1 = 2.0 * jn[1] * sg;
     for (int sl = 0; sl < 2; ++sl)
       acc[sl] = mkc(j0 * v0[sl].x - j1 * v1[sl].y, j0 * v0[sl].y + j1 * v1[sl].x);
-    for (int n = 2; n <= nt; ++n) {
+    for (int n = 2; n <= nu; ++n) {
       cd v2[2];
-      tri_matvec(d, bl, br, v1, v2, lane);
+      if (ns == 2)
+        tri_matvec(d, bl, br, v1, v2, lane);
+      else
+        tri_matvec1(d[0], bl[0], br[0], v1[0], v2[0], lane), v2[1] = mkc(0.0, 0.0);
       // c_n = 2 (sg i)^n J_n: n % 4 = 0 -> 2J, 1 -> 2 sg i J, 2 -> -2J, 3 -> -2 sg i J
       const double cj = 2.0 * jn[n];
       const int m = n & 3;
-      for (int sl = 0; sl < 2; ++sl) {
+      for (int sl = 0; sl < ns; ++sl) {
         v2[sl] = mkc(2.0 * v2[sl].x - v0[sl].x, 2.0 * v2[sl].y - v0[sl].y);
         if (m == 0)
           acc[sl] = mkc(acc[sl].x + cj * v2[sl].x, acc[sl].y + cj * v2[sl].y);
