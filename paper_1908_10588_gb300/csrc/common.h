@@ -237,8 +237,8 @@ vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, d
                               double *out, double *partial, cudaStream_t st);
 vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
                     cudaStream_t st);
-// x *= 1/ (*nrm)  (device scalar)
-vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st);
+// x *= 1/ (*nrm)  (device scalar); keep (nullable): *keep = *nrm
+vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep = nullptr);
 // y = s * x with s = *num / *den (device scalars; den may be null -> 1)
 vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st);
 // combine: y = (*nrm) * sum_j u[j] V[j]
@@ -266,9 +266,10 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
                       cplx<R> *evecs, void *work, cudaStream_t st, int rounds = 0);
 
 // Krylov tridiagonal exponential: from alpha[0..k], beta[0..k-1] (device),
-// u = exp(-i T tau) e_1 (k+1 complex) and err = bnext * |u_k| written to
-// out_err (device or mapped host).
-vb_status tridiag_expm(const double *alpha, const double *beta, int kdim, double tau,
-                       const double *bnext, cd *u, double *out_err, cudaStream_t st);
+// u = exp(-i T tau) e_1 (k+1 complex); out[0] = bnext * |u_k|, out[1] =
+// bnext (device or mapped host). With c, c2 given, alpha[k] is first set to
+// Re c[k] + Re c2[k] (the two Gram-Schmidt passes' <v_k, H v_k>).
+vb_status tridiag_expm(const cd *c, const cd *c2, double *alpha, const double *beta, int kdim, double tau,
+                       const double *bnext, cd *u, double *out, cudaStream_t st);
 
 }  // namespace vb

@@ -178,8 +178,9 @@ __global__ void norm2_final(const double *__restrict__ partial, int n_part, doub
   if (threadIdx.x == 0) out[0] = sqrt(s);
 }
 
-__global__ void scale_inv_kernel(cd *x, long long n, const double *nrm) {
+__global__ void scale_inv_kernel(cd *x, long long n, const double *nrm, double *keep) {
   double s = 1.0 / nrm[0];
+  if (keep && blockIdx.x == 0 && threadIdx.x == 0) keep[0] = nrm[0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     cd a = x[i];
@@ -223,8 +224,9 @@ __global__ void combine_kernel(const cd *__restrict__ V, long long ldv, int nv,
 // Miller's backward recurrence normalised by J_0 + 2 sum_k J_2k = 1; terms
 // stop at the last n > |z| with |J_n(z)| >= 1e-18 (at most |z| + 30; J_n
 // falls super-exponentially beyond |z|); larger |z| is cut into substeps of
-// |z| <= 40. Also writes
-// out_err = bnext |u_{kdim-1}|, the Lanczos error estimate.
+// |z| <= 40. With c != nullptr the kernel first sets the newest diagonal
+// entry alpha[kdim - 1] = Re c[kdim - 1] + Re c2[kdim - 1]. Writes
+// out[0] = bnext |u_{kdim-1}| (the Lanczos error estimate), out[1] = bnext.
 constexpr int TRI_ZMAX = 40;                 // largest |z| per substep
 constexpr int TRI_NMAX = TRI_ZMAX + 30;      // terms per substep
 constexpr int TRI_MILLER = TRI_NMAX + 40;    // start of the backward recurrence (even)
@@ -261,11 +263,14 @@ __device__ __forceinline__ void tri_matvec1(double d, double bl, double br, cd v
   w = mkc(d * v.x + bl * ux + br * dx, d * v.y + bl * uy + br * dy);
 }
 
-__global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const double *__restrict__ beta, int kdim,
-                                    double tau, const double *bnext, cd *u, double *out_err) {
+__global__ void tridiag_expm_kernel(const cd *c, const cd *c2, double *alpha, const double *__restrict__ beta,
+                                    int kdim, double tau, const double *bnext, cd *u, double *out) {
   __shared__ double jn[TRI_NMAX + 1];
   __shared__ int s_nt;
   const int lane = threadIdx.x;
+  // the newest diagonal entry: sum of the two Gram-Schmidt passes' <v_k, H v_k>
+  if (c && lane == 0) alpha[kdim - 1] = c[kdim - 1].x + c2[kdim - 1].x;
+  __syncwarp();
   double lo = 1e300, hi = -1e300;
   for (int r = lane; r < kdim; r += 32) {
     const double rad = (r > 0 ? fabs(beta[r - 1]) : 0.0) + (r + 1 < kdim ? fabs(beta[r]) : 0.0);
@@ -289,11 +294,12 @@ __global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const doub
     for (int n = 0; n <= TRI_NMAX; ++n) jn[n] = 0.0;
     if (z > 0.0) {
       double fp = 0.0, f = 1e-280, norm = 0.0;  // f_{n+1}, f_n
-      for (int n = TRI_MILLER; n >= 0; --n) {
+      const double tz = 2.0 / z;
+      for (int n = min(TRI_MILLER, nt + 40) & ~1; n >= 0; --n) {
         if (n <= nt) jn[n] = f;
         if (n % 2 == 0) norm += (n == 0 ? 1.0 : 2.0) * f;
         if (n > 0) {
-          const double fm = (2.0 * n / z) * f - fp;
+          const double fm = (n * tz) * f - fp;
           fp = f;
           f = fm;
         }
@@ -375,7 +381,8 @@ __global__ void tridiag_expm_kernel(const double *__restrict__ alpha, const doub
   __syncwarp();
   if (lane == 0) {
     const cd last = u[kdim - 1];
-    out_err[0] = bnext[0] * sqrt(cabs2(last));
+    out[0] = bnext[0] * sqrt(cabs2(last));
+    out[1] = bnext[0];
   }
 }
 
@@ -436,9 +443,9 @@ vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int 
   return VB_OK;
 }
 
-vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st) {
+vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep) {
   if (n == 0) return VB_OK;
-  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm);
+  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm, keep);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
@@ -458,10 +465,10 @@ vb_status vec_combine(const cd *V, long long ldv, int nv, const cd *u, const dou
   return VB_OK;
 }
 
-vb_status tridiag_expm(const double *alpha, const double *beta, int kdim, double tau,
-                       const double *bnext, cd *u, double *out_err, cudaStream_t st) {
+vb_status tridiag_expm(const cd *c, const cd *c2, double *alpha, const double *beta, int kdim, double tau,
+                       const double *bnext, cd *u, double *out, cudaStream_t st) {
   if (kdim < 1 || kdim > 64) return fail(VB_EINVAL, "tridiag_expm: kdim must be in 1..64");
-  tridiag_expm_kernel<<<1, 32, 0, st>>>(alpha, beta, kdim, tau, bnext, u, out_err);
+  tridiag_expm_kernel<<<1, 32, 0, st>>>(c, c2, alpha, beta, kdim, tau, bnext, u, out);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

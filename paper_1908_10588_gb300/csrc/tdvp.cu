@@ -128,10 +128,6 @@ __global__ void subspace_rows_c64(const cf *__restrict__ q, cd *__restrict__ out
   }
 }
 
-__global__ void set_alpha_kernel(const cd *c, const cd *c2, int k, double *alpha) {
-  alpha[k] = c[k].x + c2[k].x;
-}
-
 __global__ void populations_kernel(const cd *C, int d, int mR, double *out) {
   // C[0][s][b]: P_s = sum_b |C[s,b]|^2 / sum |C|^2 ; one warp per s, then normalise
   __shared__ double ps[64];
@@ -421,10 +417,8 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     }
     VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st));
     VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st));
-    set_alpha_kernel<<<1, 1, 0, st>>>(s->d_c, s->d_c2, k, s->d_alpha);
-    VB_CHECK_LAUNCH();
-    VB_TRY(tridiag_expm(s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
-    VB_TRY_CUDA(cudaMemcpyAsync(s->d_flag + 1, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
+
+    VB_TRY(tridiag_expm(s->d_c, s->d_c2, s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     {
       const double nv1 = s->dtype == VB_MIXED ? (double)(k > 0 ? 2 : 1) : (double)(k + 1);
       prof_end(PH_KRYLOV, st, Nd * (16.0 * (nv1 + k + 1) + 4.0));
@@ -438,8 +432,7 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       break;
     }
     prof_begin(PH_KRYLOV, st);
-    VB_TRY_CUDA(cudaMemcpyAsync(s->d_beta + k, s->d_bnext, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st));
+    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k));
     prof_end(PH_KRYLOV, st, 2.0 * Nd);
   }
   *iters = kdim;
