@@ -204,7 +204,7 @@ vb_status wapply(const MpoSite &site, int dir, const cplx<R> *X, WStrides xs, lo
 
 // ------------------------------------------------------------ vectors
 vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
-                        cd *partial, int n_part, cudaStream_t st);
+                        cd *partial, int n_part, cudaStream_t st, unsigned int *cnt = nullptr);
 // w -= sum_j c[j] V[j] (sign = -1) or w += ... (sign = +1); c on device; cscale applied
 vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
                          long long n, cudaStream_t st);
@@ -233,8 +233,10 @@ vb_status norm2_sq_f32(const cf *x, long long n, double *out, double *partial, i
 // out[0] = *capt, out[1] = *cnt
 vb_status subspace_status(const double *capt, const int *cnt, double *out, cudaStream_t st);
 // vec_multi_axpy, then *out = |w| (partial: at least 512 doubles)
+// cnt (nullable, zeroed device counters: one per group of 8 vectors for the
+// inner products, one for the norm): the last block reduces, no extra launch
 vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
-                              double *out, double *partial, cudaStream_t st);
+                              double *out, double *partial, cudaStream_t st, unsigned int *cnt = nullptr);
 vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
                     cudaStream_t st);
 // x *= 1/ (*nrm)  (device scalar); keep (nullable): *keep = *nrm

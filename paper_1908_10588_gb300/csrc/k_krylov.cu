@@ -69,10 +69,15 @@ __device__ __forceinline__ void dot_group(const cd *__restrict__ Vg, long long l
   }
 }
 
+// With cnt != nullptr (one zeroed counter per vector group), the last block
+// of a group to finish sums the group's partials over all blocks, in block
+// order (the same order as reduce_parts_cd), writes out[j] and re-zeroes its
+// counter: no separate reduction launch.
 __global__ void __launch_bounds__(RT) multi_dot_part(const cd *__restrict__ V, long long ldv, int nv,
                                                      const cd *__restrict__ w, long long n,
-                                                     cd *__restrict__ partial) {
+                                                     cd *__restrict__ partial, unsigned int *cnt, cd *out) {
   __shared__ double sh[(RT / 32) * 2 * DOT_JB];
+  __shared__ unsigned int s_ticket;
   const int j0 = blockIdx.y * DOT_JB;
   const int jn = min(DOT_JB, nv - j0);
   const long long chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -89,6 +94,26 @@ __global__ void __launch_bounds__(RT) multi_dot_part(const cd *__restrict__ V, l
     case 2: dot_group<2>(Vg, ldv, w, i0, i1, sh, out2); break;
     default: dot_group<1>(Vg, ldv, w, i0, i1, sh, out2); break;
   }
+  if (!cnt) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&cnt[blockIdx.y], 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = wid; j < jn; j += RT / 32) {
+    double sx = 0.0, sy = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double2 p = __ldcg(reinterpret_cast<const double2 *>(partial + (long long)b * nv + j0 + j));
+      sx += p.x;
+      sy += p.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) out[j0 + j] = mkc(sx, sy);
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
 __global__ void reduce_parts_cd(const cd *__restrict__ partial, int n_part, int nv, cd *out) {
@@ -112,7 +137,8 @@ __global__ void reduce_parts_cd(const cd *__restrict__ partial, int n_part, int 
 // the sum of |w_new[i]|^2 over its elements to partial[blockIdx.x].
 __global__ void __launch_bounds__(256) multi_axpy_kernel(const cd *__restrict__ V, long long ldv, int nv,
                                                          const cd *__restrict__ c, double sign, cd *__restrict__ w,
-                                                         long long n, double *__restrict__ partial) {
+                                                         long long n, double *__restrict__ partial,
+                                                         unsigned int *cnt, double *nrm_out) {
   __shared__ cd cs[128];
   __shared__ double sh[8];
   for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = cscale(c[j], sign);
@@ -153,6 +179,25 @@ __global__ void __launch_bounds__(256) multi_axpy_kernel(const cd *__restrict__ 
       double s = 0.0;
       for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sh[w2];
       partial[blockIdx.x] = s;
+    }
+    if (cnt) {
+      // the last block sums the block partials in block order (as
+      // norm2_final does) and writes |w|
+      __shared__ unsigned int s_ticket;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_ticket = atomicAdd(cnt, 1u);
+      __syncthreads();
+      if (s_ticket == gridDim.x - 1 && threadIdx.x < 32) {
+        __threadfence();
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(partial + b);
+        s = warp_sum(s);
+        if (threadIdx.x == 0) {
+          nrm_out[0] = sqrt(s);
+          cnt[0] = 0u;
+        }
+      }
     }
   }
 }
@@ -403,13 +448,15 @@ int reduce_parts(long long n) {
 }
 
 vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
-                        cd *partial, int n_part, cudaStream_t st) {
+                        cd *partial, int n_part, cudaStream_t st, unsigned int *cnt) {
   if (nv <= 0) return VB_OK;
   if (nv > 128 || (long long)n_part * nv > 512LL * 128) return fail(VB_EINVAL, "multi_dot: too many vectors");
-  multi_dot_part<<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial);
+  multi_dot_part<<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial, cnt, out);
   VB_CHECK_LAUNCH();
-  reduce_parts_cd<<<(nv + 7) / 8, 256, 0, st>>>(partial, n_part, nv, out);
-  VB_CHECK_LAUNCH();
+  if (!cnt) {
+    reduce_parts_cd<<<(nv + 7) / 8, 256, 0, st>>>(partial, n_part, nv, out);
+    VB_CHECK_LAUNCH();
+  }
   return VB_OK;
 }
 
@@ -417,20 +464,23 @@ vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double
                          long long n, cudaStream_t st) {
   if (nv <= 0 || n == 0) return VB_OK;
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
-  multi_axpy_kernel<<<grid_for((n + 1) / 2, 256), 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr);
+  multi_axpy_kernel<<<grid_for((n + 1) / 2, 256), 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr, nullptr,
+                                                                 nullptr);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
 
 vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
-                              double *out, double *partial, cudaStream_t st) {
+                              double *out, double *partial, cudaStream_t st, unsigned int *cnt) {
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
   if (nv <= 0 || n == 0) return vec_norm2(w, n, out, partial, reduce_parts(n), st);
   const int blocks = (int)std::min<long long>(512, std::max<long long>(1, (n + 511) / 512));
-  multi_axpy_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial);
+  multi_axpy_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out);
   VB_CHECK_LAUNCH();
-  norm2_final<<<1, 32, 0, st>>>(partial, blocks, out);
-  VB_CHECK_LAUNCH();
+  if (!cnt) {
+    norm2_final<<<1, 32, 0, st>>>(partial, blocks, out);
+    VB_CHECK_LAUNCH();
+  }
   return VB_OK;
 }
 

@@ -190,6 +190,7 @@ struct vb_mps {
   cd *d_c = nullptr, *d_c2 = nullptr, *d_u = nullptr, *d_partc = nullptr;
   double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
   int *d_tcerr = nullptr;                        // raised by a tensor-core kernel whose wait ran out
+  unsigned int *d_cnt = nullptr;                 // zeroed block counters of the last-block reductions
   // subspace iteration of the mixed split
   cf *subZ = nullptr, *subT = nullptr, *subG = nullptr, *subW = nullptr, *skws32 = nullptr;
   long long skws32_elems = 0;
@@ -409,14 +410,14 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       // then one full pass: the full pass then removes components that are
       // already small, so it loses no orthogonality to cancellation
       const int j0 = k > 0 ? k - 1 : 0;
-      VB_TRY(vec_multi_dot(V + j0 * ldv, ldv, k + 1 - j0, w, N, s->d_c + j0, s->d_partc, np, st));
+      VB_TRY(vec_multi_dot(V + j0 * ldv, ldv, k + 1 - j0, w, N, s->d_c + j0, s->d_partc, np, st, s->d_cnt));
       VB_TRY(vec_multi_axpy(V + j0 * ldv, ldv, k + 1 - j0, s->d_c + j0, -1.0, w, N, st));
     } else {
-      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st));
+      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st, s->d_cnt));
       VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
     }
-    VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st));
-    VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st));
+    VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
+    VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st, s->d_cnt + 32));
 
     VB_TRY(tridiag_expm(s->d_c, s->d_c2, s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     {
@@ -879,8 +880,10 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
     A2((void **)&s->d_u, 128 * sizeof(cd));
     A2((void **)&s->d_partc, (size_t)512 * 128 * sizeof(cd));
     A2((void **)&s->d_tcerr, 256);
+    A2((void **)&s->d_cnt, 64 * sizeof(unsigned int));
     if (e != VB_OK) return fail_free(e);
-    if (cudaMemsetAsync(s->d_tcerr, 0, sizeof(int), s->st) != cudaSuccess) {
+    if (cudaMemsetAsync(s->d_tcerr, 0, sizeof(int), s->st) != cudaSuccess ||
+        cudaMemsetAsync(s->d_cnt, 0, 64 * sizeof(unsigned int), s->st) != cudaSuccess) {
       cudaGetLastError();
       return fail_free(fail(VB_ECUDA, "mps: memset failed"));
     }
