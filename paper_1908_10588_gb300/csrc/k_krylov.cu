@@ -299,6 +299,31 @@ __device__ __forceinline__ void tri_matvec(const double *d, const double *bl, co
   w[1] = mkc(d[1] * v[1].x + bl[1] * u1x + br[1] * d1x, d[1] * v[1].y + bl[1] * u1y + br[1] * d1y);
 }
 
+// real vectors (ns row slots in use)
+__device__ __forceinline__ void tri_matvec_r(int ns, const double *d, const double *bl, const double *br,
+                                             const double *v, double *w, int lane) {
+  double u0 = __shfl_up_sync(0xffffffffu, v[0], 1), dn0 = __shfl_down_sync(0xffffffffu, v[0], 1);
+  if (ns == 1) {
+    if (lane == 0) u0 = 0.0;
+    if (lane == 31) dn0 = 0.0;
+    w[0] = d[0] * v[0] + bl[0] * u0 + br[0] * dn0;
+    w[1] = 0.0;
+    return;
+  }
+  double u1 = __shfl_up_sync(0xffffffffu, v[1], 1), dn1 = __shfl_down_sync(0xffffffffu, v[1], 1);
+  const double c0 = __shfl_sync(0xffffffffu, v[0], 31), c1 = __shfl_sync(0xffffffffu, v[1], 0);
+  if (lane == 0) {
+    u0 = 0.0;
+    u1 = c0;
+  }
+  if (lane == 31) {
+    dn0 = c1;
+    dn1 = 0.0;
+  }
+  w[0] = d[0] * v[0] + bl[0] * u0 + br[0] * dn0;
+  w[1] = d[1] * v[1] + bl[1] * u1 + br[1] * dn1;
+}
+
 // one-slot form (kdim <= 32)
 __device__ __forceinline__ void tri_matvec1(double d, double bl, double br, cd v, cd &w, int lane) {
   double ux = __shfl_up_sync(0xffffffffu, v.x, 1), uy = __shfl_up_sync(0xffffffffu, v.y, 1);
@@ -384,7 +409,35 @@ __global__ void tridiag_expm_kernel(const cd *c, const cd *c2, double *alpha, co
   sincos(-mu * ts, &ps, &pc);
   cd x[2] = {mkc(lane == 0 ? 1.0 : 0.0, 0.0), mkc(0.0, 0.0)};
   const int ns = kdim > 32 ? 2 : 1;  // row slots in use
-  for (int st = 0; st < steps; ++st) {
+  if (steps == 1) {
+    // from e_1 every T_n(H) e_1 is real and every coefficient is real or
+    // imaginary, so one real recurrence and one real update per term
+    double r0[2] = {lane == 0 ? 1.0 : 0.0, 0.0}, r1[2], r2[2];
+    double ar[2], ai[2];
+    tri_matvec_r(ns, d, bl, br, r0, r1, lane);
+    for (int sl = 0; sl < 2; ++sl) {
+      ar[sl] = jn[0] * r0[sl];
+      ai[sl] = 2.0 * jn[1] * sg * r1[sl];
+    }
+    for (int n = 2; n <= nu; ++n) {
+      tri_matvec_r(ns, d, bl, br, r1, r2, lane);
+      const double cj = 2.0 * jn[n];
+      const int m = n & 3;
+      const double cr = m == 0 ? cj : (m == 2 ? -cj : 0.0);
+      const double ci = m == 1 ? cj * sg : (m == 3 ? -cj * sg : 0.0);
+      for (int sl = 0; sl < ns; ++sl) {
+        r2[sl] = 2.0 * r2[sl] - r0[sl];
+        if (m & 1)
+          ai[sl] = fma(ci, r2[sl], ai[sl]);
+        else
+          ar[sl] = fma(cr, r2[sl], ar[sl]);
+        r0[sl] = r1[sl];
+        r1[sl] = r2[sl];
+      }
+    }
+    for (int sl = 0; sl < 2; ++sl) x[sl] = mkc(pc * ar[sl] - ps * ai[sl], pc * ai[sl] + ps * ar[sl]);
+  }
+  for (int st = 0; st < (steps == 1 ? 0 : steps); ++st) {
     cd v0[2] = {x[0], x[1]}, v1[2], acc[2];
     if (ns == 2)
       tri_matvec(d, bl, br, v0, v1, lane);
