@@ -148,6 +148,33 @@ vb_status tdvp2_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdv
  * Needs the electronic site at chain position 0 and the center there. */
 vb_status measure_populations(const vb_mps *mps, double *pop_host /* [n_el] */);
 
+/* Overlap <a|b> of two states on the same chain (same site dimensions), in
+ * any gauge: the transfer matrices are contracted site by site in complex
+ * FP64 on a's stream (b's stream is synchronised first). out_host[0], [1]
+ * receive the real and imaginary parts. With a = the initial state and b
+ * = the propagated one this is the autocorrelation function
+ * C(t) = <psi(0)|psi(t)> whose Fourier transform gives the spectra of
+ * Sec. 3.1 (Eq. autocorrelation). Temporaries (two m x m blocks and one
+ * m x d x m block) come from a's allocator. */
+vb_status mps_overlap(const vb_mps *a, const vb_mps *b, double *out_host /* [2] */);
+
+/* Energy <psi|H|psi> / <psi|psi> in eV, H the MPO the state was created for
+ * (Eq. vibronic Hamiltonian): left environments contracted over the whole
+ * chain in FP64. Two-site TDVP conserves it up to truncation (Sec. 2.1.2).
+ * Temporaries from the state's allocator. */
+vb_status mps_energy(const vb_mps *mps, double *out_host /* [1] */);
+
+/* One tdvp2_sweep for each of `count` independent instances (Sec. 2.1.2 per
+ * instance; a batch of models or parameters): one host thread per instance,
+ * so instances created on different CUDA streams run concurrently on the
+ * GPU; with the profiler on they run one after another. stats (nullable)
+ * receives one entry per instance. On failure the error of the first failing
+ * instance (in index order) is returned and its message is available from
+ * vb_last_error(); the other instances have completed their sweep. An
+ * instance may not appear twice. */
+vb_status tdvp2_sweep_batched(vb_mps *const *mps, const vb_mpo *const *mpo, int count, double dt_fs,
+                              const vb_tdvp_opts *opts, vb_sweep_stats *stats /* [count], nullable */);
+
 /* ---- single operations on caller-owned device buffers (complex double).
  * These run the same kernels as tdvp2_sweep; `stream` is a cudaStream_t. */
 

@@ -25,7 +25,8 @@ EXPORTED = [
     "mps_bond_dims", "mps_get_site", "tdvp2_sweep", "measure_populations", "vb_heff2_apply",
     "vb_heff1_apply", "vb_heff_work_elems", "vb_env_left_update", "vb_env_right_update",
     "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
-    "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc",
+    "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc", "mps_overlap", "mps_energy",
+    "tdvp2_sweep_batched",
 ]
 
 
@@ -100,6 +101,10 @@ def lib():
         "mps_get_site": (i, [vp, i, vp]),
         "tdvp2_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
         "measure_populations": (i, [vp, vp]),
+        "mps_overlap": (i, [vp, vp, vp]),
+        "mps_energy": (i, [vp, vp]),
+        "tdvp2_sweep_batched": (i, [C.POINTER(vp), C.POINTER(vp), i, d, C.POINTER(vb_tdvp_opts),
+                                    C.POINTER(vb_sweep_stats)]),
         "vb_heff2_apply": (i, [vp, i, i, i, vp, vp, vp, vp, vp, i, vp]),
         "vb_heff1_apply": (i, [vp, i, i, i, vp, vp, vp, vp, vp, i, vp]),
         "vb_heff_work_elems": (sz, [vp, i, i, i, i]),
@@ -283,6 +288,32 @@ class Mps:
         check(lib().measure_populations(self.h, out.ctypes.data))
         return out
 
+    def overlap(self, other: "Mps") -> complex:
+        """<self|other> (mps_overlap); with self the initial state this is C(t)."""
+        out = np.zeros(2)
+        check(lib().mps_overlap(self.h, other.h, out.ctypes.data))
+        return complex(out[0], out[1])
+
+    def energy(self) -> float:
+        """<psi|H|psi> / <psi|psi> in eV (mps_energy)."""
+        out = np.zeros(1)
+        check(lib().mps_energy(self.h, out.ctypes.data))
+        return float(out[0])
+
+    def save(self, path: str):
+        """Checkpoint: bond dimensions and site tensors (host copies) to an .npz
+        file; `Mps.load` recreates the handle from it."""
+        ts = self.tensors()
+        np.savez(path, n_sites=len(ts), **{f"site{p}": t for p, t in enumerate(ts)})
+
+    @classmethod
+    def load(cls, mpo: Mpo, path: str, **kw) -> "Mps":
+        """Handle from a checkpoint written by `save` (same MPO; options as for
+        the constructor: m_cap, dtype, krylov_cap, stream)."""
+        with np.load(path) as z:
+            ts = [z[f"site{p}"] for p in range(int(z["n_sites"]))]
+        return cls(mpo, tensors=ts, **kw)
+
     def close(self):
         if self.h:
             lib().mps_destroy(self.h)
@@ -293,6 +324,19 @@ class Mps:
             self.close()
         except Exception:
             pass
+
+
+def sweep_batched(states, dt_fs: float, m_max: int, eps: float = 0.0, zero_floor: float = 1e-14,
+                  krylov_max: int = 30, krylov_tol: float = 1e-13, on_noconv: int = 0):
+    """One 2TDVP step for each state (tdvp2_sweep_batched); states created on
+    different streams run concurrently. Returns the per-state statistics."""
+    n = len(states)
+    hs = (C.c_void_p * max(1, n))(*[s.h for s in states])
+    ms = (C.c_void_p * max(1, n))(*[s.mpo.h for s in states])
+    o = vb_tdvp_opts(m_max, eps, zero_floor, krylov_max, krylov_tol, on_noconv)
+    st = (vb_sweep_stats * max(1, n))()
+    check(lib().tdvp2_sweep_batched(hs, ms, n, float(dt_fs), C.byref(o), st))
+    return [st[i] for i in range(n)]
 
 
 # ------------------------------------------- single operations (device ptrs)

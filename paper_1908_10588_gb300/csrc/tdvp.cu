@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <thread>
+
 #include "common.h"
 
 using namespace vb;
@@ -957,6 +959,86 @@ vb_status build_right_envs(vb_mps *s) {
   return VB_OK;
 }
 
+// ---- observables of whole states
+
+// temporaries of one observable call, from the handle's allocator
+struct Scratch {
+  vb::Alloc *al;
+  std::vector<void *> held;
+  explicit Scratch(vb::Alloc *a) : al(a) {}
+  vb_status get(void **p, size_t bytes) {
+    VB_TRY(al->get(p, std::max<size_t>(bytes, 256)));
+    held.push_back(*p);
+    return VB_OK;
+  }
+  ~Scratch() {
+    for (void *p : held) al->put(p);
+  }
+};
+
+// <a|b> = contraction of the transfer matrices E_p[y', y] =
+// sum_{x, x', s} conj(A_p[x', s, y']) E_{p-1}[x', x] B_p[x, s, y], E_0 = 1
+// (two complex FP64 GEMMs per site), on a's stream; result left on the device
+vb_status overlap_dev(const vb_mps *a, const vb_mps *b, Scratch &sc, cd **res) {
+  const int n = a->n;
+  long long e_cap = 1, x_cap = 1;
+  for (int p = 0; p <= n; ++p) e_cap = std::max<long long>(e_cap, (long long)a->bond[p] * b->bond[p]);
+  for (int p = 0; p < n; ++p)
+    x_cap = std::max<long long>(x_cap, (long long)a->bond[p] * a->dims[p] * b->bond[p + 1]);
+  cd *E0 = nullptr, *E1 = nullptr, *X = nullptr;
+  VB_TRY(sc.get((void **)&E0, e_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&E1, e_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&X, x_cap * sizeof(cd)));
+  const cd one = mkc(1.0, 0.0);
+  VB_TRY_CUDA(cudaMemcpyAsync(E0, &one, sizeof(cd), cudaMemcpyHostToDevice, a->st));
+  for (int p = 0; p < n; ++p) {
+    const int xa = a->bond[p], ya = a->bond[p + 1], xb = b->bond[p], yb = b->bond[p + 1], d = a->dims[p];
+    GemmArgs g{};  // X[x', (s y)] = E[x', x] B[x, (s y)]
+    g.M = xa; g.N = d * yb; g.K = xb; g.batch = 1;
+    g.opA = OP_N; g.opB = OP_N;
+    g.A = E0; g.lda = xb; g.B = b->A[p]; g.ldb = (long long)d * yb; g.C = X; g.ldc = (long long)d * yb;
+    g.alpha = one; g.beta = mkc(0.0, 0.0);
+    g.a_size = (long long)xa * xb; g.b_size = (long long)xb * d * yb; g.c_size = x_cap;
+    VB_TRY(zgemm(g, a->st));
+    GemmArgs h{};  // E'[y', y] = sum_{(x' s)} conj(A[(x' s), y']) X[(x' s), y]
+    h.M = ya; h.N = yb; h.K = xa * d; h.batch = 1;
+    h.opA = OP_C; h.opB = OP_N;
+    h.A = a->A[p]; h.lda = ya; h.B = X; h.ldb = yb; h.C = E1; h.ldc = yb;
+    h.alpha = one; h.beta = mkc(0.0, 0.0);
+    h.a_size = (long long)xa * d * ya; h.b_size = x_cap; h.c_size = e_cap;
+    VB_TRY(zgemm(h, a->st));
+    std::swap(E0, E1);
+  }
+  *res = E0;
+  return VB_OK;
+}
+
+// <psi|H|psi> through the left environments of the whole chain, FP64
+vb_status energy_dev(const vb_mps *s, Scratch &sc, cd **res) {
+  const vb_mpo *mpo = s->mpo;
+  const int n = s->n;
+  long long e_cap = 1, t_cap = 1;
+  for (int p = 0; p < n; ++p) {
+    const MpoSite &S = mpo->sites[p];
+    const long long mL = s->bond[p], mR = s->bond[p + 1];
+    e_cap = std::max(e_cap, std::max(mL * S.wl * mL, mR * S.wr * mR));
+    t_cap = std::max(t_cap, std::max(mL * S.wl * S.d * mR, mL * S.d * S.wr * mR));
+  }
+  cd *E0 = nullptr, *E1 = nullptr, *T1 = nullptr, *T2 = nullptr;
+  VB_TRY(sc.get((void **)&E0, e_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&E1, e_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&T1, t_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&T2, t_cap * sizeof(cd)));
+  const cd one = mkc(1.0, 0.0);
+  VB_TRY_CUDA(cudaMemcpyAsync(E0, &one, sizeof(cd), cudaMemcpyHostToDevice, s->st));
+  for (int p = 0; p < n; ++p) {
+    VB_TRY(env_left<double>(mpo, p, s->bond[p], s->bond[p + 1], E0, s->A[p], E1, T1, T2, t_cap, s->st));
+    std::swap(E0, E1);
+  }
+  *res = E0;
+  return VB_OK;
+}
+
 }  // namespace
 }  // namespace vb
 
@@ -1149,6 +1231,80 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
   }
   for (int b = 1; b < n; ++b) st.max_bond = std::max(st.max_bond, s->bond[b]);
   if (stats) *stats = st;
+  return VB_OK;
+}
+
+vb_status mps_overlap(const vb_mps *a, const vb_mps *b, double *out_host) {
+  if (!a || !b || !out_host) return fail(VB_EINVAL, "mps_overlap: null argument");
+  if (a->n != b->n || a->dims != b->dims) return fail(VB_EINVAL, "mps_overlap: states on different chains");
+  if (a->device != b->device) return fail(VB_EINVAL, "mps_overlap: states on different devices");
+  VB_TRY(set_device_of(const_cast<vb_mps *>(a)));
+  if (b->st != a->st) VB_TRY_CUDA(cudaStreamSynchronize(b->st));
+  vb::Alloc al = a->alloc;
+  cd *res = nullptr;
+  cd h = mkc(0.0, 0.0);
+  {
+    Scratch sc(&al);
+    VB_TRY(overlap_dev(a, b, sc, &res));
+    VB_TRY_CUDA(cudaMemcpyAsync(&h, res, sizeof(cd), cudaMemcpyDeviceToHost, a->st));
+    VB_TRY_CUDA(cudaStreamSynchronize(a->st));
+  }
+  out_host[0] = h.x;
+  out_host[1] = h.y;
+  return VB_OK;
+}
+
+vb_status mps_energy(const vb_mps *s, double *out_host) {
+  if (!s || !out_host) return fail(VB_EINVAL, "mps_energy: null argument");
+  VB_TRY(set_device_of(const_cast<vb_mps *>(s)));
+  vb::Alloc al = s->alloc;
+  cd e = mkc(0.0, 0.0), nn = mkc(0.0, 0.0);
+  {
+    Scratch sc(&al);
+    cd *re = nullptr, *rn = nullptr;
+    VB_TRY(energy_dev(s, sc, &re));
+    VB_TRY(overlap_dev(s, s, sc, &rn));
+    VB_TRY_CUDA(cudaMemcpyAsync(&e, re, sizeof(cd), cudaMemcpyDeviceToHost, s->st));
+    VB_TRY_CUDA(cudaMemcpyAsync(&nn, rn, sizeof(cd), cudaMemcpyDeviceToHost, s->st));
+    VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  }
+  if (!(nn.x > 0.0)) return fail(VB_ESTATE, "mps_energy: zero norm");
+  out_host[0] = e.x / nn.x;
+  return VB_OK;
+}
+
+vb_status tdvp2_sweep_batched(vb_mps *const *mps, const vb_mpo *const *mpo, int count, double dt_fs,
+                              const vb_tdvp_opts *opts, vb_sweep_stats *stats) {
+  if (count < 0 || (count > 0 && (!mps || !mpo || !opts))) return fail(VB_EINVAL, "tdvp2_sweep_batched: bad argument");
+  for (int i = 0; i < count; ++i)
+    if (!mps[i] || !mpo[i]) return fail(VB_EINVAL, "tdvp2_sweep_batched: null instance");
+  for (int i = 0; i < count; ++i)
+    for (int j = i + 1; j < count; ++j)
+      if (mps[i] == mps[j]) return fail(VB_EINVAL, "tdvp2_sweep_batched: an instance appears twice");
+  // one host thread per instance: each instance's Lanczos loop waits on its
+  // own stream, so instances on different streams overlap on the GPU. With
+  // the profiler on (not thread-safe) the instances run one after another.
+  std::vector<vb_status> rc(count, VB_OK);
+  std::vector<std::string> msg(count);
+  auto run = [&](int i) {
+    vb_sweep_stats st{};
+    rc[i] = tdvp2_sweep(mps[i], mpo[i], dt_fs, opts, &st);
+    if (rc[i] != VB_OK) msg[i] = vb_last_error();
+    if (stats) stats[i] = st;
+  };
+  if (prof_on() || count <= 1) {
+    for (int i = 0; i < count; ++i) run(i);
+  } else {
+    std::vector<std::thread> th;
+    th.reserve(count);
+    for (int i = 0; i < count; ++i) th.emplace_back(run, i);
+    for (auto &x : th) x.join();
+  }
+  for (int i = 0; i < count; ++i)
+    if (rc[i] != VB_OK) {
+      vb::set_error("tdvp2_sweep_batched: instance " + std::to_string(i) + ": " + msg[i]);
+      return rc[i];
+    }
   return VB_OK;
 }
 
