@@ -145,6 +145,14 @@ def heff1_apply(L, W, R, C):
     return np.einsum("yvb,xqvb->xqy", R, T2, optimize=True)
 
 
+def heff0_apply(L, R, X):
+    """y = H_eff,0 X for the bond matrix between two sites (zero-site
+    Hamiltonian of the one-site TDVP, Sec. 2.1.2):
+    y[a', b'] = sum L[a', w, a] R[b', w, b] X[a, b]."""
+    T = np.einsum("xwa,ab->xwb", L, X, optimize=True)
+    return np.einsum("ywb,xwb->xy", R, T, optimize=True)
+
+
 # ------------------------------------------------------ Krylov exponential
 def krylov_expm(apply, theta, dt_fs, kmax=30, tol=1e-13):
     """exp(-i H dt/hbar) theta from the Krylov space of Eq. Krylov subspace.
@@ -322,6 +330,79 @@ class Tdvp2:
                 L0, W0, R0 = L[i], W[i], R[i + 1]
                 C = self._evolve(lambda x: heff1_apply(L0, W0, R0, x), C, -tau, st)
             A[i] = C
+        self.mps.center = 0
+        st.max_bond = max(self.mps.bond_dims()) if n > 1 else 1
+        self.time += dt_fs
+        return st
+
+
+class Tdvp1:
+    """One-site TDVP (Sec. 2.1.2, the one-site variant) at the fixed bond
+    dimensions of the initial state. One time step = left-to-right half sweep
+    with tau = dt/2, then right-to-left with tau = dt/2 (as for 2TDVP):
+      left to right, site i: C_i <- exp(-i H_eff,1 tau) C_i; unless i is the
+      last site: C_i = A_i R (QR), grow L, R <- exp(+i H_eff,0 tau) R,
+      C_{i+1} = R B_{i+1};
+      right to left, mirrored with C_i = R Q (QR of C_i^+), grow R,
+      R <- exp(+i H_eff,0 tau) R, C_{i-1} = A_{i-1} R.
+    The last site is evolved twice in a row at the turn (once per half)."""
+
+    def __init__(self, mps: MPS, W, opts: TdvpOptions | None = None):
+        assert mps.center == 0
+        self.mps = mps
+        self.W = [np.asarray(w, dtype=np.complex128) for w in W]
+        self.opts = opts or TdvpOptions()
+        n = mps.n
+        one = np.ones((1, 1, 1), dtype=np.complex128)
+        self.L = [None] * (n + 1)
+        self.R = [None] * (n + 1)
+        self.L[0] = one
+        self.R[n] = one
+        for p in range(n - 1, 0, -1):
+            self.R[p] = env_right_update(self.R[p + 1], self.mps.A[p], self.W[p])
+        self.time = 0.0
+
+    def _evolve(self, apply, x, dt, st: StepStats):
+        y, it, conv = krylov_expm(apply, x, dt, self.opts.krylov_max, self.opts.krylov_tol)
+        st.krylov_iters.append(it)
+        st.krylov_max_iters = max(st.krylov_max_iters, it)
+        if not conv:
+            st.noconv += 1
+        return y
+
+    def step(self, dt_fs: float) -> StepStats:
+        st = StepStats()
+        A, W, L, R = self.mps.A, self.W, self.L, self.R
+        n = self.mps.n
+        tau = 0.5 * dt_fs
+        # left to right
+        for i in range(n):
+            Li, Wi, Ri = L[i], W[i], R[i + 1]
+            C = self._evolve(lambda x: heff1_apply(Li, Wi, Ri, x), A[i], tau, st)
+            if i == n - 1:
+                A[i] = C
+                break
+            mL, d, mR = C.shape
+            Q, Rm = np.linalg.qr(C.reshape(mL * d, mR))
+            A[i] = Q.reshape(mL, d, mR)
+            L[i + 1] = env_left_update(L[i], A[i], W[i])
+            L1, R1 = L[i + 1], R[i + 1]
+            Rm = self._evolve(lambda x: heff0_apply(L1, R1, x), Rm, -tau, st)
+            A[i + 1] = np.einsum("ab,bsc->asc", Rm, A[i + 1])
+        # right to left
+        for i in range(n - 1, -1, -1):
+            Li, Wi, Ri = L[i], W[i], R[i + 1]
+            C = self._evolve(lambda x: heff1_apply(Li, Wi, Ri, x), A[i], tau, st)
+            if i == 0:
+                A[0] = C
+                break
+            mL, d, mR = C.shape
+            Qh, Rh = np.linalg.qr(C.reshape(mL, d * mR).conj().T)  # C = Rh^+ Qh^+
+            A[i] = Qh.conj().T.reshape(mL, d, mR)
+            R[i] = env_right_update(R[i + 1], A[i], W[i])
+            L0, R0 = L[i], R[i]
+            Rm = self._evolve(lambda x: heff0_apply(L0, R0, x), Rh.conj().T, -tau, st)
+            A[i - 1] = np.einsum("asb,bc->asc", A[i - 1], Rm)
         self.mps.center = 0
         st.max_bond = max(self.mps.bond_dims()) if n > 1 else 1
         self.time += dt_fs

@@ -105,3 +105,78 @@ def test_capped_run_populations_physical_and_bonds_bounded():
         assert abs(p.sum() - 1.0) < 1e-12 and np.all(p >= -1e-15)
         assert st.max_bond <= 8 and st.noconv == 0
     assert max(sim.mps.bond_dims()) >= 4
+
+
+# ---- one-site TDVP (Sec. 2.1.2, the one-site variant)
+def test_full_bond_1tdvp_is_exact():
+    # at full bond dimensions the tangent-space projector is the identity and
+    # the one-site projector-splitting step reproduces exact propagation
+    import scipy.sparse.linalg as sla
+    m = vm.model_small_2state(n_modes=3, levels=4)
+    dims = vm.local_dims(m)
+    ts = vm.random_right_canonical_mps(5, dims, 64)
+    W = mpo.build_mpo(m)
+    st = tdvp.Tdvp1(tdvp.MPS(ts), W)
+    v = tdvp.to_vector(tdvp.MPS(ts))
+    H = vibronic.hamiltonian_sparse(m)
+    for _ in range(6):
+        st.step(0.5)
+        v = sla.expm_multiply(-1j * H * (0.5 / vm.HBAR_EV_FS), v)
+        assert np.max(np.abs(tdvp.to_vector(st.mps) - v)) < 1e-9
+    assert st.mps.bond_dims() == [2, 8, 4]
+
+
+def test_1tdvp_conserves_norm_and_energy_at_reduced_bonds():
+    # fixed bond dimensions below full: the state leaves the exact
+    # trajectory, but 1TDVP conserves norm and energy (no truncation)
+    m = vm.model_small_2state(n_modes=4, levels=6)
+    dims = vm.local_dims(m)
+    ts = vm.random_right_canonical_mps(6, dims, 5)
+    W = mpo.build_mpo(m)
+    st = tdvp.Tdvp1(tdvp.MPS(ts), W)
+    e0, n0 = tdvp.energy(st.mps, W), tdvp.overlap(st.mps, st.mps)
+    v = tdvp.to_vector(tdvp.MPS(ts))
+    H = vibronic.hamiltonian_sparse(m)
+    import scipy.sparse.linalg as sla
+    for _ in range(6):
+        st.step(0.5)
+        v = sla.expm_multiply(-1j * H * (0.5 / vm.HBAR_EV_FS), v)
+        assert abs(tdvp.energy(st.mps, W) - e0) < 1e-10 * max(1.0, abs(e0))
+        assert abs(tdvp.overlap(st.mps, st.mps) - n0) < 1e-12
+    assert st.mps.bond_dims() == [2, 5, 5, 5]
+    # and the projection error is real at these bonds
+    assert np.max(np.abs(tdvp.to_vector(st.mps) - v)) > 1e-6
+
+
+def test_heff0_is_the_bond_projection_of_h():
+    # <X'|H_eff,0|X> equals <psi(X')|H|psi(X)> for states that share the
+    # orthonormal tensors left and right of the bond
+    m = vm.model_small_2state(n_modes=3, levels=3)
+    dims = vm.local_dims(m)
+    ts = vm.random_right_canonical_mps(9, dims, 64)
+    W = mpo.build_mpo(m)
+    H = vibronic.hamiltonian_sparse(m).toarray()
+    rng = np.random.default_rng(3)
+    # left-orthonormal A_0, A_1 from QR, right-orthonormal B_2, B_3 as given
+    A = [np.array(t) for t in ts]
+    for i in range(2):
+        mL, d, mR = A[i].shape
+        Q, Rm = np.linalg.qr(A[i].reshape(mL * d, mR))
+        A[i] = Q.reshape(mL, d, mR)
+        A[i + 1] = np.einsum("ab,bsc->asc", Rm, A[i + 1])
+    mb = A[1].shape[2]
+    Lb = np.ones((1, 1, 1), dtype=np.complex128)
+    for i in range(2):
+        Lb = tdvp.env_left_update(Lb, A[i], W[i])
+    Rb = np.ones((1, 1, 1), dtype=np.complex128)
+    for i in range(3, 1, -1):
+        Rb = tdvp.env_right_update(Rb, A[i], W[i])
+    X = rng.standard_normal((mb, mb)) + 1j * rng.standard_normal((mb, mb))
+    Y = rng.standard_normal((mb, mb)) + 1j * rng.standard_normal((mb, mb))
+
+    def vec(Z):
+        B = [A[0], np.einsum("asb,bc->asc", A[1], Z), A[2], A[3]]
+        return tdvp.to_vector(tdvp.MPS(B))
+    lhs = np.vdot(Y, tdvp.heff0_apply(Lb, Rb, X))
+    rhs = np.vdot(vec(Y), H @ vec(X))
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs)
