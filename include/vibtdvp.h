@@ -144,6 +144,19 @@ vb_status mps_get_site(const vb_mps *mps, int site, double *host_out);
 vb_status tdvp2_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts,
                       vb_sweep_stats *stats /* nullable */);
 
+/* ---- one one-site TDVP time step (Sec. 2.1.2, the one-site variant) at
+ * the state's current bond dimensions (no truncation, no growth): left to
+ * right with dt/2, each site evolved by H_eff,1, split by a QR into an
+ * orthonormal site tensor and a bond matrix that is evolved backwards by the
+ * zero-site H_eff,0 and absorbed into the next site; then right to left with
+ * dt/2, mirrored (LQ). The QR/LQ are Cholesky QR done twice in FP64 (bond
+ * dimensions up to 112; columns that depend on earlier ones get orthonormal
+ * completions). Norm and energy are conserved up to the Krylov tolerance.
+ * m_max, eps and zero_floor of opts are not used. Works in both forms (H_eff,1
+ * as in tdvp2_sweep; H_eff,0, QR and LQ in FP64). */
+vb_status tdvp1_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts,
+                      vb_sweep_stats *stats /* nullable */);
+
 /* Electronic populations P_k = <psi| |k><k| |psi> / <psi|psi> (Sec. 3.1).
  * Needs the electronic site at chain position 0 and the center there. */
 vb_status measure_populations(const vb_mps *mps, double *pop_host /* [n_el] */);

@@ -26,7 +26,7 @@ EXPORTED = [
     "vb_heff1_apply", "vb_heff_work_elems", "vb_env_left_update", "vb_env_right_update",
     "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
     "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc", "mps_overlap", "mps_energy",
-    "tdvp2_sweep_batched",
+    "tdvp2_sweep_batched", "tdvp1_sweep",
 ]
 
 
@@ -101,6 +101,7 @@ def lib():
         "mps_get_site": (i, [vp, i, vp]),
         "tdvp2_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
         "measure_populations": (i, [vp, vp]),
+        "tdvp1_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
         "mps_overlap": (i, [vp, vp, vp]),
         "mps_energy": (i, [vp, vp]),
         "tdvp2_sweep_batched": (i, [C.POINTER(vp), C.POINTER(vp), i, d, C.POINTER(vb_tdvp_opts),
@@ -280,6 +281,13 @@ class Mps:
         o = vb_tdvp_opts(m_max, eps, zero_floor, krylov_max, krylov_tol, on_noconv)
         st = vb_sweep_stats()
         check(lib().tdvp2_sweep(self.h, self.mpo.h, float(dt_fs), C.byref(o), C.byref(st)))
+        return st
+
+    def sweep1(self, dt_fs: float, krylov_max: int = 30, krylov_tol: float = 1e-13, on_noconv: int = 0):
+        """One one-site TDVP step at the current bond dimensions (tdvp1_sweep)."""
+        o = vb_tdvp_opts(1, 0.0, 0.0, krylov_max, krylov_tol, on_noconv)
+        st = vb_sweep_stats()
+        check(lib().tdvp1_sweep(self.h, self.mpo.h, float(dt_fs), C.byref(o), C.byref(st)))
         return st
 
     def populations(self) -> np.ndarray:

@@ -228,6 +228,10 @@ vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned lon
 // Jacobi solver: evals descending, eigenvectors as rows W[k][n]; info[0] =
 // sweeps used. VB_EINVAL for larger n (use eig_values / eig_vectors)
 vb_status ritz_eig_small(const cf *S, int n, int k, float *evals, cf *W, int *info, cudaStream_t st);
+// FP64 Cholesky factor W (r x r, r <= 112) with W G W^+ = I on the accepted
+// rows of the Gram matrix G; rejected rows (scaled pivot <= 1e-28: zero rows
+// and exact dependencies) are zero in W with flag[i] = 1, flag[r] = their count
+vb_status chol_w64(const cd *G, int r, cd *W, int *flag, cudaStream_t st);
 // *out = sum |x_i|^2 accumulated in FP64
 vb_status norm2_sq_f32(const cf *x, long long n, double *out, double *partial, int n_part, cudaStream_t st);
 // out[0] = *capt, out[1] = *cnt

@@ -62,73 +62,76 @@ __global__ void fill_flagged_kernel(cf *__restrict__ Q, int r, int n, const int 
 // step needs a single barrier. The lower triangle holds the elimination,
 // the strictly upper triangle holds M transposed.
 constexpr int CHOL_THREADS = 1024;
-__global__ void __launch_bounds__(CHOL_THREADS) chol_rows_kernel(const cf *__restrict__ G, int r, float tau,
-                                                                 cf *__restrict__ W, int *__restrict__ flag) {
+template <class R>
+__global__ void __launch_bounds__(CHOL_THREADS) chol_rows_kernel(const cplx<R> *__restrict__ G, int r, R tau,
+                                                                 cplx<R> *__restrict__ W, int *__restrict__ flag) {
+  typedef cplx<R> C_;
   extern __shared__ __align__(16) unsigned char chol_smem[];
-  cf *S = reinterpret_cast<cf *>(chol_smem);
-  float *dsc = reinterpret_cast<float *>(S + (size_t)r * r);
-  float *piv = dsc + r;  // p_j, 0 for a rejected row
+  C_ *S = reinterpret_cast<C_ *>(chol_smem);
+  R *dsc = reinterpret_cast<R *>(S + (size_t)r * r);
+  R *piv = dsc + r;  // p_j, 0 for a rejected row
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const R zero = R(0), one = R(1);
   for (int i = tid; i < r; i += nt) {
-    const float g = G[(long long)i * r + i].x;
-    dsc[i] = g > 0.f ? 1.0f / sqrtf(g) : 0.f;
+    const R g = G[(long long)i * r + i].x;
+    dsc[i] = g > zero ? one / sqrt(g) : zero;
   }
   __syncthreads();
   for (int e = tid; e < r * r; e += nt) {
     const int i = e / r, j = e % r;
     if (j <= i) {
-      const cf g = G[e];
-      const float s = dsc[i] * dsc[j];
-      S[e] = mkc(g.x * s, g.y * s);
+      const C_ g = G[e];
+      const R s = dsc[i] * dsc[j];
+      S[e] = mkc<R>(g.x * s, g.y * s);
     }
   }
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    const float p = S[j * r + j].x;
+    const R p = S[j * r + j].x;
     const bool ok = p > tau;
-    const float inv = ok ? 1.0f / p : 0.f;
+    const R inv = ok ? one / p : zero;
     // warps take rows i > j, lanes the columns c <= i
     for (int i = j + 1 + wid; i < r; i += nw) {
-      const cf a = S[i * r + j];
-      const float lx = a.x * inv, ly = a.y * inv;
+      const C_ a = S[i * r + j];
+      const R lx = a.x * inv, ly = a.y * inv;
       for (int c = lane; c <= i; c += 32) {
         if (!ok) {
-          if (c == j) S[j * r + i] = mkc(0.f, 0.f);
+          if (c == j) S[j * r + i] = mkc<R>(zero, zero);
           continue;
         }
         if (c > j) {  // trailing update of the lower triangle
-          const cf b = S[c * r + j];
-          const cf cur = S[i * r + c];
-          S[i * r + c] = mkc(cur.x - (lx * b.x + ly * b.y), cur.y - (ly * b.x - lx * b.y));
+          const C_ b = S[c * r + j];
+          const C_ cur = S[i * r + c];
+          S[i * r + c] = mkc<R>(cur.x - (lx * b.x + ly * b.y), cur.y - (ly * b.x - lx * b.y));
         } else if (c < j) {  // M_ic -= l_ij M_jc
-          const cf mj = S[c * r + j];
-          const cf cur = S[c * r + i];
-          S[c * r + i] = mkc(cur.x - (lx * mj.x - ly * mj.y), cur.y - (lx * mj.y + ly * mj.x));
+          const C_ mj = S[c * r + j];
+          const C_ cur = S[c * r + i];
+          S[c * r + i] = mkc<R>(cur.x - (lx * mj.x - ly * mj.y), cur.y - (lx * mj.y + ly * mj.x));
         } else {  // M_ij = -l_ij
-          S[j * r + i] = mkc(-lx, -ly);
+          S[j * r + i] = mkc<R>(-lx, -ly);
         }
       }
     }
-    if (tid == 0) piv[j] = ok ? p : 0.f;
+    if (tid == 0) piv[j] = ok ? p : zero;
     __syncthreads();
   }
   for (int e = tid; e < r * r; e += nt) {
     const int i = e / r, c = e % r;
-    cf w = mkc(0.f, 0.f);
-    if (piv[i] > 0.f && c <= i) {
-      const cf mv = c == i ? mkc(1.f, 0.f) : S[c * r + i];
-      const float s = dsc[c] / sqrtf(piv[i]);
-      w = mkc(mv.x * s, mv.y * s);
+    C_ w = mkc<R>(zero, zero);
+    if (piv[i] > zero && c <= i) {
+      const C_ mv = c == i ? mkc<R>(one, zero) : S[c * r + i];
+      const R s = dsc[c] / sqrt(piv[i]);
+      w = mkc<R>(mv.x * s, mv.y * s);
     }
     W[e] = w;
   }
   if (tid == 0) {
     int cnt = 0;
-    for (int i = 0; i < r; ++i) cnt += piv[i] > 0.f ? 0 : 1;
+    for (int i = 0; i < r; ++i) cnt += piv[i] > zero ? 0 : 1;
     flag[r] = cnt;
   }
-  for (int i = tid; i < r; i += nt) flag[i] = piv[i] > 0.f ? 0 : 1;
+  for (int i = tid; i < r; i += nt) flag[i] = piv[i] > zero ? 0 : 1;
 }
 
 // One-CTA Jacobi eigensolver for the small Hermitian Rayleigh-Ritz matrix
@@ -340,7 +343,7 @@ static vb_status orth_pass(const cf *A, cf *T, int r, int n, const SubspaceWork 
   VB_TRY(gemm<float>(g, st));
   prof_end(PH_ORTHGEMM, st, 0.0);
   prof_begin(PH_CHOL, st);
-  chol_rows_kernel<<<1, CHOL_THREADS, subspace_chol_smem(r), st>>>(w.G, r, 1e-4f, w.W, w.flag);
+  chol_rows_kernel<float><<<1, CHOL_THREADS, subspace_chol_smem(r), st>>>(w.G, r, 1e-4f, w.W, w.flag);
   VB_CHECK_LAUNCH();
   prof_end(PH_CHOL, st, 0.0);
   GemmArgsF h{};
@@ -363,12 +366,38 @@ vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned lon
   int dev = 0;
   VB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !smem_set[dev]) {
-    VB_TRY_CUDA(cudaFuncSetAttribute(chol_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VB_TRY_CUDA(cudaFuncSetAttribute(chol_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)subspace_chol_smem(128)));
     smem_set[dev] = 1;
   }
   VB_TRY(orth_pass(Q, w.T, r, n, w, seed, st));
   VB_TRY(orth_pass(w.T, Q, r, n, w, seed ^ 0x5bd1e995ull, st));
+  return VB_OK;
+}
+
+// ---- FP64 Cholesky factor for the orthonormalisations of the one-site sweep
+// W (r x r) with W G W^+ = I on the accepted rows, from G (r x r, r <= 112):
+// the same row-scaled elimination in FP64; only rows without a resolvable
+// independent part (scaled pivot <= 1e-28, i.e. zero rows and exact
+// dependencies) are rejected (zero row in W, flag[i] = 1, flag[r] = count):
+// a row with any independent part keeps it, so that span(W A) contains every
+// row of A (the caller's second pass restores orthogonality)
+constexpr int CHOL64_MAX_R = 112;
+size_t chol64_smem(int r) { return (size_t)r * r * sizeof(cd) + 2 * (size_t)r * sizeof(double); }
+
+vb_status chol_w64(const cd *G, int r, cd *W, int *flag, cudaStream_t st) {
+  if (r < 1 || r > CHOL64_MAX_R) return fail(VB_EINVAL, "chol_w64: needs 1 <= r <= 112");
+  static int smem_set[64] = {0};
+  int dev = 0;
+  VB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "chol_w64: device ordinal out of range");
+  if (!smem_set[dev]) {
+    VB_TRY_CUDA(cudaFuncSetAttribute(chol_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)chol64_smem(CHOL64_MAX_R)));
+    smem_set[dev] = 1;
+  }
+  chol_rows_kernel<double><<<1, CHOL_THREADS, chol64_smem(r), st>>>(G, r, 1e-28, W, flag);
+  VB_CHECK_LAUNCH();
   return VB_OK;
 }
 

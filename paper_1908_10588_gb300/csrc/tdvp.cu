@@ -122,6 +122,26 @@ __global__ void ritz_gather_kernel(const cd *__restrict__ src, int len, const in
   }
 }
 
+// entries of the rows (cols == 0) or columns (cols == 1) flagged in flag[] of
+// an r x n (rows) or n x r (columns) row-major matrix get counter-based random
+// values (splitmix64 finaliser) in [-1, 1)
+__device__ __forceinline__ double urand64(unsigned long long seed, unsigned long long idx) {
+  unsigned long long z = seed + (idx + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+__global__ void fill_flagged64(cd *__restrict__ Q, int r, long long n, int cols, const int *__restrict__ flag,
+                               unsigned long long seed) {
+  const long long tot = (long long)r * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int j = cols ? (int)(e % r) : (int)(e / n);
+    if (flag[j]) Q[e] = mkc(urand64(seed, 2ull * e), urand64(seed, 2ull * e + 1));
+  }
+}
+
 // FP64 copy of the FP32 basis rows, conjugated when conj != 0
 __global__ void subspace_rows_c64(const cf *__restrict__ q, cd *__restrict__ out, long long n, int conj) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -193,6 +213,10 @@ struct vb_mps {
   double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
   int *d_tcerr = nullptr;                        // raised by a tensor-core kernel whose wait ran out
   unsigned int *d_cnt = nullptr;                 // zeroed block counters of the last-block reductions
+  // one-site sweep (allocated on its first use)
+  bool t1_ready = false;
+  cd *q_G = nullptr, *q_W = nullptr, *q_Q = nullptr, *q_Rm = nullptr;
+  int *q_flag = nullptr;
   // subspace iteration of the mixed split
   cf *subZ = nullptr, *subT = nullptr, *subG = nullptr, *subW = nullptr, *skws32 = nullptr;
   long long skws32_elems = 0;
@@ -343,7 +367,7 @@ vb_status env_right(const vb_mpo *mpo, int p, int mL, int mR, const cplx<Rt> *R,
 
 // ---- operator applied inside the Krylov loop
 struct HeffOp {
-  int two_site;
+  int two_site;  // 1: two-site, 0: one-site, -1: zero-site (bond between site and site + 1)
   int site;
   int mL, mR;
   const cd *L, *R;
@@ -370,7 +394,31 @@ double heff_flops(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
   return 8.0 * c * mL * S.wl + wsite_flops(S, (double)mL * mR) + 8.0 * c * S.wr * mR;
 }
 
+// ---- H_eff,0 X for the bond matrix X (m_a x m_b) between site and site + 1
+// (zero-site Hamiltonian of the one-site sweep): T[(a' w), b] = L[(a' w), a] X[a, b],
+// y[a', b'] = sum_{(w b)} T[a', (w b)] R[b', (w b)]; two complex FP64 GEMMs
+vb_status heff0_fp64(const vb_mpo *mpo, int site, int ma, int mb, const cd *L, const cd *R, const cd *x, cd *y,
+                     cd *T, long long t_cap, cudaStream_t st) {
+  const long long w = mpo->sites[site].wr;
+  GemmArgs g{};
+  g.M = (int)(ma * w); g.N = mb; g.K = ma; g.batch = 1;
+  g.opA = OP_N; g.opB = OP_N;
+  g.A = L; g.lda = ma; g.B = x; g.ldb = mb; g.C = T; g.ldc = mb;
+  g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
+  g.a_size = ma * w * ma; g.b_size = (long long)ma * mb; g.c_size = t_cap;
+  VB_TRY(zgemm(g, st));
+  GemmArgs h{};
+  h.M = ma; h.N = mb; h.K = (int)(w * mb); h.batch = 1;
+  h.opA = OP_N; h.opB = OP_T;
+  h.A = T; h.lda = w * mb; h.B = R; h.ldb = w * mb; h.C = y; h.ldc = mb;
+  h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
+  h.a_size = t_cap; h.b_size = (long long)mb * w * mb; h.c_size = (long long)ma * mb;
+  return zgemm(h, st);
+}
+
 vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
+  if (op.two_site < 0)  // zero-site (bond) Hamiltonian: FP64 in both forms
+    return heff0_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->inter_cap, s->st);
   const int ph = op.two_site ? PH_HEFF2 : PH_HEFF1;
   prof_begin(ph, s->st);
   vb_status r;
@@ -1039,6 +1087,72 @@ vb_status energy_dev(const vb_mps *s, Scratch &sc, cd **res) {
   return VB_OK;
 }
 
+// ---- orthonormalisations of the one-site sweep (Cholesky QR, twice, FP64)
+// QR of M (n1 x m, row-major): Q (n1 x m) with orthonormal columns, Rm = Q^+ M
+// (m x m), M = Q Rm. Columns that depend on earlier ones get random
+// orthonormal completions (their rows of Rm vanish).
+vb_status qr_cols(vb_mps *s, const cd *M, long long n1, int m, cd *Q, cd *Rm, unsigned long long seed) {
+  cudaStream_t st = s->st;
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  const long long nm = n1 * m, mm = (long long)m * m;
+  auto G = [&](int Mm, int Nn, int Kk, int opA, const cd *A, long long lda, long long asz, int opB, const cd *B,
+               long long ldb, long long bsz, cd *C, long long ldc, long long csz) {
+    GemmArgs g{};
+    g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    return zgemm(g, st);
+  };
+  VB_TRY(G(m, m, (int)n1, OP_C, M, m, nm, OP_N, M, m, nm, s->q_G, m, mm));  // G = M^+ M
+  VB_TRY(chol_w64(s->q_G, m, s->q_W, s->q_flag, st));
+  VB_TRY(G((int)n1, m, m, OP_N, M, m, nm, OP_C, s->q_W, m, mm, s->q_Q, m, nm));  // Q1 = M W^+
+  fill_flagged64<<<grid1(nm), 256, 0, st>>>(s->q_Q, m, n1, 1, s->q_flag, seed);
+  VB_CHECK_LAUNCH();
+  VB_TRY(G(m, m, (int)n1, OP_C, s->q_Q, m, nm, OP_N, s->q_Q, m, nm, s->q_G, m, mm));  // G2 = Q1^+ Q1
+  VB_TRY(chol_w64(s->q_G, m, s->q_W, s->q_flag, st));
+  VB_TRY(G((int)n1, m, m, OP_N, s->q_Q, m, nm, OP_C, s->q_W, m, mm, Q, m, nm));  // Q = Q1 W2^+
+  return G(m, m, (int)n1, OP_C, Q, m, nm, OP_N, M, m, nm, Rm, m, mm);  // Rm = Q^+ M
+}
+
+// LQ of C (m x n2): Q (m x n2) with orthonormal rows, Rm = C Q^+ (m x m), C = Rm Q
+vb_status lq_rows(vb_mps *s, const cd *Cm, int m, long long n2, cd *Q, cd *Rm, unsigned long long seed) {
+  cudaStream_t st = s->st;
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  const long long nm = n2 * m, mm = (long long)m * m;
+  auto G = [&](int Mm, int Nn, int Kk, int opA, const cd *A, long long lda, long long asz, int opB, const cd *B,
+               long long ldb, long long bsz, cd *C, long long ldc, long long csz) {
+    GemmArgs g{};
+    g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    return zgemm(g, st);
+  };
+  VB_TRY(G(m, m, (int)n2, OP_N, Cm, n2, nm, OP_C, Cm, n2, nm, s->q_G, m, mm));  // G = C C^+
+  VB_TRY(chol_w64(s->q_G, m, s->q_W, s->q_flag, st));
+  VB_TRY(G(m, (int)n2, m, OP_N, s->q_W, m, mm, OP_N, Cm, n2, nm, s->q_Q, n2, nm));  // Q1 = W C
+  fill_flagged64<<<grid1(nm), 256, 0, st>>>(s->q_Q, m, n2, 0, s->q_flag, seed);
+  VB_CHECK_LAUNCH();
+  VB_TRY(G(m, m, (int)n2, OP_N, s->q_Q, n2, nm, OP_C, s->q_Q, n2, nm, s->q_G, m, mm));  // G2 = Q1 Q1^+
+  VB_TRY(chol_w64(s->q_G, m, s->q_W, s->q_flag, st));
+  VB_TRY(G(m, (int)n2, m, OP_N, s->q_W, m, mm, OP_N, s->q_Q, n2, nm, Q, n2, nm));  // Q = W2 Q1
+  return G(m, m, (int)n2, OP_N, Cm, n2, nm, OP_C, Q, n2, nm, Rm, m, mm);  // Rm = C Q^+
+}
+
+vb_status tdvp1_setup(vb_mps *s) {
+  if (s->t1_ready) return VB_OK;
+  int mmax = 1;
+  for (int b : s->bcap) mmax = std::max(mmax, b);
+  if (mmax > 112) return fail(VB_EINVAL, "tdvp1_sweep: bond capacity above 112");
+  const size_t mm = (size_t)mmax * mmax;
+  VB_TRY(mps_alloc(s, (void **)&s->q_G, mm * sizeof(cd)));
+  VB_TRY(mps_alloc(s, (void **)&s->q_W, mm * sizeof(cd)));
+  VB_TRY(mps_alloc(s, (void **)&s->q_Rm, mm * sizeof(cd)));
+  VB_TRY(mps_alloc(s, (void **)&s->q_Q, (size_t)s->theta_cap * sizeof(cd)));
+  VB_TRY(mps_alloc(s, (void **)&s->q_flag, (size_t)(mmax + 2) * sizeof(int)));
+  s->t1_ready = true;
+  return VB_OK;
+}
+
 }  // namespace
 }  // namespace vb
 
@@ -1231,6 +1345,90 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
   }
   for (int b = 1; b < n; ++b) st.max_bond = std::max(st.max_bond, s->bond[b]);
   if (stats) *stats = st;
+  return VB_OK;
+}
+
+vb_status tdvp1_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *o, vb_sweep_stats *stats) {
+  if (!s || !mpo || !o) return fail(VB_EINVAL, "tdvp1_sweep: null argument");
+  if (mpo != s->mpo) return fail(VB_EINVAL, "tdvp1_sweep: MPS was created for another MPO");
+  if (s->center != 0) return fail(VB_ESTATE, "tdvp1_sweep: center is not on site 0");
+  if (o->krylov_max < 1 || o->krylov_max > s->kcap)
+    return fail(VB_EINVAL, "tdvp1_sweep: krylov_max outside 1..krylov_cap");
+  if (!(o->krylov_tol > 0)) return fail(VB_EINVAL, "tdvp1_sweep: krylov_tol must be > 0");
+  for (int b = 1; b < s->n; ++b)
+    if ((long long)s->bond[b] > (long long)s->bond[b - 1] * s->dims[b - 1] ||
+        (long long)s->bond[b] > (long long)s->dims[b] * s->bond[b + 1])
+      return fail(VB_ESTATE, "tdvp1_sweep: a bond dimension exceeds what its neighbours can carry");
+  VB_TRY(set_device_of(s));
+  VB_TRY(tdvp1_setup(s));
+  const int n = s->n;
+  const double tau = 0.5 * dt_fs;
+  cudaStream_t st = s->st;
+  vb_sweep_stats ss{};
+  auto evolve = [&](const HeffOp &op, cd *x, long long N, double dt) -> vb_status {
+    int it = 0, conv = 0;
+    VB_TRY(krylov_expm(s, op, x, N, dt, o->krylov_max, o->krylov_tol, &it, &conv));
+    ss.krylov_iters_max = std::max(ss.krylov_iters_max, it);
+    ss.krylov_iters_total += it;
+    if (!conv) {
+      ss.noconv++;
+      if (o->on_noconv) return fail(VB_ENOCONV, "Krylov exponential did not converge");
+    }
+    return VB_OK;
+  };
+  const unsigned long long seed = 0x6A09E667F3BCC909ull + 0x9E3779B97F4A7C15ull * (++s->split_calls);
+  // left to right: C_i forward, C_i = A_i Rm, Rm backward, C_{i+1} = Rm B_{i+1}
+  for (int i = 0; i < n; ++i) {
+    const int mL = s->bond[i], mR = s->bond[i + 1], d = s->dims[i];
+    HeffOp op1{0, i, mL, mR, s->L[i], s->R[i + 1]};
+    VB_TRY(evolve(op1, s->A[i], (long long)mL * d * mR, tau));
+    if (i == n - 1) break;
+    const long long n1 = (long long)mL * d;
+    VB_TRY(qr_cols(s, s->A[i], n1, mR, s->theta, s->q_Rm, seed + 2 * i));
+    VB_TRY_CUDA(cudaMemcpyAsync(s->A[i], s->theta, n1 * mR * sizeof(cd), cudaMemcpyDeviceToDevice, st));
+    prof_begin(PH_ENV, st);
+    VB_TRY(env_update(s, true, i, mL, mR, s->L[i], s->A[i], s->L[i + 1]));
+    prof_end(PH_ENV, st, 0.0);
+    HeffOp op0{-1, i, mR, mR, s->L[i + 1], s->R[i + 1]};
+    VB_TRY(evolve(op0, s->q_Rm, (long long)mR * mR, -tau));
+    // C_{i+1} = Rm B_{i+1}
+    const long long n2 = (long long)s->dims[i + 1] * s->bond[i + 2];
+    GemmArgs g{};
+    g.M = mR; g.N = (int)n2; g.K = mR; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = s->q_Rm; g.lda = mR; g.B = s->A[i + 1]; g.ldb = n2; g.C = s->theta; g.ldc = n2;
+    g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
+    g.a_size = (long long)mR * mR; g.b_size = mR * n2; g.c_size = s->theta_cap;
+    VB_TRY(zgemm(g, st));
+    VB_TRY_CUDA(cudaMemcpyAsync(s->A[i + 1], s->theta, mR * n2 * sizeof(cd), cudaMemcpyDeviceToDevice, st));
+  }
+  // right to left: C_i forward, C_i = Rm Q_i, Rm backward, C_{i-1} = A_{i-1} Rm
+  for (int i = n - 1; i >= 0; --i) {
+    const int mL = s->bond[i], mR = s->bond[i + 1], d = s->dims[i];
+    HeffOp op1{0, i, mL, mR, s->L[i], s->R[i + 1]};
+    VB_TRY(evolve(op1, s->A[i], (long long)mL * d * mR, tau));
+    if (i == 0) break;
+    const long long n2 = (long long)d * mR;
+    VB_TRY(lq_rows(s, s->A[i], mL, n2, s->theta, s->q_Rm, seed + 2 * i + 1));
+    VB_TRY_CUDA(cudaMemcpyAsync(s->A[i], s->theta, (long long)mL * n2 * sizeof(cd), cudaMemcpyDeviceToDevice, st));
+    prof_begin(PH_ENV, st);
+    VB_TRY(env_update(s, false, i, mL, mR, s->R[i + 1], s->A[i], s->R[i]));
+    prof_end(PH_ENV, st, 0.0);
+    HeffOp op0{-1, i - 1, mL, mL, s->L[i], s->R[i]};
+    VB_TRY(evolve(op0, s->q_Rm, (long long)mL * mL, -tau));
+    // C_{i-1} = A_{i-1} Rm
+    const long long n0 = (long long)s->bond[i - 1] * s->dims[i - 1];
+    GemmArgs g{};
+    g.M = (int)n0; g.N = mL; g.K = mL; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = s->A[i - 1]; g.lda = mL; g.B = s->q_Rm; g.ldb = mL; g.C = s->theta; g.ldc = mL;
+    g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
+    g.a_size = n0 * mL; g.b_size = (long long)mL * mL; g.c_size = s->theta_cap;
+    VB_TRY(zgemm(g, st));
+    VB_TRY_CUDA(cudaMemcpyAsync(s->A[i - 1], s->theta, n0 * mL * sizeof(cd), cudaMemcpyDeviceToDevice, st));
+  }
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  ss.max_bond = 1;
+  for (int b = 1; b < n; ++b) ss.max_bond = std::max(ss.max_bond, s->bond[b]);
+  if (stats) *stats = ss;
   return VB_OK;
 }
 
