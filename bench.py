@@ -266,6 +266,25 @@ def run_ours(args):
         m64.close()
         m32.close()
 
+    # ---- one-site TDVP (the next row of the scope) on the same state at the
+    # same fixed bonds: one warm-up and two timed steps, energy drift
+    tdvp1 = None
+    if not args.no_tdvp1:
+        m1 = P.Mps(mpo, m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=stream, tensors=tensors)
+        e0 = m1.energy()
+        m1.sweep1(DT_FS)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(2):
+            m1.sweep1(DT_FS)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        t1_ms = c0.elapsed_time(c1) / 2
+        tdvp1 = {"sweeps_per_s": 1e3 / t1_ms, "ms_per_step": t1_ms, "steps_timed": 2,
+                 "energy_drift_ev_after_3_steps": abs(m1.energy() - e0), "bond_dims": "fixed at the state's (<= 64)"}
+        m1.close()
+
     # ---- roofline of the H_eff products
     peaks, src = _peaks()
     h2 = prof["heff2"]
@@ -320,6 +339,8 @@ def run_ours(args):
     }
     if compare is not None:
         line["fp64_form"] = compare
+    if tdvp1 is not None:
+        line["tdvp1"] = tdvp1
     if rank == 0 and not args.no_cpu_baseline:
         v, pairs, el, _ = _oracle_sample(model, tensors, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -381,6 +402,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tdvp1", action="store_true")
     ap.add_argument("--kernel-case", default=None, choices=[None, "heff2"])
     args = ap.parse_args()
     if args.kernel_case:

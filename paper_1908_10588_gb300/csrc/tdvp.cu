@@ -215,7 +215,8 @@ struct vb_mps {
   unsigned int *d_cnt = nullptr;                 // zeroed block counters of the last-block reductions
   // one-site sweep (allocated on its first use)
   bool t1_ready = false;
-  cd *q_G = nullptr, *q_W = nullptr, *q_Q = nullptr, *q_Rm = nullptr;
+  cd *q_G = nullptr, *q_W = nullptr, *q_Q = nullptr, *q_Rm = nullptr, *q_ws = nullptr;
+  long long q_ws_elems = 0;
   int *q_flag = nullptr;
   // subspace iteration of the mixed split
   cf *subZ = nullptr, *subT = nullptr, *subG = nullptr, *subW = nullptr, *skws32 = nullptr;
@@ -398,7 +399,7 @@ double heff_flops(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
 // (zero-site Hamiltonian of the one-site sweep): T[(a' w), b] = L[(a' w), a] X[a, b],
 // y[a', b'] = sum_{(w b)} T[a', (w b)] R[b', (w b)]; two complex FP64 GEMMs
 vb_status heff0_fp64(const vb_mpo *mpo, int site, int ma, int mb, const cd *L, const cd *R, const cd *x, cd *y,
-                     cd *T, long long t_cap, cudaStream_t st) {
+                     cd *T, long long t_cap, cd *ws, long long ws_elems, cudaStream_t st) {
   const long long w = mpo->sites[site].wr;
   GemmArgs g{};
   g.M = (int)(ma * w); g.N = mb; g.K = ma; g.batch = 1;
@@ -413,12 +414,14 @@ vb_status heff0_fp64(const vb_mpo *mpo, int site, int ma, int mb, const cd *L, c
   h.A = T; h.lda = w * mb; h.B = R; h.ldb = w * mb; h.C = y; h.ldc = mb;
   h.alpha = mkc(1.0, 0.0); h.beta = mkc(0.0, 0.0);
   h.a_size = t_cap; h.b_size = (long long)mb * w * mb; h.c_size = (long long)ma * mb;
+  h.ws = ws; h.ws_elems = ws_elems;  // one output tile, K = w m: split-K
   return zgemm(h, st);
 }
 
 vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
   if (op.two_site < 0)  // zero-site (bond) Hamiltonian: FP64 in both forms
-    return heff0_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->inter_cap, s->st);
+    return heff0_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->inter_cap, s->q_ws, s->q_ws_elems,
+                      s->st);
   const int ph = op.two_site ? PH_HEFF2 : PH_HEFF1;
   prof_begin(ph, s->st);
   vb_status r;
@@ -1101,6 +1104,7 @@ vb_status qr_cols(vb_mps *s, const cd *M, long long n1, int m, cd *Q, cd *Rm, un
     g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
     g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    g.ws = s->q_ws; g.ws_elems = s->q_ws_elems;  // split-K for the m x m products with long K
     return zgemm(g, st);
   };
   VB_TRY(G(m, m, (int)n1, OP_C, M, m, nm, OP_N, M, m, nm, s->q_G, m, mm));  // G = M^+ M
@@ -1125,6 +1129,7 @@ vb_status lq_rows(vb_mps *s, const cd *Cm, int m, long long n2, cd *Q, cd *Rm, u
     g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
     g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    g.ws = s->q_ws; g.ws_elems = s->q_ws_elems;  // split-K for the m x m products with long K
     return zgemm(g, st);
   };
   VB_TRY(G(m, m, (int)n2, OP_N, Cm, n2, nm, OP_C, Cm, n2, nm, s->q_G, m, mm));  // G = C C^+
@@ -1149,6 +1154,9 @@ vb_status tdvp1_setup(vb_mps *s) {
   VB_TRY(mps_alloc(s, (void **)&s->q_Rm, mm * sizeof(cd)));
   VB_TRY(mps_alloc(s, (void **)&s->q_Q, (size_t)s->theta_cap * sizeof(cd)));
   VB_TRY(mps_alloc(s, (void **)&s->q_flag, (size_t)(mmax + 2) * sizeof(int)));
+  s->q_ws_elems = 320LL * 64 * 64;  // split-K chunks x one 64 x 64 tile (chunks <= 2 x 152 / tiles)
+  s->q_ws_elems = std::max<long long>(s->q_ws_elems, 320LL * mm);
+  VB_TRY(mps_alloc(s, (void **)&s->q_ws, (size_t)s->q_ws_elems * sizeof(cd)));
   s->t1_ready = true;
   return VB_OK;
 }
