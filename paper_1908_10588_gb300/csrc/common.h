@@ -243,8 +243,10 @@ vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, d
                               double *out, double *partial, cudaStream_t st, unsigned int *cnt = nullptr);
 vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int n_part,
                     cudaStream_t st);
-// x *= 1/ (*nrm)  (device scalar); keep (nullable): *keep = *nrm
-vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep = nullptr);
+// x *= 1/ (*nrm) (device scalar; a zero norm gives zero); keep (nullable):
+// *keep = *nrm; alpha_k (nullable): *alpha_k = Re *c + Re *c2
+vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep = nullptr,
+                        const cd *c = nullptr, const cd *c2 = nullptr, double *alpha_k = nullptr);
 // y = s * x with s = *num / *den (device scalars; den may be null -> 1)
 vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st);
 // combine: y = (*nrm) * sum_j u[j] V[j]

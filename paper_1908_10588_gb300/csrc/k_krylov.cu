@@ -223,9 +223,14 @@ __global__ void norm2_final(const double *__restrict__ partial, int n_part, doub
   if (threadIdx.x == 0) out[0] = sqrt(s);
 }
 
-__global__ void scale_inv_kernel(cd *x, long long n, const double *nrm, double *keep) {
-  double s = 1.0 / nrm[0];
-  if (keep && blockIdx.x == 0 && threadIdx.x == 0) keep[0] = nrm[0];
+__global__ void scale_inv_kernel(cd *x, long long n, const double *nrm, double *keep, const cd *c, const cd *c2,
+                                 double *alpha_k) {
+  // a zero norm (Lanczos breakdown, zero input) gives a zero vector
+  const double s = nrm[0] > 0.0 ? 1.0 / nrm[0] : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (keep) keep[0] = nrm[0];
+    if (alpha_k) alpha_k[0] = c[0].x + c2[0].x;
+  }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     cd a = x[i];
@@ -546,9 +551,10 @@ vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int 
   return VB_OK;
 }
 
-vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep) {
+vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep, const cd *c,
+                        const cd *c2, double *alpha_k) {
   if (n == 0) return VB_OK;
-  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm, keep);
+  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm, keep, c, c2, alpha_k);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

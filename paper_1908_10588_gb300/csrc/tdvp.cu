@@ -213,6 +213,7 @@ struct vb_mps {
   double *h_flag = nullptr, *d_flag = nullptr;  // mapped: [0] err, [1] beta_next
   int *d_tcerr = nullptr;                        // raised by a tensor-core kernel whose wait ran out
   unsigned int *d_cnt = nullptr;                 // zeroed block counters of the last-block reductions
+  std::vector<int> khint;                        // Krylov steps of the last call per operator
   // one-site sweep (allocated on its first use)
   bool t1_ready = false;
   cd *q_G = nullptr, *q_W = nullptr, *q_Q = nullptr, *q_Rm = nullptr, *q_ws = nullptr;
@@ -440,6 +441,13 @@ vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
 vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt_fs, int kmax,
                       double tol, int *iters, int *converged) {
   cudaStream_t st = s->st;
+  // convergence is checked (small exponential + host wait) from two steps
+  // before the count the previous call for the same operator needed; the
+  // steps before run without a host wait. Checking later only adds steps,
+  // which makes the result more accurate, never less.
+  const size_t hk = (size_t)(op.two_site + 1) * (s->n + 1) + op.site;
+  if (s->khint.size() < (size_t)3 * (s->n + 1)) s->khint.assign((size_t)3 * (s->n + 1), 0);
+  const int check_from = std::max(1, s->khint[hk] - 2);
   const int np = reduce_parts(N);
   const long long ldv = s->theta_cap;
   cd *V = s->V;
@@ -472,24 +480,30 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
     VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st, s->d_cnt + 32));
 
-    VB_TRY(tridiag_expm(s->d_c, s->d_c2, s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
+    const bool check = k + 1 >= check_from || k + 1 == kmax;
+    if (check)
+      VB_TRY(tridiag_expm(s->d_c, s->d_c2, s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     {
       const double nv1 = s->dtype == VB_MIXED ? (double)(k > 0 ? 2 : 1) : (double)(k + 1);
       prof_end(PH_KRYLOV, st, Nd * (16.0 * (nv1 + k + 1) + 4.0));
     }
-    VB_TRY_CUDA(cudaStreamSynchronize(st));
-    const double err = s->h_flag[0], b = s->h_flag[1];
     kdim = k + 1;
-    if (!(err == err) || !(b == b)) return fail(VB_ECUDA, "krylov: NaN in the Lanczos recurrence");
-    if (err < tol || b <= 1e-300 || k + 1 == N) {
-      *converged = 1;
-      break;
+    if (check) {
+      VB_TRY_CUDA(cudaStreamSynchronize(st));
+      const double err = s->h_flag[0], b = s->h_flag[1];
+      if (!(err == err) || !(b == b)) return fail(VB_ECUDA, "krylov: NaN in the Lanczos recurrence");
+      if (err < tol || b <= 1e-300 || k + 1 == N) {
+        *converged = 1;
+        break;
+      }
     }
     prof_begin(PH_KRYLOV, st);
-    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k));
+    // v_{k+1} = w / beta_{k+1}; also records beta_{k+1} and alpha_k
+    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k, s->d_c + k, s->d_c2 + k, s->d_alpha + k));
     prof_end(PH_KRYLOV, st, 2.0 * Nd);
   }
   *iters = kdim;
+  if (*converged) s->khint[hk] = kdim;
   prof_begin(PH_KRYLOV, st);
   VB_TRY(vec_combine(V, ldv, kdim, s->d_u, s->d_nrm, x, N, st));
   prof_end(PH_KRYLOV, st, 8.0 * Nd * kdim);
