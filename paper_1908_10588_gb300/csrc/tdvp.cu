@@ -227,11 +227,11 @@ struct vb_mps {
   float *ev32 = nullptr;
   void *eigw32 = nullptr;
   unsigned long long split_calls = 0;
-  // mixed split: FP32 eigenvectors of rho, FP64 Rayleigh-Ritz
+  // mixed split: FP32 subspace iteration and Ritz vectors, FP64 basis, projection and weights
   int rcap = 0;
   cf *M32 = nullptr, *Q32 = nullptr;
   cd *Q64 = nullptr, *Qo = nullptr, *G = nullptr, *X = nullptr;
-  cd *skws = nullptr;  // split-K workspace of the Rayleigh-Ritz products
+  cd *skws = nullptr;  // split-K workspace of the FP64 projection products
   long long skws_elems = 0;
   // mixed form: environment updates in complex FP32
   cf *envA32 = nullptr, *envE32 = nullptr, *envO32 = nullptr, *envT1 = nullptr, *envT2 = nullptr;
@@ -559,7 +559,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old,
   cudaStream_t st = s->st;
   const int n1 = mL * d1, n2 = d2 * mR;
   const int n = left ? n1 : n2;
-  // mixed form: FP32 eigenvectors + FP64 Rayleigh-Ritz once the matrix is
+  // mixed form: FP32 subspace iteration + FP64 projection once the matrix is
   // large enough for the FP64 reduction to matter
   if (s->dtype == VB_MIXED && n > MIXED_SPLIT_MIN_N && o.m_max + 1 + 8 <= s->rcap)
     return split_mixed(s, left, mL, d1, d2, mR, m_old, o, dstA, dstC, k_out, disc);
