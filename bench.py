@@ -12,7 +12,9 @@ ranks (each rank propagates its own replica: a single trajectory does not
 shard); `e2e` is the same metric through the C ABI with host buffers;
 `roofline` describes the H_eff products (the operation the metric names)
 measured live with CUDA events, `roofline_krylov` the FP64 Krylov vector
-work (the largest phase of the mixed form); `cpu_baseline` times the CPU oracle on a
+work (the largest phase of the mixed form); `site_order_search` times the
+same workload on the chain order the cost-model search picks (Sec. 3.1,
+ordering of local sites); `cpu_baseline` times the CPU oracle on a
 bounded sample of the same sweep. `--impl reference` times that oracle as
 the reference arm.
 """
@@ -285,6 +287,40 @@ def run_ours(args):
                  "energy_drift_ev_after_3_steps": abs(m1.energy() - e0), "bond_dims": "fixed at the state's (<= 64)"}
         m1.close()
 
+    # ---- site ordering (Sec. 3.1): the order the cost-model search picks for
+    # this model, timed from a random state at that order's saturated bonds
+    # (one warm-up and two timed steps), beside the default order above
+    order_line = None
+    if not args.no_order_search:
+        t0 = time.perf_counter()
+        order, cost = P.site_order_search(model, m_max=M_MAX)
+        search_s = time.perf_counter() - t0
+        cdef = P.site_order_cost(model, None, m_max=M_MAX)[0]
+        mo = dict(model, site_order=order)
+        mpo_o = P.Mpo(mo)
+        to = vm.random_right_canonical_mps(STATE_SEED + rank, vm.local_dims(mo), M_MAX)
+        mso = P.Mps(mpo_o, m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=stream, tensors=to)
+        mso.sweep(DT_FS, **sweep_kw)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        st_o = [mso.sweep(DT_FS, **sweep_kw) for _ in range(2)]
+        c1.record(stream)
+        torch.cuda.synchronize()
+        o_ms = c0.elapsed_time(c1) / 2
+        po = mso.populations()
+        order_line = {
+            "order": order, "search_s": round(search_s, 3),
+            "predicted_vs_default": {"heff_flops": cost["heff_flops"] / cdef["heff_flops"],
+                                     "tensor_elems": cost["tensor_elems"] / cdef["tensor_elems"],
+                                     "coupling_dist": cost["coupling_dist"] / cdef["coupling_dist"],
+                                     "max_mpo_bond": [cdef["max_w"], cost["max_w"]]},
+            "ms_per_step": o_ms, "steps_timed": 2, "speedup_vs_default_order": (ms / args.steps) / o_ms,
+            "krylov_iters_max": max(x.krylov_iters_max for x in st_o), "max_bond": max(mso.bond_dims()),
+            "populations": [float(x) for x in po],
+        }
+        mso.close()
+
     # ---- roofline of the H_eff products
     peaks, src = _peaks()
     h2 = prof["heff2"]
@@ -321,6 +357,7 @@ def run_ours(args):
         "dtype": "f64" if dtype == P.VB_FP64 else "tf32x3-f32acc/f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_sites": len(dims), "m_max": M_MAX, "eps": EPS, "dt_fs": DT_FS,
+                   "site_order": "electronic site first, modes by index",
                    "parallelism": f"replicas x{ws}",
                    "l2": "per-step working set (Krylov basis ~0.8 GB) exceeds L2"},
         "roofline": roof,
@@ -341,6 +378,8 @@ def run_ours(args):
         line["fp64_form"] = compare
     if tdvp1 is not None:
         line["tdvp1"] = tdvp1
+    if order_line is not None:
+        line["site_order_search"] = order_line
     if rank == 0 and not args.no_cpu_baseline:
         v, pairs, el, _ = _oracle_sample(model, tensors, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -403,6 +442,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tdvp1", action="store_true")
+    ap.add_argument("--no-order-search", action="store_true")
     ap.add_argument("--kernel-case", default=None, choices=[None, "heff2"])
     args = ap.parse_args()
     if args.kernel_case:

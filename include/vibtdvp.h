@@ -158,7 +158,11 @@ vb_status tdvp1_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdv
                       vb_sweep_stats *stats /* nullable */);
 
 /* Electronic populations P_k = <psi| |k><k| |psi> / <psi|psi> (Sec. 3.1).
- * Needs the electronic site at chain position 0 and the center there. */
+ * Needs the center on site 0 (where every sweep leaves it). The electronic
+ * site may sit anywhere on the chain: at position e > 0 the transfer matrix
+ * of sites 0 .. e-1 is contracted first (complex FP64, temporaries of
+ * m_e^2 + m_e d m_{e+1} elements and the transfer blocks from the state's
+ * allocator); the sites right of e are right-orthonormal and drop out. */
 vb_status measure_populations(const vb_mps *mps, double *pop_host /* [n_el] */);
 
 /* Overlap <a|b> of two states on the same chain (same site dimensions), in
@@ -187,6 +191,69 @@ vb_status mps_energy(const vb_mps *mps, double *out_host /* [1] */);
  * instance may not appear twice. */
 vb_status tdvp2_sweep_batched(vb_mps *const *mps, const vb_mpo *const *mpo, int count, double dt_fs,
                               const vb_tdvp_opts *opts, vb_sweep_stats *stats /* [count], nullable */);
+
+/* ---- ordering of the chain sites (Sec. 3.1, ordering of local sites;
+ * Sec. 4: strongly coupled sites next to each other, the small-basis
+ * entangled sites in the middle, bath modes at one end). Host only: these
+ * calls need no GPU and ignore model->site_order unless stated.
+ *
+ * Cost model of an order (n = n_modes + 1 sites, the MPO of that order as
+ * mpo_build would build it, MPS bonds at their saturated size
+ * m_b = min(m_max, product of the site dimensions on either side of bond b)):
+ *   heff_flops    F = sum over pairs i of the floating-point operations of
+ *                 one H_eff,2 application (Eq. two-site Hamiltonian; counted as
+ *                 vb_profile counts them);
+ *   tensor_elems  T = sum over pairs of m_{i-1} d_i d_{i+1} m_{i+1} (the
+ *                 Krylov vectors and the split scale with it);
+ *   max_tensor    the largest two-site tensor;
+ *   coupling_dist D = sum over site pairs (a, b) of K_ab |pos_a - pos_b|,
+ *                 K_ab = sum of |c| / omega-bar over the terms c * (...) of
+ *                 Eqs. Helvib_2 acting on both a and b, omega-bar the geometric
+ *                 mean frequency of the term's modes;
+ *   objective     J = (w_F F/F0 + w_T T/T0 + w_D D/D0) / (w_F + w_T + w_D),
+ *                 F0, T0, D0 those of the default order (electronic site
+ *                 first, modes by index), which therefore has J = 1;
+ *   max_w         the largest MPO bond dimension. */
+typedef struct {
+  int m_max;                /* MPS bond cap of the saturated-bond estimate */
+  double w_flops;           /* weights of F, T and D in J (>= 0, not all 0) */
+  double w_size;
+  double w_coupling;
+  int iters;                /* search: 0 = every order for n <= 8 sites, else
+                               20000 annealing moves; > 0 = that many moves;
+                               < 0 = every order (n <= 10) */
+  unsigned long long seed;  /* annealing random stream */
+  int n_strong;             /* modes the rule of thumb places around the
+                               electronic site (0 = 4) */
+} vb_order_opts;
+
+typedef struct {
+  double heff_flops;
+  double tensor_elems;
+  double max_tensor;
+  double coupling_dist;
+  double objective;
+  int max_w;
+} vb_order_cost;
+
+/* Cost of `order` ([n] chain positions -> -1 electronic site / k mode k; NULL
+ * = model->site_order, or the default order if that is NULL too). opts NULL =
+ * m_max 64, all weights 1. mpo_bonds [n-1] (nullable) receives the MPO bond
+ * dimensions; site_blocks [2n] (nullable) the number of nonzero operator
+ * blocks (non-identity, identity) of every site's MPO tensor. */
+vb_status vb_site_order_cost(const vb_model *model, const int *order, const vb_order_opts *opts,
+                             vb_order_cost *out, int *mpo_bonds, int *site_blocks);
+/* The order minimising J over all orders (n <= 8 by default) or the best
+ * one met by simulated annealing (swaps, segment reversals, single-site
+ * moves), started from the better of the default order and
+ * vb_site_order_rule's. Deterministic for a given seed. order_out: [n]. */
+vb_status vb_site_order_search(const vb_model *model, const vb_order_opts *opts, int *order_out,
+                               vb_order_cost *cost_out /* nullable */);
+/* The paper's rule of thumb (Sec. 3.1): the n_strong modes with the largest
+ * total coupling strength sum_b K_ab, in decreasing strength, alternately
+ * to the right and to the left of the electronic site; the remaining (bath)
+ * modes after them by increasing frequency. order_out: [n]. */
+vb_status vb_site_order_rule(const vb_model *model, int n_strong, int *order_out);
 
 /* ---- single operations on caller-owned device buffers (complex double).
  * These run the same kernels as tdvp2_sweep; `stream` is a cudaStream_t. */

@@ -26,7 +26,7 @@ EXPORTED = [
     "vb_heff1_apply", "vb_heff_work_elems", "vb_env_left_update", "vb_env_right_update",
     "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
     "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc", "mps_overlap", "mps_energy",
-    "tdvp2_sweep_batched", "tdvp1_sweep",
+    "tdvp2_sweep_batched", "tdvp1_sweep", "vb_site_order_cost", "vb_site_order_search", "vb_site_order_rule",
 ]
 
 
@@ -67,6 +67,16 @@ PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "spl
           "split_out", "split_subspace_products", "split_subspace_orth", "eigvec_invit", "eigvec_gram_schmidt",
           "eigvec_backtransform", "split_rayleigh_ritz", "split_ritz_fp32", "split_ritz_fp64",
           "split_orth_cholesky", "split_orth_products"]
+
+
+class vb_order_opts(C.Structure):
+    _fields_ = [("m_max", C.c_int), ("w_flops", C.c_double), ("w_size", C.c_double), ("w_coupling", C.c_double),
+                ("iters", C.c_int), ("seed", C.c_ulonglong), ("n_strong", C.c_int)]
+
+
+class vb_order_cost(C.Structure):
+    _fields_ = [("heff_flops", C.c_double), ("tensor_elems", C.c_double), ("max_tensor", C.c_double),
+                ("coupling_dist", C.c_double), ("objective", C.c_double), ("max_w", C.c_int)]
 
 
 class vb_sweep_stats(C.Structure):
@@ -118,6 +128,10 @@ def lib():
         "vb_kernel_launches": (C.c_ulonglong, []),
         "vb_profile_enable": (i, [i]),
         "vb_profile_read": (i, [C.POINTER(vb_profile), i]),
+        "vb_site_order_cost": (i, [C.POINTER(vb_model), vp, C.POINTER(vb_order_opts), C.POINTER(vb_order_cost),
+                                   vp, vp]),
+        "vb_site_order_search": (i, [C.POINTER(vb_model), C.POINTER(vb_order_opts), vp, C.POINTER(vb_order_cost)]),
+        "vb_site_order_rule": (i, [C.POINTER(vb_model), i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -156,48 +170,49 @@ def _stream_ptr(stream):
     return stream.cuda_stream
 
 
+
+def _model_struct(model: dict, keep: list) -> "vb_model":
+    """vb_model view of a model dict (see vibmodels); the arrays it points to
+    are appended to `keep`, which must outlive the struct."""
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    e0 = arr(model["e0"], np.float64)
+    v0 = arr(model["v0"], np.float64).reshape(-1)
+    lev = arr(model["levels"], np.int32)
+    g1 = arr(model["g1"], np.float64).reshape(-1)
+    g2 = model["g2"]
+    g2i = arr(np.array([[I, J, i, j] for (I, J, i, j, _) in g2], dtype=np.int32).reshape(-1, 4), np.int32)
+    g2v = arr(np.array([v for (*_, v) in g2], dtype=np.float64), np.float64)
+    om = arr(model["omega"], np.float64)
+    so = model.get("site_order")
+    m = vb_model()
+    m.n_el = int(model["n_el"])
+    m.e0 = _dp(e0, C.c_double)
+    m.v0 = _dp(v0, C.c_double)
+    m.n_modes = om.size
+    m.omega = _dp(om, C.c_double)
+    m.levels = _dp(lev, C.c_int)
+    m.g1 = _dp(g1, C.c_double)
+    m.n_g2 = len(g2)
+    m.g2_idx = _dp(g2i, C.c_int) if len(g2) else None
+    m.g2_val = _dp(g2v, C.c_double) if len(g2) else None
+    m.site_order = _dp(arr(so, np.int32), C.c_int) if so is not None else None
+    m.include_zpe = int(model.get("include_zpe", 1))
+    return m
+
+
 # ----------------------------------------------------------------- MPO
 class Mpo:
     """MPO of a vibronic model dict (see vibmodels); owns the C handle."""
 
     def __init__(self, model: dict):
         L = lib()
-        n_el = int(model["n_el"])
-        omega = np.ascontiguousarray(model["omega"], dtype=np.float64)
-        nm = omega.size
         self._keep = []
-
-        def arr(a, dt):
-            a = np.ascontiguousarray(a, dtype=dt)
-            self._keep.append(a)
-            return a
-
-        e0 = arr(model["e0"], np.float64)
-        v0 = arr(model["v0"], np.float64).reshape(-1)
-        lev = arr(model["levels"], np.int32)
-        g1 = arr(model["g1"], np.float64).reshape(-1)
-        g2 = model["g2"]
-        g2i = arr(np.array([[I, J, i, j] for (I, J, i, j, _) in g2], dtype=np.int32).reshape(-1, 4), np.int32)
-        g2v = arr(np.array([v for (*_, v) in g2], dtype=np.float64), np.float64)
-        so = model.get("site_order")
-        m = vb_model()
-        m.n_el = n_el
-        m.e0 = _dp(e0, C.c_double)
-        m.v0 = _dp(v0, C.c_double)
-        m.n_modes = nm
-        om = arr(omega, np.float64)
-        m.omega = _dp(om, C.c_double)
-        m.levels = _dp(lev, C.c_int)
-        m.g1 = _dp(g1, C.c_double)
-        m.n_g2 = len(g2)
-        m.g2_idx = _dp(g2i, C.c_int) if len(g2) else None
-        m.g2_val = _dp(g2v, C.c_double) if len(g2) else None
-        if so is not None:
-            soa = arr(so, np.int32)
-            m.site_order = _dp(soa, C.c_int)
-        else:
-            m.site_order = None
-        m.include_zpe = int(model.get("include_zpe", 1))
+        m = _model_struct(model, self._keep)
+        self.n_el = int(model["n_el"])
         h = C.c_void_p()
         check(L.mpo_build(C.byref(m), C.byref(h)))
         self.h = h
@@ -291,8 +306,7 @@ class Mps:
         return st
 
     def populations(self) -> np.ndarray:
-        n_el = self.mpo.site_dims(0)[1]
-        out = np.zeros(n_el)
+        out = np.zeros(self.mpo.n_el)
         check(lib().measure_populations(self.h, out.ctypes.data))
         return out
 
@@ -408,3 +422,55 @@ def vb_herm_eig_top_noalloc(n, rho, k_want, k_vec, evals, evecs, stream=None):
     allocation; n <= 256, k_want <= 128; concurrent calls race)."""
     check(lib().vb_herm_eig_top_noalloc(n, _ptr(rho), k_want, k_vec, _ptr(evals), _ptr(evecs),
                                         _stream_ptr(stream)))
+
+
+# ----------------------------------------------------------------- site order
+def _order_opts(m_max, w_flops, w_size, w_coupling, iters=0, seed=0, n_strong=0):
+    return vb_order_opts(int(m_max), float(w_flops), float(w_size), float(w_coupling), int(iters), int(seed),
+                         int(n_strong))
+
+
+def _cost_dict(c: "vb_order_cost") -> dict:
+    return {"heff_flops": c.heff_flops, "tensor_elems": c.tensor_elems, "max_tensor": c.max_tensor,
+            "coupling_dist": c.coupling_dist, "objective": c.objective, "max_w": c.max_w}
+
+
+def site_order_cost(model: dict, order=None, m_max: int = 64, w_flops: float = 1.0, w_size: float = 1.0,
+                    w_coupling: float = 1.0):
+    """Cost model of a chain order (vb_site_order_cost): returns the cost
+    dict, the MPO bond dimensions and the (operator, identity) block counts of
+    every site."""
+    keep = []
+    m = _model_struct(model, keep)
+    n = m.n_modes + 1
+    o = _order_opts(m_max, w_flops, w_size, w_coupling)
+    c = vb_order_cost()
+    bonds = np.zeros(max(1, n - 1), dtype=np.int32)
+    blocks = np.zeros(2 * n, dtype=np.int32)
+    oa = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    check(lib().vb_site_order_cost(C.byref(m), None if oa is None else oa.ctypes.data, C.byref(o), C.byref(c),
+                                   bonds.ctypes.data, blocks.ctypes.data))
+    return _cost_dict(c), [int(x) for x in bonds[: n - 1]], blocks.reshape(n, 2).tolist()
+
+
+def site_order_search(model: dict, m_max: int = 64, w_flops: float = 1.0, w_size: float = 1.0,
+                      w_coupling: float = 1.0, iters: int = 0, seed: int = 0, n_strong: int = 0):
+    """Order minimising the cost model (vb_site_order_search): returns
+    (order, cost dict), order[p] = -1 for the electronic site, k for mode k."""
+    keep = []
+    m = _model_struct(model, keep)
+    n = m.n_modes + 1
+    o = _order_opts(m_max, w_flops, w_size, w_coupling, iters, seed, n_strong)
+    out = np.zeros(n, dtype=np.int32)
+    c = vb_order_cost()
+    check(lib().vb_site_order_search(C.byref(m), C.byref(o), out.ctypes.data, C.byref(c)))
+    return [int(x) for x in out], _cost_dict(c)
+
+
+def site_order_rule(model: dict, n_strong: int = 4):
+    """The rule-of-thumb order of vb_site_order_rule."""
+    keep = []
+    m = _model_struct(model, keep)
+    out = np.zeros(m.n_modes + 1, dtype=np.int32)
+    check(lib().vb_site_order_rule(C.byref(m), int(n_strong), out.ctypes.data))
+    return [int(x) for x in out]

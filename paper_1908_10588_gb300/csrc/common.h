@@ -142,6 +142,36 @@ vb_status gemm(const GemmArgsT<R> &g, cudaStream_t st);
 inline vb_status zgemm(const GemmArgs &g, cudaStream_t st) { return gemm<double>(g, st); }
 
 // ------------------------------------------------------------ MPO
+// Terms of the vibronic Hamiltonian (Eqs. Hel_2, Hvib_2, Helvib_2) as
+// products of local operators. A factor's `pos` is a chain position in the
+// builder; model_terms() returns factors on entities instead: ENT_EL the
+// electronic site, k >= 0 mode k, ENT_POS0 chain position 0 whatever sits
+// there (the zero-point constant).
+enum { OPC_ID = 0, OPC_Q = 1, OPC_Q2 = 2, OPC_N = 3, OPC_E = 16 /* + i*n_el + j */ };
+constexpr int ENT_EL = -1, ENT_POS0 = -2;
+struct Factor {
+  int pos, code;
+};
+struct Term {
+  double coef;
+  std::vector<Factor> f;
+};
+// every nonzero term of the model, factors on entities (unsorted); checks the
+// coupling indices; `who` prefixes error messages
+vb_status model_terms(const vb_model *m, const char *who, std::vector<Term> &terms);
+
+// algorithmic floating-point operations of one H_eff,2 application at the
+// pair (i, i + 1): the left environment contraction, the two W-site
+// applications (a non-identity d x d block costs 4 d^2 per stacked vector,
+// an identity block 2 d) and the right environment contraction
+inline double heff2_flops_of(double mL, double mR, int d1, int d2, int wl1, int wr2, long long nop1,
+                             long long nid1, long long nop2, long long nid2) {
+  const double th = mL * d1 * d2 * mR;
+  const double w1 = (double)nid1 * 2.0 * d1 + (double)nop1 * 4.0 * d1 * d1;
+  const double w2 = (double)nid2 * 2.0 * d2 + (double)nop2 * 4.0 * d2 * d2;
+  return 8.0 * th * mL * wl1 + w1 * (mL * d2 * mR) + w2 * (mL * d1 * mR) + 8.0 * th * wr2 * mR;
+}
+
 struct MpoBlock {
   int win, wout;
   int ident;   // operator is the identity

@@ -53,17 +53,6 @@ void Alloc::put(void *p) {
 
 namespace {
 
-// local operator codes
-enum { OPC_ID = 0, OPC_Q = 1, OPC_Q2 = 2, OPC_N = 3, OPC_E = 16 /* + i*n_el + j */ };
-
-struct Factor {
-  int pos, code;
-};
-struct Term {
-  double coef;
-  std::vector<Factor> f;  // sorted by position
-};
-
 std::vector<double> local_op(int code, int d, int n_el) {
   std::vector<double> m((size_t)d * d, 0.0);
   if (code == OPC_ID) {
@@ -109,6 +98,40 @@ Key key_at(const Term &t, int b) {
 }
 
 }  // namespace
+
+vb_status model_terms(const vb_model *m, const char *who, std::vector<Term> &terms) {
+  terms.clear();
+  const int n_el = m->n_el, nm = m->n_modes;
+  auto add = [&](double c, std::vector<Factor> f) {
+    if (c != 0.0) terms.push_back(Term{c, std::move(f)});
+  };
+  for (int i = 0; i < n_el; ++i)
+    for (int j = 0; j < n_el; ++j) {
+      double h = (i == j) ? m->e0[i] : (m->v0 ? m->v0[i * n_el + j] : 0.0);
+      add(h, {{ENT_EL, OPC_E + i * n_el + j}});
+    }
+  double zpe = 0.0;
+  for (int I = 0; I < nm; ++I) {
+    add(m->omega[I], {{I, OPC_N}});
+    zpe += 0.5 * m->omega[I];
+  }
+  if (m->include_zpe) add(zpe, {{ENT_POS0, OPC_ID}});
+  for (int I = 0; I < nm; ++I)
+    for (int i = 0; i < n_el; ++i)
+      for (int j = 0; j < n_el; ++j)
+        add(m->g1[((size_t)I * n_el + i) * n_el + j], {{ENT_EL, OPC_E + i * n_el + j}, {I, OPC_Q}});
+  for (int k = 0; k < m->n_g2; ++k) {
+    int I = m->g2_idx[4 * k], J = m->g2_idx[4 * k + 1], i = m->g2_idx[4 * k + 2], j = m->g2_idx[4 * k + 3];
+    if (I < 0 || J < 0 || I >= nm || J >= nm || I > J || i < 0 || j < 0 || i >= n_el || j >= n_el)
+      return fail(VB_EINVAL, std::string(who) + ": g2 index out of range (need 0 <= I <= J < n_modes)");
+    if (I == J)
+      add(m->g2_val[k], {{ENT_EL, OPC_E + i * n_el + j}, {I, OPC_Q2}});
+    else
+      add(m->g2_val[k], {{ENT_EL, OPC_E + i * n_el + j}, {I, OPC_Q}, {J, OPC_Q}});
+  }
+  return VB_OK;
+}
+
 }  // namespace vb
 
 using namespace vb;
@@ -154,36 +177,12 @@ vb_status mpo_build(const vb_model *m, vb_mpo **out) {
       pos_of_mode[order[p]] = p;
     }
   }
-  // ---- terms (Eqs. Hel_2, Hvib_2, Helvib_2)
+  // ---- terms (Eqs. Hel_2, Hvib_2, Helvib_2), placed on the chain
   std::vector<Term> terms;
-  auto add = [&](double c, std::vector<Factor> f) {
-    if (c == 0.0) return;
-    std::sort(f.begin(), f.end(), [](const Factor &a, const Factor &b) { return a.pos < b.pos; });
-    terms.push_back(Term{c, f});
-  };
-  for (int i = 0; i < n_el; ++i)
-    for (int j = 0; j < n_el; ++j) {
-      double h = (i == j) ? m->e0[i] : (m->v0 ? m->v0[i * n_el + j] : 0.0);
-      add(h, {{el_pos, OPC_E + i * n_el + j}});
-    }
-  double zpe = 0.0;
-  for (int I = 0; I < nm; ++I) {
-    add(m->omega[I], {{pos_of_mode[I], OPC_N}});
-    zpe += 0.5 * m->omega[I];
-  }
-  if (m->include_zpe) add(zpe, {{0, OPC_ID}});
-  for (int I = 0; I < nm; ++I)
-    for (int i = 0; i < n_el; ++i)
-      for (int j = 0; j < n_el; ++j)
-        add(m->g1[((size_t)I * n_el + i) * n_el + j], {{el_pos, OPC_E + i * n_el + j}, {pos_of_mode[I], OPC_Q}});
-  for (int k = 0; k < m->n_g2; ++k) {
-    int I = m->g2_idx[4 * k], J = m->g2_idx[4 * k + 1], i = m->g2_idx[4 * k + 2], j = m->g2_idx[4 * k + 3];
-    if (I < 0 || J < 0 || I >= nm || J >= nm || I > J || i < 0 || j < 0 || i >= n_el || j >= n_el)
-      return fail(VB_EINVAL, "mpo_build: g2 index out of range (need 0 <= I <= J < n_modes)");
-    if (I == J)
-      add(m->g2_val[k], {{el_pos, OPC_E + i * n_el + j}, {pos_of_mode[I], OPC_Q2}});
-    else
-      add(m->g2_val[k], {{el_pos, OPC_E + i * n_el + j}, {pos_of_mode[I], OPC_Q}, {pos_of_mode[J], OPC_Q}});
+  VB_TRY(model_terms(m, "mpo_build", terms));
+  for (Term &t : terms) {
+    for (Factor &x : t.f) x.pos = x.pos == ENT_EL ? el_pos : x.pos == ENT_POS0 ? 0 : pos_of_mode[x.pos];
+    std::sort(t.f.begin(), t.f.end(), [](const Factor &a, const Factor &b) { return a.pos < b.pos; });
   }
   // merge factors on the same site (cannot happen for this model, but keep exact)
   for (Term &t : terms)

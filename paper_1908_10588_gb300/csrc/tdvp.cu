@@ -168,6 +168,29 @@ __global__ void populations_kernel(const cd *C, int d, int mR, double *out) {
   }
 }
 
+__global__ void populations_proj_kernel(const cd *A, const cd *X, int me, int d, int mr, double *out) {
+  // P_k = Re sum_{x', y} conj(A[x', k, y]) X[x', k, y] / sum over k; one warp per k
+  __shared__ double ps[64];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long rows = (long long)me * mr;
+  for (int k = w; k < d; k += nw) {
+    double a = 0.0;
+    for (long long r = lane; r < rows; r += 32) {
+      const long long o = (r / mr) * d * mr + (long long)k * mr + r % mr;
+      const cd u = A[o], v = X[o];
+      a += u.x * v.x + u.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) ps[k] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < d; ++k) t += ps[k];
+    for (int k = 0; k < d; ++k) out[k] = ps[k] / t;
+  }
+}
+
 inline int grid1(long long n) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
@@ -388,9 +411,7 @@ double heff_flops(const vb_mpo *mpo, int site, int two_site, int mL, int mR) {
   const MpoSite &S = mpo->sites[site];
   if (two_site) {
     const MpoSite &S2 = mpo->sites[site + 1];
-    const double th = (double)mL * S.d * S2.d * mR;
-    return 8.0 * th * mL * S.wl + wsite_flops(S, (double)mL * S2.d * mR) +
-           wsite_flops(S2, (double)mL * S.d * mR) + 8.0 * th * S2.wr * mR;
+    return heff2_flops_of(mL, mR, S.d, S2.d, S.wl, S2.wr, S.nnz_ops, S.n_ident, S2.nnz_ops, S2.n_ident);
   }
   const double c = (double)mL * S.d * mR;
   return 8.0 * c * mL * S.wl + wsite_flops(S, (double)mL * mR) + 8.0 * c * S.wr * mR;
@@ -1041,14 +1062,13 @@ struct Scratch {
   }
 };
 
-// <a|b> = contraction of the transfer matrices E_p[y', y] =
+// transfer matrix of sites 0 .. p_end-1: E_p[y', y] =
 // sum_{x, x', s} conj(A_p[x', s, y']) E_{p-1}[x', x] B_p[x, s, y], E_0 = 1
 // (two complex FP64 GEMMs per site), on a's stream; result left on the device
-vb_status overlap_dev(const vb_mps *a, const vb_mps *b, Scratch &sc, cd **res) {
-  const int n = a->n;
+vb_status transfer_left(const vb_mps *a, const vb_mps *b, int p_end, Scratch &sc, cd **res) {
   long long e_cap = 1, x_cap = 1;
-  for (int p = 0; p <= n; ++p) e_cap = std::max<long long>(e_cap, (long long)a->bond[p] * b->bond[p]);
-  for (int p = 0; p < n; ++p)
+  for (int p = 0; p <= p_end; ++p) e_cap = std::max<long long>(e_cap, (long long)a->bond[p] * b->bond[p]);
+  for (int p = 0; p < p_end; ++p)
     x_cap = std::max<long long>(x_cap, (long long)a->bond[p] * a->dims[p] * b->bond[p + 1]);
   cd *E0 = nullptr, *E1 = nullptr, *X = nullptr;
   VB_TRY(sc.get((void **)&E0, e_cap * sizeof(cd)));
@@ -1056,7 +1076,7 @@ vb_status overlap_dev(const vb_mps *a, const vb_mps *b, Scratch &sc, cd **res) {
   VB_TRY(sc.get((void **)&X, x_cap * sizeof(cd)));
   const cd one = mkc(1.0, 0.0);
   VB_TRY_CUDA(cudaMemcpyAsync(E0, &one, sizeof(cd), cudaMemcpyHostToDevice, a->st));
-  for (int p = 0; p < n; ++p) {
+  for (int p = 0; p < p_end; ++p) {
     const int xa = a->bond[p], ya = a->bond[p + 1], xb = b->bond[p], yb = b->bond[p + 1], d = a->dims[p];
     GemmArgs g{};  // X[x', (s y)] = E[x', x] B[x, (s y)]
     g.M = xa; g.N = d * yb; g.K = xb; g.batch = 1;
@@ -1076,6 +1096,11 @@ vb_status overlap_dev(const vb_mps *a, const vb_mps *b, Scratch &sc, cd **res) {
   }
   *res = E0;
   return VB_OK;
+}
+
+// <a|b>: the transfer matrix of the whole chain (1 x 1)
+vb_status overlap_dev(const vb_mps *a, const vb_mps *b, Scratch &sc, cd **res) {
+  return transfer_left(a, b, a->n, sc, res);
 }
 
 // <psi|H|psi> through the left environments of the whole chain, FP64
@@ -1530,12 +1555,36 @@ vb_status tdvp2_sweep_batched(vb_mps *const *mps, const vb_mpo *const *mpo, int 
 
 vb_status measure_populations(const vb_mps *s, double *pop_host) {
   if (!s || !pop_host) return fail(VB_EINVAL, "measure_populations: null argument");
-  if (s->mpo->el_pos != 0) return fail(VB_EINVAL, "measure_populations: electronic site must be first");
   if (s->center != 0) return fail(VB_ESTATE, "measure_populations: center is not on site 0");
-  const int d = s->dims[0];
+  const int e = s->mpo->el_pos;
+  const int d = s->dims[e];
   if (d > 64) return fail(VB_EINVAL, "measure_populations: more than 64 electronic states");
-  populations_kernel<<<1, 256, 0, s->st>>>(s->A[0], d, s->bond[1], s->d_pop);
-  VB_CHECK_LAUNCH();
+  if (e == 0) {
+    populations_kernel<<<1, 256, 0, s->st>>>(s->A[0], d, s->bond[1], s->d_pop);
+    VB_CHECK_LAUNCH();
+  } else {
+    // sites right of e are right-orthonormal, so only the transfer matrix of
+    // sites 0 .. e-1 enters: P_k = sum conj(A_e[x', k, y]) (E A_e)[x', k, y]
+    VB_TRY(set_device_of(const_cast<vb_mps *>(s)));
+    vb::Alloc al = s->alloc;
+    Scratch sc(&al);
+    cd *E = nullptr, *X = nullptr;
+    VB_TRY(transfer_left(s, s, e, sc, &E));
+    const int me = s->bond[e], mr = s->bond[e + 1];
+    VB_TRY(sc.get((void **)&X, (size_t)me * d * mr * sizeof(cd)));
+    GemmArgs g{};  // X[x', (k y)] = E[x', x] A_e[x, (k y)]
+    g.M = me; g.N = d * mr; g.K = me; g.batch = 1;
+    g.opA = OP_N; g.opB = OP_N;
+    g.A = E; g.lda = me; g.B = s->A[e]; g.ldb = (long long)d * mr; g.C = X; g.ldc = (long long)d * mr;
+    g.alpha = mkc(1.0, 0.0); g.beta = mkc(0.0, 0.0);
+    g.a_size = (long long)me * me; g.b_size = (long long)me * d * mr; g.c_size = (long long)me * d * mr;
+    VB_TRY(zgemm(g, s->st));
+    populations_proj_kernel<<<1, 256, 0, s->st>>>(s->A[e], X, me, d, mr, s->d_pop);
+    VB_CHECK_LAUNCH();
+    VB_TRY_CUDA(cudaMemcpyAsync(pop_host, s->d_pop, d * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    VB_TRY_CUDA(cudaStreamSynchronize(s->st));  // before the scratch returns to the allocator
+    return VB_OK;
+  }
   VB_TRY_CUDA(cudaMemcpyAsync(pop_host, s->d_pop, d * sizeof(double), cudaMemcpyDeviceToHost, s->st));
   VB_TRY_CUDA(cudaStreamSynchronize(s->st));
   return VB_OK;
