@@ -43,6 +43,7 @@ M_MAX = 64
 EPS = 1e-8
 DT_FS = 0.5
 STATE_SEED = 424242
+PROF_EVERY = 4  # per-phase events on one call in four (systematic sampling; each event pair costs host time)
 WORKLOAD = ("internal-conversion-like: 2 states + 24 modes (d 10-30, seed 1002), linear + quadratic "
             "+ 24 bilinear couplings, max bond 64, DBSS 1e-8, dt 0.5 fs, bond-saturated state")
 # GB300 FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
@@ -201,7 +202,7 @@ def run_ours(args):
 
     # ---- timed region (device time, CUDA events on the library's stream)
     P.vb_profile_read(reset=True)
-    P.vb_profile_enable(True)
+    P.vb_profile_enable(True, every=PROF_EVERY)
     launches0 = P.vb_kernel_launches()
     proc, cpath = _clock_sampler_start()
     if ws > 1:
@@ -302,11 +303,15 @@ def run_ours(args):
         mso = P.Mps(mpo_o, m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=stream, tensors=to)
         mso.sweep(DT_FS, **sweep_kw)
         torch.cuda.synchronize()
+        P.vb_profile_read(reset=True)
+        P.vb_profile_enable(True, every=PROF_EVERY)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
         st_o = [mso.sweep(DT_FS, **sweep_kw) for _ in range(2)]
         c1.record(stream)
         torch.cuda.synchronize()
+        P.vb_profile_enable(False)
+        prof_o = P.vb_profile_read(reset=True)
         o_ms = c0.elapsed_time(c1) / 2
         po = mso.populations()
         order_line = {
@@ -317,6 +322,10 @@ def run_ours(args):
                                      "max_mpo_bond": [cdef["max_w"], cost["max_w"]]},
             "ms_per_step": o_ms, "steps_timed": 2, "speedup_vs_default_order": (ms / args.steps) / o_ms,
             "krylov_iters_max": max(x.krylov_iters_max for x in st_o), "max_bond": max(mso.bond_dims()),
+            "krylov_iters_per_step": sum(x.krylov_iters_total for x in st_o) / 2,
+            "phases_ms_per_step": {k: round(prof_o[k]["ms"] / 2, 3)
+                                   for k in ("heff2", "heff1", "krylov", "split", "env", "merge")},
+            "heff_flops_per_step": (prof_o["heff2"]["flops"] + prof_o["heff1"]["flops"]) / 2,
             "populations": [float(x) for x in po],
         }
         mso.close()
@@ -338,6 +347,7 @@ def run_ours(args):
                 "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio (tf32 pipe)",
                 "useful_ceiling_split_tf32": pk / 3.0, "frac_of_useful_ceiling": achieved / (pk / 3.0)}
     roof["kernel"] = "H_eff products (two- and one-site), algorithmic flops / event time"
+    roof["events"] = f"CUDA events on 1 of every {PROF_EVERY} calls of each phase in the timed region, times scaled"
     roof["heff_calls"] = h2["calls"] + prof["heff1"]["calls"]
     roof["heff_ms_per_call"] = heff_ms / max(1, roof["heff_calls"])
     # second roofline: the Krylov vector work (the largest phase), FP64 ALU-bound
@@ -371,6 +381,8 @@ def run_ours(args):
                         for k in ("heff2", "heff1", "krylov", "split", "env", "merge")},
         "heff_tflops": achieved,
         "krylov_iters_max": max(s.krylov_iters_max for s in stats),
+        "krylov_iters_per_step": sum(s.krylov_iters_total for s in stats) / len(stats),
+        "heff_flops_per_step": heff_flops / args.steps,
         "max_bond": max(bonds),
         "populations": [float(x) for x in pops],
     }

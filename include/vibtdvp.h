@@ -327,14 +327,20 @@ unsigned long long vb_kernel_launches(void);
  * multiply-add is 8, real-times-complex 4, an identity-block add 2);
  * krylov_flops counts the FP64 operations of the Krylov vector work (phase
  * 2: inner products, updates, norms, scaling, the final combination) the same
- * way. */
+ * way. Each event pair costs a few microseconds of host time on the
+ * launching thread, about 10^4 pairs per time step of a 25-site chain, so
+ * the profiler can sample: vb_profile_enable(k) records events for the calls
+ * of each phase numbered 0, k, 2k, ... (every run of k consecutive calls
+ * gives one) and ms[p] = sampled time x calls[p] / sampled calls; calls and
+ * flops count every call. k = 1 times every call, 0 switches the profiler
+ * off. Host-side state, not thread-safe. */
 typedef struct {
   double ms[24];
   long long calls[24];
   double heff_flops[2];
   double krylov_flops;
 } vb_profile;
-vb_status vb_profile_enable(int on);
+vb_status vb_profile_enable(int every);
 vb_status vb_profile_read(vb_profile *out, int reset);
 
 #ifdef __cplusplus

@@ -403,8 +403,10 @@ def vb_kernel_launches() -> int:
     return int(lib().vb_kernel_launches())
 
 
-def vb_profile_enable(on: bool = True):
-    check(lib().vb_profile_enable(int(on)))
+def vb_profile_enable(on=True, every: int = 1):
+    """Switch the per-phase event profiler on (events for one call in
+    `every` of each phase, times scaled) or off."""
+    check(lib().vb_profile_enable(int(every) if on else 0))
 
 
 def vb_profile_read(reset: bool = True) -> dict:

@@ -11,15 +11,21 @@ std::atomic<unsigned long long> g_launches{0};
 struct Pending {
   int phase;
   cudaEvent_t a, b;
-  double flops;
 };
+// Calls of a phase are numbered in order; with every = k > 1 only calls
+// whose number is a multiple of k get events (systematic sampling: every
+// stretch of k consecutive calls contributes one), and the phase's time is
+// the sampled time scaled by calls / sampled calls. Call counts and flops
+// are exact.
 struct Prof {
-  bool on = false;
+  int every = 0;
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> open_start;  // per phase
+  unsigned long long seq[PH_COUNT] = {0};
   double ms[PH_COUNT] = {0};
   long long calls[PH_COUNT] = {0};
+  long long sampled[PH_COUNT] = {0};
   double flops[2] = {0, 0};
   double krylov_flops = 0;
 } g_prof;
@@ -38,21 +44,29 @@ cudaEvent_t take_event() {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-bool prof_on() { return g_prof.on; }
+bool prof_on() { return g_prof.every > 0; }
 
 void prof_begin(int phase, cudaStream_t st) {
-  if (!g_prof.on) return;
+  if (!g_prof.every) return;
   if (g_prof.open_start.size() < PH_COUNT) g_prof.open_start.assign(PH_COUNT, nullptr);
+  g_prof.calls[phase]++;
+  if (g_prof.seq[phase]++ % (unsigned long long)g_prof.every != 0) {
+    g_prof.open_start[phase] = nullptr;
+    return;
+  }
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
   g_prof.open_start[phase] = e;
 }
 
 void prof_end(int phase, cudaStream_t st, double flops) {
-  if (!g_prof.on || g_prof.open_start.size() < PH_COUNT || !g_prof.open_start[phase]) return;
+  if (!g_prof.every) return;
+  if (phase < 2) g_prof.flops[phase] += flops;
+  if (phase == PH_KRYLOV) g_prof.krylov_flops += flops;
+  if (g_prof.open_start.size() < PH_COUNT || !g_prof.open_start[phase]) return;
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
-  g_prof.pending.push_back(Pending{phase, g_prof.open_start[phase], e, flops});
+  g_prof.pending.push_back(Pending{phase, g_prof.open_start[phase], e});
   g_prof.open_start[phase] = nullptr;
 }
 
@@ -68,9 +82,7 @@ void prof_collect() {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p.a, p.b);
     g_prof.ms[p.phase] += ms;
-    g_prof.calls[p.phase] += 1;
-    if (p.phase < 2) g_prof.flops[p.phase] += p.flops;
-    if (p.phase == PH_KRYLOV) g_prof.krylov_flops += p.flops;
+    g_prof.sampled[p.phase] += 1;
     g_prof.pool.push_back(p.a);
     g_prof.pool.push_back(p.b);
   }
@@ -83,8 +95,9 @@ extern "C" {
 
 unsigned long long vb_kernel_launches(void) { return vb::g_launches.load(); }
 
-vb_status vb_profile_enable(int on) {
-  vb::g_prof.on = on != 0;
+vb_status vb_profile_enable(int every) {
+  if (every < 0) return vb::fail(VB_EINVAL, "vb_profile_enable: negative sampling interval");
+  vb::g_prof.every = every;
   return VB_OK;
 }
 
@@ -93,8 +106,9 @@ vb_status vb_profile_read(vb_profile *out, int reset) {
   vb::prof_collect();
   std::memset(out, 0, sizeof(*out));
   for (int i = 0; i < vb::PH_COUNT; ++i) {
-    out->ms[i] = vb::g_prof.ms[i];
-    out->calls[i] = vb::g_prof.calls[i];
+    const long long c = vb::g_prof.calls[i], k = vb::g_prof.sampled[i];
+    out->ms[i] = k > 0 ? vb::g_prof.ms[i] * ((double)c / (double)k) : 0.0;
+    out->calls[i] = c;
   }
   out->heff_flops[0] = vb::g_prof.flops[0];
   out->heff_flops[1] = vb::g_prof.flops[1];
@@ -103,6 +117,8 @@ vb_status vb_profile_read(vb_profile *out, int reset) {
     for (int i = 0; i < vb::PH_COUNT; ++i) {
       vb::g_prof.ms[i] = 0;
       vb::g_prof.calls[i] = 0;
+      vb::g_prof.sampled[i] = 0;
+      vb::g_prof.seq[i] = 0;
     }
     vb::g_prof.flops[0] = vb::g_prof.flops[1] = 0;
     vb::g_prof.krylov_flops = 0;

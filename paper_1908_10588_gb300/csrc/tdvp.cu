@@ -572,6 +572,81 @@ int choose_rank(const std::vector<double> &lam, int n, double tot, int rank_boun
 // or (right) C (dstA) and right-orthonormal B (dstC). Returns the new bond.
 vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old, const TruncOpts &o,
                       cd *dstA, cd *dstC, int *k_out, double *disc);
+vb_status qr_cols(vb_mps *s, const cd *M, long long n1, int m, cd *Q, cd *Rm, unsigned long long seed);
+vb_status lq_rows(vb_mps *s, const cd *Cm, int m, long long n2, cd *Q, cd *Rm, unsigned long long seed);
+vb_status tdvp1_setup(vb_mps *s);
+
+// The same split from the Gram matrix of the other, smaller side (FP64),
+// for pairs whose two sides differ much in size (a small-basis site next to
+// a large one): the Schmidt vectors of the small side come from its
+// eigenvectors, the large side's are theta applied to them, orthonormalised
+// by Cholesky QR done twice, and the bond tensor is theta projected on those.
+// Mathematically the same truncation as the eigenvectors of the large side's
+// rho; the eigenproblem is only min(n1, n2) wide.
+vb_status split_small_side(vb_mps *s, bool left, int n1, int n2, const TruncOpts &o, cd *dstA, cd *dstC,
+                           int *k_out, double *disc) {
+  cudaStream_t st = s->st;
+  const int ns = left ? n2 : n1;
+  const cd *M = s->theta;
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  auto G64 = [&](int Mm, int Nn, int Kk, int opA, const cd *A, long long lda, long long asz, int opB, const cd *B,
+                 long long ldb, long long bsz, cd *C, long long ldc, long long csz) {
+    GemmArgs g{};
+    g.M = Mm; g.N = Nn; g.K = Kk; g.batch = 1; g.opA = opA; g.opB = opB;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.alpha = one; g.beta = zero; g.a_size = asz; g.b_size = bsz; g.c_size = csz;
+    g.ws = s->skws; g.ws_elems = s->skws_elems;
+    return zgemm(g, st);
+  };
+  const long long nm = (long long)n1 * n2, rs = (long long)s->nrho_cap * s->nrho_cap;
+  prof_begin(PH_RHO, st);
+  if (left)  // rho_s = M^+ M (n2 x n2)
+    VB_TRY(G64(ns, ns, n1, OP_C, M, n2, nm, OP_N, M, n2, nm, s->rho, ns, rs));
+  else  // rho_s = M M^+ (n1 x n1)
+    VB_TRY(G64(ns, ns, n2, OP_N, M, n2, nm, OP_C, M, n2, nm, s->rho, ns, rs));
+  trace_kernel<<<1, 256, 0, st>>>(s->rho, ns, s->d_trace);
+  VB_CHECK_LAUNCH();
+  prof_end(PH_RHO, st, 0.0);
+  const int kw = std::min(ns, o.m_max + 1);
+  prof_begin(PH_EIGVAL, st);
+  VB_TRY(eig_values(ns, s->rho, kw, s->d_evals, s->eigw, st));
+  prof_end(PH_EIGVAL, st, 0.0);
+  std::vector<double> lam(kw);
+  double tot = 0.0;
+  VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), s->d_evals, kw * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaMemcpyAsync(&tot, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  VB_TRY(EigWork::check(ns, kw, sizeof(double), s->eigw, st));
+  const int k = choose_rank(lam, ns, tot, ns, o, disc);
+  prof_begin(PH_EIGVEC, st);
+  VB_TRY(eig_vectors(ns, s->rho, kw, k, s->d_evals, s->Z, s->eigw, st));
+  prof_end(PH_EIGVEC, st, 0.0);
+  prof_begin(PH_SPLITOUT, st);
+  const unsigned long long seed = 0x452821E638D01377ull + 0x9E3779B97F4A7C15ull * (++s->split_calls);
+  cd *Y = s->X;
+  if (left) {
+    // rows z_j of Z: right vectors conj(z_j); Y = M Z^T (n1 x k) has columns
+    // sigma_j u_j; A = Q of Y, C = A^+ M
+    VB_TRY(G64(n1, k, n2, OP_N, M, n2, nm, OP_T, s->Z, ns, (long long)k * ns, Y, k, (long long)n1 * k));
+    VB_TRY(qr_cols(s, Y, n1, k, dstA, s->q_Rm, seed));
+    VB_TRY(G64(k, n2, n1, OP_C, dstA, k, (long long)n1 * k, OP_N, M, n2, nm, dstC, n2, (long long)k * n2));
+    const long long nc = (long long)k * n2;
+    VB_TRY(vec_norm2(dstC, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
+    VB_TRY(vec_scale_inv(dstC, nc, s->d_nrm, st));
+  } else {
+    // rows z_j of Z: left vectors u_j = z_j; Y = conj(Z) M (k x n2) has rows
+    // sigma_j v_j^+; B = the LQ factor of Y with orthonormal rows, C = M B^+
+    VB_TRY(G64(k, n2, n1, OP_R, s->Z, ns, (long long)k * ns, OP_N, M, n2, nm, Y, n2, (long long)k * n2));
+    VB_TRY(lq_rows(s, Y, k, n2, dstC, s->q_Rm, seed));
+    VB_TRY(G64(n1, k, n2, OP_N, M, n2, nm, OP_C, dstC, n2, (long long)k * n2, dstA, k, (long long)n1 * k));
+    const long long nc = (long long)n1 * k;
+    VB_TRY(vec_norm2(dstA, nc, s->d_nrm, s->d_part, reduce_parts(nc), st));
+    VB_TRY(vec_scale_inv(dstA, nc, s->d_nrm, st));
+  }
+  prof_end(PH_SPLITOUT, st, 0.0);
+  *k_out = k;
+  return VB_OK;
+}
 
 // m_old: the bond dimension between the two sites before this split; dstA
 // (left) or dstC (right) still holds the old tensor on entry
@@ -582,8 +657,15 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old,
   const int n = left ? n1 : n2;
   // mixed form: FP32 subspace iteration + FP64 projection once the matrix is
   // large enough for the FP64 reduction to matter
-  if (s->dtype == VB_MIXED && n > MIXED_SPLIT_MIN_N && o.m_max + 1 + 8 <= s->rcap)
-    return split_mixed(s, left, mL, d1, d2, mR, m_old, o, dstA, dstC, k_out, disc);
+  if (s->dtype == VB_MIXED && n > MIXED_SPLIT_MIN_N) {
+    // the other side small: its FP64 eigenproblem, then theta maps the
+    // vectors across (bond capacities within the one-site QR buffers' 112)
+    if ((left ? n2 : n1) <= MIXED_SPLIT_MIN_N && *std::max_element(s->bcap.begin(), s->bcap.end()) <= 112) {
+      VB_TRY(tdvp1_setup(s));
+      return split_small_side(s, left, n1, n2, o, dstA, dstC, k_out, disc);
+    }
+    if (o.m_max + 1 + 8 <= s->rcap) return split_mixed(s, left, mL, d1, d2, mR, m_old, o, dstA, dstC, k_out, disc);
+  }
   const cd *M = s->theta;
   GemmArgs g{};
   g.M = n; g.N = n; g.batch = 1;

@@ -72,3 +72,28 @@ def test_full_bond_dynamics_do_not_depend_on_the_site_order(P):
             mps.sweep(0.5, m_max=64, zero_floor=0.0)
             pe = vibronic.populations_from_vector(m, ex[k + 1])
             assert np.max(np.abs(mps.populations() - pe)) < 1e-9
+
+
+def test_mixed_split_from_the_small_side(P):
+    # the electronic site (d = 2) between modes with d = 12..16 at bonds 32:
+    # at its pairs one side of theta is 32 * 2 = 64 wide, the other up to
+    # 32 * 16 = 512, so the mixed form splits from the small side's Gram
+    # matrix and maps the vectors across (Cholesky QR twice)
+    base = vm.model_internal_conversion(seed=41, n_modes=5, level_range=(12, 16), n_offdiag=2, n_bilinear=4)
+    order = [0, 1, -1, 2, 3, 4]
+    m = dict(base, site_order=order)
+    dims = vm.local_dims(m)
+    e = order.index(-1)
+    assert max(32 * dims[e - 1], 32 * dims[e + 1]) > 192 and 32 * dims[e] <= 192
+    ts = vm.random_right_canonical_mps(78, dims, 32)
+    mps = P.Mps(P.Mpo(m), m_cap=32, dtype=P.VB_MIXED, tensors=ts)
+    ref = otdvp.Tdvp2(otdvp.MPS(ts), ompo.build_mpo(m), otdvp.TdvpOptions(m_max=32, eps=1e-8))
+    for _ in range(4):
+        st = mps.sweep(0.5, m_max=32, eps=1e-8, krylov_tol=1e-10)
+        ref.step(0.5)
+        assert st.noconv == 0
+        assert np.max(np.abs(mps.populations() - otdvp.populations(ref.mps, e))) < POP_TOL_MIXED
+    # every site right of the center stays right-orthonormal
+    for B in mps.tensors()[1:]:
+        Bm = B.reshape(B.shape[0], -1)
+        assert np.max(np.abs(Bm @ Bm.conj().T - np.eye(B.shape[0]))) < 1e-11
