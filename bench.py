@@ -442,6 +442,59 @@ def run_kernel_case(args):
     return 0
 
 
+def run_order_case(args):
+    """Site ordering (Sec. 3.1): the workload on the default order, the
+    orders the cost-model search picks under three weightings and the rule of
+    thumb, each from a random state at its saturated bonds (one warm-up step,
+    --steps timed, per-phase events on one call in PROF_EVERY). One JSON line."""
+    import torch
+    from paper_1908_10588_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1908_10588_gb300 as P
+    dtype = P.VB_MIXED if args.dtype == "mixed" else P.VB_FP64
+    model = vm.model_internal_conversion()
+    sweep_kw = dict(m_max=M_MAX, eps=EPS, zero_floor=1e-14, krylov_max=30, krylov_tol=1e-13)
+    st = torch.cuda.current_stream()
+    cands = [("default", None), ("search w=(1,1,1)", P.site_order_search(model, m_max=M_MAX)[0]),
+             ("search w=(1,1,0)", P.site_order_search(model, m_max=M_MAX, w_coupling=0)[0]),
+             ("search w=(0,1,0)", P.site_order_search(model, m_max=M_MAX, w_flops=0, w_coupling=0)[0]),
+             ("rule of thumb, 4 strong modes", P.site_order_rule(model, 4))]
+    c0 = P.site_order_cost(model, None, m_max=M_MAX)[0]
+    rows = []
+    for name, order in cands:
+        m = model if order is None else dict(model, site_order=order)
+        ts = vm.random_right_canonical_mps(STATE_SEED, vm.local_dims(m), M_MAX)
+        mps = P.Mps(P.Mpo(m), m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=st, tensors=ts)
+        mps.sweep(DT_FS, **sweep_kw)
+        torch.cuda.synchronize()
+        P.vb_profile_read(reset=True)
+        P.vb_profile_enable(True, every=PROF_EVERY)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            mps.sweep(DT_FS, **sweep_kw)
+        e1.record(st)
+        torch.cuda.synchronize()
+        P.vb_profile_enable(False)
+        pr = P.vb_profile_read(reset=True)
+        c = P.site_order_cost(model, order, m_max=M_MAX)[0]
+        rows.append({"order_name": name, "order": order if order is not None else "electronic site first",
+                     "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                     "predicted_vs_default": {"heff_flops": c["heff_flops"] / c0["heff_flops"],
+                                              "tensor_elems": c["tensor_elems"] / c0["tensor_elems"],
+                                              "coupling_dist": c["coupling_dist"] / c0["coupling_dist"],
+                                              "max_mpo_bond": c["max_w"]},
+                     "phases_ms_per_step": {k: round(pr[k]["ms"] / args.steps, 2) for k in
+                                            ("heff2", "heff1", "krylov", "split", "env", "merge",
+                                             "split_subspace_products", "split_subspace_orth",
+                                             "split_rayleigh_ritz", "split_rho", "split_out")},
+                     "subspace_iterations_per_step": pr["split_subspace_products"]["calls"] / args.steps,
+                     "populations": [float(x) for x in mps.populations()]})
+        mps.close()
+    print(json.dumps({"case": "site_order", "workload": WORKLOAD, "steps": args.steps, "orders": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,9 +509,12 @@ def main():
     ap.add_argument("--no-tdvp1", action="store_true")
     ap.add_argument("--no-order-search", action="store_true")
     ap.add_argument("--kernel-case", default=None, choices=[None, "heff2"])
+    ap.add_argument("--order-case", action="store_true")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.order_case:
+        return run_order_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
