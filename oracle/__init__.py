@@ -15,6 +15,8 @@ Modules
             (Eqs. one-site Hamiltonian 1, two-site Hamiltonian), Krylov
             exponential (Eq. Krylov subspace), truncated split (Sec. 2.1.1,
             DBSS), the symmetric 2TDVP sweep (Sec. 2.1.2) and observables
+  global_krylov  MPO x MPS application, MPS compression and sums, the global
+            Krylov time step and pre-steps before one-site TDVP (Sec. 2.1.2)
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: dense projections, library routines (scipy expm/eigh/SVD), closed
