@@ -460,6 +460,8 @@ def run_order_case(args):
              ("search w=(0,1,0)", P.site_order_search(model, m_max=M_MAX, w_flops=0, w_coupling=0)[0]),
              ("rule of thumb, 4 strong modes", P.site_order_rule(model, 4))]
     c0 = P.site_order_cost(model, None, m_max=M_MAX)[0]
+    if args.order_growth > 0:
+        return _order_growth(args, P, model, cands[:2] + cands[-1:], sweep_kw, st, dtype)
     rows = []
     for name, order in cands:
         m = model if order is None else dict(model, site_order=order)
@@ -495,6 +497,34 @@ def run_order_case(args):
     return 0
 
 
+def _order_growth(args, P, model, cands, sweep_kw, st, dtype):
+    """Bond growth under DBSS from the product state |upper state> x |0..0>
+    (Sec. 3.1): --order-growth steps on each chain order, every step timed
+    with CUDA events; bonds and populations along the way."""
+    import torch
+    rows = []
+    for name, order in cands:
+        m = model if order is None else dict(model, site_order=order)
+        mps = P.Mps(P.Mpo(m), vm.product_state_indices(m), m_cap=M_MAX, dtype=dtype, krylov_cap=40, stream=st)
+        ms, bonds, pops, disc = [], [], [], 0.0
+        for _ in range(args.order_growth):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sg = mps.sweep(DT_FS, **sweep_kw)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            bonds.append(max(mps.bond_dims()))
+            pops.append(float(mps.populations()[0]))
+            disc += sg.discarded_weight
+        rows.append({"order_name": name, "total_ms": sum(ms), "ms_per_step": [round(x, 1) for x in ms],
+                     "max_bond_per_step": bonds, "population_0_per_step": pops, "discarded_weight_sum": disc})
+        mps.close()
+    print(json.dumps({"case": "site_order_growth", "workload": WORKLOAD, "start": "product state",
+                      "steps": args.order_growth, "orders": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,6 +540,7 @@ def main():
     ap.add_argument("--no-order-search", action="store_true")
     ap.add_argument("--kernel-case", default=None, choices=[None, "heff2"])
     ap.add_argument("--order-case", action="store_true")
+    ap.add_argument("--order-growth", type=int, default=0)
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
