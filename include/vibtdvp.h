@@ -220,8 +220,9 @@ typedef struct {
   double w_size;
   double w_coupling;
   int iters;                /* search: 0 = every order for n <= 8 sites, else
-                               20000 annealing moves; > 0 = that many moves;
-                               < 0 = every order (n <= 10) */
+                               max(2000, 20000 * min(n, 32) / n) annealing
+                               moves; > 0 = that many moves; < 0 = every
+                               order (n <= 10) */
   unsigned long long seed;  /* annealing random stream */
   int n_strong;             /* modes the rule of thumb places around the
                                electronic site (0 = 4) */

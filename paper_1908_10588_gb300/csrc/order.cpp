@@ -26,7 +26,8 @@
 //    so J = 1 for that order.
 //
 // Search: all orders for chains of up to 8 sites, else simulated annealing
-// (swap, segment reversal and single-site moves; geometric cooling) started
+// (swap, segment reversal and single-site moves; geometric cooling; 20000
+// moves up to 32 sites, proportionally fewer beyond, at least 2000) started
 // from the better of the default order and the paper's rule of thumb.
 #include <algorithm>
 #include <cmath>
@@ -393,7 +394,9 @@ vb_status vb_site_order_search(const vb_model *model, const vb_order_opts *opts,
   const int n_strong = opts && opts->n_strong > 0 ? opts->n_strong : 4;
   uint64_t rng = opts ? opts->seed : 0;
   if (iters < 0 && n > 10) return fail(VB_EINVAL, std::string(who) + ": exhaustive search needs <= 10 sites");
-  if (iters == 0) iters = n <= 8 ? -1 : 20000;
+  // default: every order up to 8 sites; else 20000 moves, fewer on long
+  // chains (one evaluation costs O(terms x chain length))
+  if (iters == 0) iters = n <= 8 ? -1 : std::max(2000, (int)(20000LL * std::min(n, 32) / n));
 
   std::vector<uint64_t> keys;
   std::vector<std::pair<uint64_t, uint64_t>> blk;

@@ -206,3 +206,18 @@ def test_order_calls_reject_bad_arguments(P):
         P.site_order_cost(m, None, w_flops=-1)
     with pytest.raises(P.VbError):
         P.site_order_search(vm.model_internal_conversion(n_modes=12), iters=-1)
+
+
+def test_chains_of_one_and_two_sites(P):
+    m0 = _hand_model(2, [], [])
+    assert P.site_order_rule(m0, 4) == [-1]
+    order, c = P.site_order_search(m0)
+    assert order == [-1] and c["objective"] == 1.0 and c["tensor_elems"] == 0
+    m1 = _hand_model(2, [0.1], [5], g1=[[[0.03, 0.01], [0.01, -0.03]]])
+    for order in ([-1, 0], [0, -1]):
+        _, bonds, blocks = P.site_order_cost(m1, order)
+        _, b2, bl2 = _builder_structure(P, m1, order)
+        assert bonds == b2 and blocks == bl2
+    order, c = P.site_order_search(m1)
+    assert sorted(order) == [-1, 0]
+    assert c["tensor_elems"] == 10  # one pair: 1 * 2 * 5 * 1
