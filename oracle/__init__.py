@@ -17,6 +17,8 @@ Modules
             DBSS), the symmetric 2TDVP sweep (Sec. 2.1.2) and observables
   global_krylov  MPO x MPS application, MPS compression and sums, the global
             Krylov time step and pre-steps before one-site TDVP (Sec. 2.1.2)
+  gradient  dP_k(t)/dg of the populations with respect to the linear
+            couplings (Duhamel formula in the eigenbasis; tiny systems)
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: dense projections, library routines (scipy expm/eigh/SVD), closed
