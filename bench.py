@@ -49,6 +49,9 @@ WORKLOAD = ("internal-conversion-like: 2 states + 24 modes (d 10-30, seed 1002),
 # GB300 FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 / bf16 tensor-core ratio
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# is now (profiles/); a kernel changed since its capture has no entry (null)
+TRAFFIC: dict = {}
 
 
 def _peaks():
@@ -116,12 +119,13 @@ def _clock_sampler_stop(proc, path, gpu_index):
     return out
 
 
-def _oracle_sample(model, tensors, budget_s: float):
-    """Time the CPU oracle on the first two-site updates of one sweep of the
-    same workload, growing the sample until about budget_s seconds are spent;
-    returns (sweeps/s extrapolated by update count, updates timed, seconds,
-    environment set-up seconds). The first updates sit at the chain end where
-    bonds are small, so the extrapolation overstates the oracle's speed."""
+def _oracle_sweep(model, tensors, n_slices: int = 1, warmup: int = 0):
+    """One whole 2TDVP time step (sweep) of the CPU oracle on the workload,
+    from the same bond-saturated state, cut into `n_slices` consecutive
+    slices of two-site updates (2 (n - 1) updates in all) that are timed
+    separately; together they time the complete sweep, nothing is
+    extrapolated. `warmup` untimed single updates on a copy come first.
+    Returns (slice seconds, updates per slice, environment set-up seconds)."""
     import copy
 
     from oracle import mpo as ompo
@@ -130,19 +134,39 @@ def _oracle_sample(model, tensors, budget_s: float):
     n = len(tensors)
     per_sweep = 2 * (n - 1)
     t0 = time.perf_counter()
-    base = otdvp.Tdvp2(otdvp.MPS([t.copy() for t in tensors]), W,
-                       otdvp.TdvpOptions(m_max=M_MAX, eps=EPS, krylov_max=30, krylov_tol=1e-13))
+    sim = otdvp.Tdvp2(otdvp.MPS([t.copy() for t in tensors]), W,
+                      otdvp.TdvpOptions(m_max=M_MAX, eps=EPS, krylov_max=30, krylov_tol=1e-13))
     setup = time.perf_counter() - t0
-    pairs, elapsed = 1, 0.0
-    while True:
-        sim = copy.deepcopy(base)
+    for _ in range(warmup):
+        copy.deepcopy(sim).step(DT_FS, max_pairs=1)
+    n_slices = max(1, min(n_slices, per_sweep))
+    bounds = [round(per_sweep * k / n_slices) for k in range(n_slices + 1)]
+    gen = sim.step_updates(DT_FS, otdvp.StepStats())
+    secs, counts = [], []
+    for k in range(n_slices):
+        cnt = bounds[k + 1] - bounds[k]
         t0 = time.perf_counter()
-        sim.step(DT_FS, max_pairs=pairs)
-        elapsed = time.perf_counter() - t0
-        if elapsed >= 0.5 * budget_s or pairs >= per_sweep:
-            break
-        pairs += 1
-    return (pairs / per_sweep) / elapsed, pairs, elapsed, setup
+        for _ in range(cnt):
+            next(gen)
+        secs.append(time.perf_counter() - t0)
+        counts.append(cnt)
+    for _ in gen:  # nothing left: the sweep is complete
+        pass
+    return secs, counts, setup
+
+
+def _cpu_info():
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
 
 
 def run_reference(args):
@@ -151,30 +175,54 @@ def run_reference(args):
         return 0
     model = vm.model_internal_conversion()
     tensors = vm.random_right_canonical_mps(STATE_SEED, vm.local_dims(model), M_MAX)
-    budget = max(4.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        _oracle_sample(model, tensors, min(budget, 2.0))
-    vals, pairs_l, secs = [], [], []
-    for _ in range(args.steps):
-        v, pairs, el, _ = _oracle_sample(model, tensors, budget)
-        vals.append(v)
-        pairs_l.append(pairs)
-        secs.append(el)
-    value = float(np.mean(vals))
-    cores = os.cpu_count()
+    secs, counts, _ = _oracle_sweep(model, tensors, n_slices=args.steps, warmup=args.warmup)
+    total = sum(secs)
+    value = 1.0 / total
+    steps = len(secs)
+    info = _cpu_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "first two-site updates of one sweep, extrapolated"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{pairs_l[-1]} of {2 * (len(tensors) - 1)} two-site updates of one "
-                                   f"sweep per step ({secs[-1]:.1f} s), extrapolated by update count"},
+        "config": {"workload": WORKLOAD,
+                   "step": f"one of {steps} consecutive slices of ONE complete oracle sweep "
+                           f"({sum(counts)} two-site updates); value = 1 sweep / summed slice time",
+                   "host": info},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["nproc"], "kind": "oracle",
+                         "sample": f"one complete sweep ({sum(counts)} two-site updates, {total:.1f} s) "
+                                   f"timed in {steps} consecutive slices, no extrapolation"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _trajectory_error(P, stream, dtype):
+    """Mixed (or FP64) form over the stored oracle trajectory of the reduced
+    internal-conversion model (8 modes, d 10..30, bond 64, DBSS 1e-8, from the
+    product state; tests/golden/ic8_trajectory.json, written by the oracle):
+    the largest population difference over all its steps."""
+    path = os.path.join(ROOT, "tests", "golden", "ic8_trajectory.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f)
+    m = vm.model_internal_conversion(seed=1002, n_modes=8, level_range=(10, 30), n_offdiag=2, n_bilinear=8)
+    if [int(x) for x in m["levels"]] != g["fingerprint"]["levels"]:
+        return None
+    mps = P.Mps(P.Mpo(m), vm.product_state_indices(m), m_cap=64, dtype=dtype, krylov_cap=40, stream=stream)
+    errs = []
+    t0 = time.perf_counter()
+    for pops in g["populations"]:
+        mps.sweep(g["dt_fs"], m_max=g["m_max"], eps=g["eps"], zero_floor=g["zero_floor"], krylov_max=30,
+                  krylov_tol=g["krylov_tol"])
+        errs.append(float(np.max(np.abs(mps.populations() - np.array(pops)))))
+    wall = time.perf_counter() - t0
+    mps.close()
+    return {"model": g["model"], "steps": len(errs), "fs": len(errs) * g["dt_fs"],
+            "max_pop_err_vs_oracle": max(errs), "pop_err_vs_oracle_last_step": errs[-1],
+            "oracle_bond_max": max(g["bonds"][-1]), "wall_s": round(wall, 2)}
 
 
 def run_ours(args):
@@ -330,27 +378,51 @@ def run_ours(args):
         }
         mso.close()
 
-    # ---- roofline of the H_eff products
+    # ---- rooflines. The metric's H_eff TFLOP/s is the whole product (all its
+    # kernels); `roofline` is its dominant kernel alone: in the mixed form the
+    # tcgen05 GEMM of the two dense legs (tensor pipe), in the FP64 form the
+    # FP64 complex GEMM of the same legs (FP64 FMA pipe)
     peaks, src = _peaks()
     h2 = prof["heff2"]
     heff_ms = h2["ms"] + prof["heff1"]["ms"]
     heff_flops = h2["flops"] + prof["heff1"]["flops"]
     achieved = heff_flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else 0.0
+    events = f"CUDA events on 1 of every {PROF_EVERY} calls of each phase in the timed region, times scaled"
     if dtype == P.VB_FP64:
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz (nominal)"}
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz (nominal)",
+                "kernel": "H_eff products (two- and one-site), algorithmic flops / event time"}
+        roof_legs = None
     else:
         pk = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk, "traffic": None,
-                "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio (tf32 pipe)",
-                "useful_ceiling_split_tf32": pk / 3.0, "frac_of_useful_ceiling": achieved / (pk / 3.0)}
-    roof["kernel"] = "H_eff products (two- and one-site), algorithmic flops / event time"
-    roof["events"] = f"CUDA events on 1 of every {PROF_EVERY} calls of each phase in the timed region, times scaled"
+        tc = prof["heff_tc_legs"]
+        tc_ach = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else 0.0
+        roof = {"bound": "tensor", "achieved": tc_ach, "peak": pk, "unit": "TFLOP/s", "frac": tc_ach / pk,
+                "traffic": TRAFFIC.get("tc_gemm_tf32_kernel"),
+                "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio (tf32 pipe), of measured",
+                "useful_ceiling_split_tf32": pk / 3.0, "frac_of_useful_ceiling": tc_ach / (pk / 3.0),
+                "kernel": "tc_gemm_tf32_kernel (tcgen05 kind::tf32, split-TF32 x3): the dense L and R legs of "
+                          "every H_eff product; useful complex flops 8|theta|(mL wL + mR wR) / event time",
+                "launches_per_step": tc["calls"] / args.steps, "ms_per_step": tc["ms"] / args.steps,
+                "ms_per_launch": tc["ms"] / max(1, tc["calls"])}
+        wl = prof["heff_sparse_legs"]
+        w_gbs = wl["bytes"] / (wl["ms"] / 1e3) / 1e9 if wl["ms"] > 0 else 0.0
+        roof_legs = {
+            "sparse_mpo_legs": {"bound": "hbm", "achieved": w_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                "frac": w_gbs / peaks["hbm_gbs"], "traffic": TRAFFIC.get("sparse_legs"),
+                                "kernel": "sparse MPO legs (FP32, CUDA cores); algorithmic bytes = one read of "
+                                          "each leg's input and one write of its output",
+                                "ms_per_step": wl["ms"] / args.steps, "launches_per_step": wl["calls"] / args.steps},
+            "operand_prep_ms_per_step": prof["heff_prep"]["ms"] / args.steps,
+            "heff_products": {"achieved": achieved, "unit": "TFLOP/s", "frac_of_tf32_peak": achieved / pk,
+                              "frac_of_useful_ceiling": achieved / (pk / 3.0),
+                              "kernel": "whole H_eff products (all legs, prep and reductions)"},
+        }
+    roof["events"] = events
     roof["heff_calls"] = h2["calls"] + prof["heff1"]["calls"]
     roof["heff_ms_per_call"] = heff_ms / max(1, roof["heff_calls"])
-    # second roofline: the Krylov vector work (the largest phase), FP64 ALU-bound
+    # the Krylov vector work (the largest phase), FP64 ALU-bound
     kr = prof["krylov"]
     kr_ach = kr["flops"] / (kr["ms"] / 1e3) / 1e12 if kr["ms"] > 0 else 0.0
     roof_krylov = {"bound": "alu", "achieved": kr_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -371,6 +443,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}",
                    "l2": "per-step working set (Krylov basis ~0.8 GB) exceeds L2"},
         "roofline": roof,
+        "roofline_legs": roof_legs,
         "roofline_krylov": roof_krylov,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -388,15 +461,21 @@ def run_ours(args):
     }
     if compare is not None:
         line["fp64_form"] = compare
+    if not args.no_trajectory:
+        tr = _trajectory_error(P, stream, dtype)
+        if tr is not None:
+            line["trajectory_error"] = tr
     if tdvp1 is not None:
         line["tdvp1"] = tdvp1
     if order_line is not None:
         line["site_order_search"] = order_line
     if rank == 0 and not args.no_cpu_baseline:
-        v, pairs, el, _ = _oracle_sample(model, tensors, args.cpu_budget)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{pairs} of {2 * (len(dims) - 1)} two-site updates of one sweep "
-                                          f"({el:.1f} s), extrapolated by update count"}
+        secs, counts, _ = _oracle_sweep(model, tensors, n_slices=1, warmup=1)
+        info = _cpu_info()
+        line["cpu_baseline"] = {"value": 1.0 / sum(secs), "unit": UNIT, "cores": info["nproc"], "kind": "oracle",
+                                "sample": f"one complete sweep of the same workload from the same state "
+                                          f"({sum(counts)} two-site updates, {sum(secs):.1f} s), timed whole",
+                                "host": info}
     if rank == 0:
         print(json.dumps(line), flush=True)
     mps.close()
@@ -533,7 +612,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-trajectory", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tdvp1", action="store_true")

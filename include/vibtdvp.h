@@ -138,9 +138,19 @@ int mps_n_sites(const vb_mps *mps);
 vb_status mps_bond_dims(const vb_mps *mps, int *host_out /* [n-1] */);
 /* complex double [m_{p-1}][d_p][m_p] of site p copied to host_out */
 vb_status mps_get_site(const vb_mps *mps, int site, double *host_out);
+/* The same tensor copied device to device into dev_out (caller-owned device
+ * memory of at least m_{p-1} d_p m_p complex doubles), the bridge to tensors
+ * of a host framework (e.g. torch) without a host round trip. The copy runs
+ * on the handle's stream; when `stream` (cudaStream_t) is another stream the
+ * handle's stream is synchronised before returning, so dev_out is ready for
+ * work queued on `stream` afterwards. */
+vb_status mps_get_tensor(const vb_mps *mps, int site, double *dev_out, void *stream);
 
 /* ---- one 2TDVP time step (Sec. 2.1.2): left-to-right half sweep with
- * dt/2 then right-to-left half sweep with dt/2; the center returns to site 0. */
+ * dt/2 then right-to-left half sweep with dt/2; the center returns to site 0.
+ * Mixed form: a tensor-core kernel whose bounded wait ran out raises a flag
+ * on the device; the sweep (and tdvp1_sweep) reads it at its end, returns
+ * VB_ETIMEOUT (the state is then invalid) and clears the flag. */
 vb_status tdvp2_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts,
                       vb_sweep_stats *stats /* nullable */);
 
@@ -174,6 +184,20 @@ vb_status measure_populations(const vb_mps *mps, double *pop_host /* [n_el] */);
  * Sec. 3.1 (Eq. autocorrelation). Temporaries (two m x m blocks and one
  * m x d x m block) come from a's allocator. */
 vb_status mps_overlap(const vb_mps *a, const vb_mps *b, double *out_host /* [2] */);
+
+/* Spectrum from the autocorrelation function (Sec. 3.1: the pyrazine
+ * spectra are the Fourier transform of C(t) damped by exp(-|t|/tau)):
+ *   I(E) = 1/(pi hbar) Re sum_k w_k C(k dt) exp(+i E k dt/hbar) exp(-k dt/tau)
+ * with trapezoidal weights w_k = dt (dt/2 for k = 0 and k = n_t - 1): the
+ * half-axis integral, whose real part is half the transform over the whole
+ * time axis since C(-t) = conj C(t); a stationary state exp(-i E0 t/hbar)
+ * gives a unit-area Lorentzian of half-width hbar/tau at E0 (long records).
+ * c_t: device, n_t complex doubles C(0), C(dt), ... (e.g. from mps_overlap
+ * after every step); energies: device [n_e] eV; out: device [n_e]. dt_fs,
+ * tau_fs > 0. Complex FP64, one kernel on `stream` (cudaStream_t); no host
+ * synchronisation, no allocation. */
+vb_status vb_spectrum(const double *c_t, int n_t, double dt_fs, double tau_fs, const double *energies,
+                      int n_e, double *out, void *stream);
 
 /* Energy <psi|H|psi> / <psi|psi> in eV, H the MPO the state was created for
  * (Eq. vibronic Hamiltonian): left environments contracted over the whole
@@ -285,7 +309,10 @@ size_t vb_env_work_elems(const vb_mpo *mpo, int site, int mL, int mR);
  * row-major; destroyed). Householder reduction to tridiagonal form,
  * bisection for the k_want largest eigenvalues, inverse iteration and back
  * transformation. evals: [k_want] descending (device); evecs: [k_vec][n]
- * (device, row j = eigenvector j); k_vec <= k_want. work: >= vb_eig_work_bytes(n, k_want). */
+ * (device, row j = eigenvector j); k_vec <= k_want. work: >= vb_eig_work_bytes(n, k_want).
+ * Synchronises `stream` before returning: the cooperative reduction used for
+ * 64 < n <= 256 has a bounded grid barrier whose error word is read back, and
+ * a barrier that ran out returns VB_ETIMEOUT (evals / evecs then invalid). */
 vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *evals,
                           double *evecs, void *work, void *stream);
 size_t vb_eig_work_bytes(int n, int k_want);
@@ -300,12 +327,22 @@ size_t vb_eig_work_bytes(int n, int k_want);
  * The caller still owns rho (destroyed), evals and evecs. The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * The address lookup itself is safe from several host threads at once.
  * All calls share the one array: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * The array keeps the previous call's contents; the solver writes every
- * entry it reads, so nothing needs clearing. */
+ * entry it reads, so nothing needs clearing. Like vb_herm_eig_top the call
+ * synchronises `stream` and returns VB_ETIMEOUT when a grid barrier of the
+ * reduction ran out. */
 vb_status vb_herm_eig_top_noalloc(int n, double *rho, int k_want, int k_vec, double *evals,
                                   double *evecs, void *stream);
+
+/* Test hook of the failure path (the paper has no counterpart): sets the
+ * device flag of a mixed-form handle that a tensor-core kernel raises when a
+ * bounded wait runs out, exactly as that kernel would, without any fault. The
+ * next tdvp2_sweep / tdvp1_sweep must then return VB_ETIMEOUT and clear it.
+ * VB_EINVAL for an FP64-form handle. */
+vb_status vb_test_raise_wait_flag(vb_mps *mps);
 
 /* ---- measurement (not part of the method; the paper has no counterpart).
  * Number of CUDA kernels this library has launched since it was loaded. */
@@ -323,7 +360,12 @@ unsigned long long vb_kernel_launches(void);
  * basis, projection and weights), and 18 / 19 the Cholesky kernels and the
  * Gram and transform products of the orthonormalisations; 12, 13, 14 are the
  * inverse iteration, Gram-Schmidt and back-transformation parts of every
- * eigenvector stage). heff_flops[c] counts the algorithmic
+ * eigenvector stage; inside the mixed-form H_eff products 20 = the tcgen05
+ * legs (L and R contractions, incl. their split-K reductions), 21 = the
+ * sparse MPO legs, 22 = the operand preparation). flops[p] / bytes[p] are
+ * the algorithmic work of every call of phase p (20: the useful complex
+ * flops of the two dense legs; 21: one read of each leg's input and one write
+ * of its output, FP32; 0 where not counted). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
  * multiply-add is 8, real-times-complex 4, an identity-block add 2);
  * krylov_flops counts the FP64 operations of the Krylov vector work (phase
@@ -340,6 +382,8 @@ typedef struct {
   long long calls[24];
   double heff_flops[2];
   double krylov_flops;
+  double flops[24];
+  double bytes[24];
 } vb_profile;
 vb_status vb_profile_enable(int every);
 vb_status vb_profile_read(vb_profile *out, int reset);

@@ -296,15 +296,20 @@ class Tdvp2:
         two-site updates (a bounded timing sample; the state is then left
         mid-sweep and the step is not complete)."""
         st = StepStats()
-        done = 0
+        for done, _ in enumerate(self.step_updates(dt_fs, st)):
+            if max_pairs is not None and done + 1 >= max_pairs:
+                break
+        return st
+
+    def step_updates(self, dt_fs: float, st: StepStats):
+        """The time step of `step` as a generator that yields after every
+        two-site update (2 (n - 1) of them), so that a caller can time the
+        sweep in consecutive slices; the step is complete once it is exhausted."""
         A, W, L, R = self.mps.A, self.W, self.L, self.R
         n = self.mps.n
         tau = 0.5 * dt_fs
         # left to right
         for i in range(n - 1):
-            if max_pairs is not None and done >= max_pairs:
-                return st
-            done += 1
             theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
             Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
             theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
@@ -315,11 +320,9 @@ class Tdvp2:
                 L1, W1, R1 = L[i + 1], W[i + 1], R[i + 2]
                 C = self._evolve(lambda x: heff1_apply(L1, W1, R1, x), C, -tau, st)
             A[i + 1] = C
+            yield i
         # right to left
         for i in range(n - 2, -1, -1):
-            if max_pairs is not None and done >= max_pairs:
-                return st
-            done += 1
             theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
             Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
             theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
@@ -330,10 +333,14 @@ class Tdvp2:
                 L0, W0, R0 = L[i], W[i], R[i + 1]
                 C = self._evolve(lambda x: heff1_apply(L0, W0, R0, x), C, -tau, st)
             A[i] = C
-        self.mps.center = 0
-        st.max_bond = max(self.mps.bond_dims()) if n > 1 else 1
-        self.time += dt_fs
-        return st
+            if i == 0:
+                self.mps.center = 0
+                st.max_bond = max(self.mps.bond_dims())
+                self.time += dt_fs
+            yield i
+        if n < 2:
+            st.max_bond = 1
+            self.time += dt_fs
 
 
 class Tdvp1:

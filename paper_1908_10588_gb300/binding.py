@@ -27,6 +27,7 @@ EXPORTED = [
     "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
     "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc", "mps_overlap", "mps_energy",
     "tdvp2_sweep_batched", "tdvp1_sweep", "vb_site_order_cost", "vb_site_order_search", "vb_site_order_rule",
+    "mps_get_tensor", "vb_test_raise_wait_flag", "vb_spectrum",
 ]
 
 
@@ -60,13 +61,13 @@ class vb_tdvp_opts(C.Structure):
 
 class vb_profile(C.Structure):
     _fields_ = [("ms", C.c_double * 24), ("calls", C.c_longlong * 24), ("heff_flops", C.c_double * 2),
-                ("krylov_flops", C.c_double)]
+                ("krylov_flops", C.c_double), ("flops", C.c_double * 24), ("bytes", C.c_double * 24)]
 
 
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
           "split_out", "split_subspace_products", "split_subspace_orth", "eigvec_invit", "eigvec_gram_schmidt",
           "eigvec_backtransform", "split_rayleigh_ritz", "split_ritz_fp32", "split_ritz_fp64",
-          "split_orth_cholesky", "split_orth_products"]
+          "split_orth_cholesky", "split_orth_products", "heff_tc_legs", "heff_sparse_legs", "heff_prep"]
 
 
 class vb_order_opts(C.Structure):
@@ -109,6 +110,9 @@ def lib():
         "mps_n_sites": (i, [vp]),
         "mps_bond_dims": (i, [vp, C.POINTER(i)]),
         "mps_get_site": (i, [vp, i, vp]),
+        "mps_get_tensor": (i, [vp, i, vp, vp]),
+        "vb_test_raise_wait_flag": (i, [vp]),
+        "vb_spectrum": (i, [vp, i, d, d, vp, i, vp, vp]),
         "tdvp2_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
         "measure_populations": (i, [vp, vp]),
         "tdvp1_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
@@ -291,6 +295,21 @@ class Mps:
     def tensors(self):
         return [self.site(p) for p in range(self.n_sites)]
 
+    def site_shape(self, p: int):
+        b = [1] + self.bond_dims() + [1]
+        return (b[p], self.mpo.site_dims(p)[1], b[p + 1])
+
+    def get_tensor(self, p: int, out, stream=None):
+        """Copy site p device to device into `out` (a caller-owned device
+        buffer, e.g. a complex128 torch tensor of `site_shape(p)`), mps_get_tensor."""
+        check(lib().mps_get_tensor(self.h, p, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def raise_wait_flag(self):
+        """Test hook: set the device flag a timed-out tensor-core wait raises
+        (vb_test_raise_wait_flag); the next sweep returns VB_ETIMEOUT."""
+        check(lib().vb_test_raise_wait_flag(self.h))
+
     def sweep(self, dt_fs: float, m_max: int, eps: float = 0.0, zero_floor: float = 1e-14,
               krylov_max: int = 30, krylov_tol: float = 1e-13, on_noconv: int = 0):
         o = vb_tdvp_opts(m_max, eps, zero_floor, krylov_max, krylov_tol, on_noconv)
@@ -399,6 +418,13 @@ def vb_herm_eig_top(n, rho, k_want, k_vec, evals, evecs, work, stream=None):
                                 _stream_ptr(stream)))
 
 
+def vb_spectrum(c_t, n_t, dt_fs, tau_fs, energies, n_e, out, stream=None):
+    """Damped Fourier transform of C(t) (device buffers: c_t complex128 [n_t],
+    energies float64 [n_e], out float64 [n_e])."""
+    check(lib().vb_spectrum(_ptr(c_t), int(n_t), float(dt_fs), float(tau_fs), _ptr(energies), int(n_e),
+                            _ptr(out), _stream_ptr(stream)))
+
+
 def vb_kernel_launches() -> int:
     return int(lib().vb_kernel_launches())
 
@@ -412,7 +438,8 @@ def vb_profile_enable(on=True, every: int = 1):
 def vb_profile_read(reset: bool = True) -> dict:
     p = vb_profile()
     check(lib().vb_profile_read(C.byref(p), int(reset)))
-    out = {name: {"ms": p.ms[k], "calls": int(p.calls[k])} for k, name in enumerate(PHASES)}
+    out = {name: {"ms": p.ms[k], "calls": int(p.calls[k]), "flops": p.flops[k], "bytes": p.bytes[k]}
+           for k, name in enumerate(PHASES)}
     out["heff2"]["flops"] = p.heff_flops[0]
     out["heff1"]["flops"] = p.heff_flops[1]
     out["krylov"]["flops"] = p.krylov_flops

@@ -42,10 +42,11 @@ void count_launch();
 enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5, PH_RHO = 6, PH_EIGVAL = 7,
        PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_SUBPROD = 10, PH_SUBORTH = 11, PH_INVIT = 12,
        PH_CGS = 13, PH_BACKT = 14, PH_RR = 15, PH_RR32 = 16, PH_RR64 = 17, PH_CHOL = 18,
-       PH_ORTHGEMM = 19, PH_COUNT = 24 };
+       PH_ORTHGEMM = 19, PH_TC = 20, PH_WLEG = 21, PH_PREP = 22, PH_COUNT = 24 };
 bool prof_on();
 void prof_begin(int phase, cudaStream_t st);
-void prof_end(int phase, cudaStream_t st, double flops);
+// flops / bytes: algorithmic work of the call, summed per phase
+void prof_end(int phase, cudaStream_t st, double flops, double bytes = 0.0);
 void prof_collect();  // after a stream synchronisation: fold finished events into the totals
 
 inline vb_status fail(vb_status s, const std::string &msg) {
@@ -236,8 +237,16 @@ vb_status wapply(const MpoSite &site, int dir, const cplx<R> *X, WStrides xs, lo
 vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long long n, cd *out,
                         cd *partial, int n_part, cudaStream_t st, unsigned int *cnt = nullptr);
 // w -= sum_j c[j] V[j] (sign = -1) or w += ... (sign = +1); c on device; cscale applied
+// w32 (nullable): also write the FP32 copy of the result
 vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
-                         long long n, cudaStream_t st);
+                         long long n, cudaStream_t st, cf *w32 = nullptr);
+// the full Gram-Schmidt pass of the mixed form on FP32 copies of the Krylov
+// vectors (FP32 products, FP64 sums; cnt: zeroed group counters as for
+// vec_multi_dot, required) and its update of the FP64 w followed by |w|
+vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cf *w, long long n, cd *out, cd *partial,
+                          int n_part, cudaStream_t st, unsigned int *cnt);
+vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
+                                double *out, double *partial, cudaStream_t st, unsigned int *cnt);
 // ------------------------------------------------------------ subspace iteration
 struct SubspaceWork {
   cf *G, *W, *T;  // r x r Gram matrix, r x r transform, r x n scratch rows
@@ -275,8 +284,10 @@ vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int 
                     cudaStream_t st);
 // x *= 1/ (*nrm) (device scalar; a zero norm gives zero); keep (nullable):
 // *keep = *nrm; alpha_k (nullable): *alpha_k = Re *c + Re *c2
+// shadow (nullable): also write the FP32 copy of the scaled vector
 vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep = nullptr,
-                        const cd *c = nullptr, const cd *c2 = nullptr, double *alpha_k = nullptr);
+                        const cd *c = nullptr, const cd *c2 = nullptr, double *alpha_k = nullptr,
+                        cf *shadow = nullptr);
 // y = s * x with s = *num / *den (device scalars; den may be null -> 1)
 vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st);
 // combine: y = (*nrm) * sum_j u[j] V[j]

@@ -17,6 +17,8 @@
 //  5. Back-transformation z = Q D y.
 #include <algorithm>
 
+#include <atomic>
+
 #include "common.h"
 
 namespace vb {
@@ -1000,24 +1002,28 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = 3u << 20;  // 3 MiB
 
 static __device__ __align__(256) unsigned char g_eig_scratch[NOALLOC_SCRATCH_BYTES];
 
-// device address of g_eig_scratch, looked up once per device
+// device address of g_eig_scratch, looked up once per device; atomic so that
+// host threads making their first call on one device at the same time do not
+// race (they look up and store the same address)
 constexpr int NOALLOC_MAX_DEVICES = 64;
-void *g_scratch_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::atomic<void *> g_scratch_addr[NOALLOC_MAX_DEVICES];
 
 vb_status scratch_address(void **out) {
   int dev = -1;
   VB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(VB_EINVAL, "noalloc eig: device ordinal out of range");
-  if (!g_scratch_addr[dev]) {
+  void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_eig_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return fail(VB_ECUDA, std::string("noalloc eig: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
     }
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev].store(p, std::memory_order_release);
+    addr = p;
   }
-  *out = g_scratch_addr[dev];
+  *out = addr;
   return VB_OK;
 }
 
@@ -1043,6 +1049,8 @@ extern "C" vb_status vb_herm_eig_top_noalloc(int n, double *rho, int k_want, int
   cudaStream_t st = (cudaStream_t)stream;
   VB_TRY(eig_values(n, (cd *)rho, k_want, evals, work, st));
   if (k_vec > 0) VB_TRY(eig_vectors(n, (cd *)rho, k_want, k_vec, evals, (cd *)evecs, work, st));
-  return VB_OK;
+  // a grid barrier of the reduction that ran out leaves its error word in the
+  // scratch array: report it before the next call clears it
+  return EigWork::check(n, k_want, sizeof(double), work, st);
 }
 

@@ -135,10 +135,11 @@ __global__ void reduce_parts_cd(const cd *__restrict__ partial, int n_part, int 
 // w[i] += sign * sum_j c[j] V_j[i], two elements per thread (four
 // independent FMA chains). With partial != nullptr each block also writes
 // the sum of |w_new[i]|^2 over its elements to partial[blockIdx.x].
+// With w32 != nullptr the kernel also writes the FP32 copy of w_new.
 __global__ void __launch_bounds__(256) multi_axpy_kernel(const cd *__restrict__ V, long long ldv, int nv,
                                                          const cd *__restrict__ c, double sign, cd *__restrict__ w,
                                                          long long n, double *__restrict__ partial,
-                                                         unsigned int *cnt, double *nrm_out) {
+                                                         unsigned int *cnt, double *nrm_out, cf *__restrict__ w32) {
   __shared__ cd cs[128];
   __shared__ double sh[8];
   for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = cscale(c[j], sign);
@@ -163,12 +164,14 @@ __global__ void __launch_bounds__(256) multi_axpy_kernel(const cd *__restrict__ 
     const cd o = w[i];
     const cd r = mkc(o.x + ax, o.y + ay);
     w[i] = r;
-    nn = fma(r.x, r.x, fma(r.y, r.y, nn));
+    if (w32) w32[i] = mkc((float)r.x, (float)r.y);
+    if (partial) nn = fma(r.x, r.x, fma(r.y, r.y, nn));
     if (two) {
       const cd o2 = w[i2];
       const cd r2 = mkc(o2.x + bx, o2.y + by);
       w[i2] = r2;
-      nn = fma(r2.x, r2.x, fma(r2.y, r2.y, nn));
+      if (w32) w32[i2] = mkc((float)r2.x, (float)r2.y);
+      if (partial) nn = fma(r2.x, r2.x, fma(r2.y, r2.y, nn));
     }
   }
   if (partial) {
@@ -224,7 +227,7 @@ __global__ void norm2_final(const double *__restrict__ partial, int n_part, doub
 }
 
 __global__ void scale_inv_kernel(cd *x, long long n, const double *nrm, double *keep, const cd *c, const cd *c2,
-                                 double *alpha_k) {
+                                 double *alpha_k, cf *shadow) {
   // a zero norm (Lanczos breakdown, zero input) gives a zero vector
   const double s = nrm[0] > 0.0 ? 1.0 / nrm[0] : 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -234,7 +237,156 @@ __global__ void scale_inv_kernel(cd *x, long long n, const double *nrm, double *
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     cd a = x[i];
-    x[i] = mkc(a.x * s, a.y * s);
+    const cd r = mkc(a.x * s, a.y * s);
+    x[i] = r;
+    if (shadow) shadow[i] = mkc((float)r.x, (float)r.y);
+  }
+}
+
+// ---- the full Gram-Schmidt pass of the mixed form on FP32 copies of the
+// Krylov vectors. The first pass (against v_{k-1} and v_k, FP64) has removed
+// the large components; what the full pass removes is of the size of the
+// FP32 error of the H_eff product (~1e-7 |w|), so its coefficients need only
+// a few correct digits: products and per-thread sums in FP32, the block and
+// final sums in FP64, and the correction sum_j c_j v_j (tiny) formed in FP32
+// and added to the FP64 vector. Half the bytes of the FP64 pass, no FP64
+// arithmetic beyond the sums and the norm.
+template <int JB>
+__device__ __forceinline__ void dot32_group(const cf *__restrict__ Vg, long long ldv, const cf *__restrict__ w,
+                                            long long i0, long long i1, double *sh, double *out2) {
+  float sx[JB], sy[JB];
+#pragma unroll
+  for (int j = 0; j < JB; ++j) sx[j] = sy[j] = 0.f;
+  for (long long i = i0 + threadIdx.x; i < i1; i += RT) {
+    const cf b = w[i];
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+      const cf a = Vg[j * ldv + i];
+      sx[j] = fmaf(a.x, b.x, fmaf(a.y, b.y, sx[j]));
+      sy[j] = fmaf(a.x, b.y, fmaf(-a.y, b.x, sy[j]));
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < JB; ++j) {
+    const double rx = warp_sum((double)sx[j]), ry = warp_sum((double)sy[j]);
+    if (lane == 0) {
+      sh[wid * 2 * DOT_JB + 2 * j] = rx;
+      sh[wid * 2 * DOT_JB + 2 * j + 1] = ry;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * JB) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < RT / 32; ++w2) s += sh[w2 * 2 * DOT_JB + threadIdx.x];
+    out2[threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V, long long ldv, int nv,
+                                                       const cf *__restrict__ w, long long n,
+                                                       cd *__restrict__ partial, unsigned int *cnt, cd *out) {
+  __shared__ double sh[(RT / 32) * 2 * DOT_JB];
+  __shared__ unsigned int s_ticket;
+  const int j0 = blockIdx.y * DOT_JB;
+  const int jn = min(DOT_JB, nv - j0);
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  const cf *Vg = V + j0 * ldv;
+  double *out2 = reinterpret_cast<double *>(partial + (long long)blockIdx.x * nv + j0);
+  switch (jn) {
+    case 8: dot32_group<8>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 7: dot32_group<7>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 6: dot32_group<6>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 5: dot32_group<5>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 4: dot32_group<4>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 3: dot32_group<3>(Vg, ldv, w, i0, i1, sh, out2); break;
+    case 2: dot32_group<2>(Vg, ldv, w, i0, i1, sh, out2); break;
+    default: dot32_group<1>(Vg, ldv, w, i0, i1, sh, out2); break;
+  }
+  // the last block of the group sums the partials in block order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&cnt[blockIdx.y], 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = wid; j < jn; j += RT / 32) {
+    double sx = 0.0, sy = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double2 p = __ldcg(reinterpret_cast<const double2 *>(partial + (long long)b * nv + j0 + j));
+      sx += p.x;
+      sy += p.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) out[j0 + j] = mkc(sx, sy);
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
+}
+
+// w[i] += sign * sum_j c[j] V32_j[i] (correction in FP32, w in FP64), then
+// |w| in FP64 by the last block (cnt: one zeroed counter)
+__global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__restrict__ V, long long ldv, int nv,
+                                                                const cd *__restrict__ c, double sign,
+                                                                cd *__restrict__ w, long long n,
+                                                                double *__restrict__ partial, unsigned int *cnt,
+                                                                double *nrm_out) {
+  __shared__ cf cs[128];
+  __shared__ double sh[8];
+  __shared__ unsigned int s_ticket;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = mkc((float)(sign * c[j].x), (float)(sign * c[j].y));
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double nn = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    const long long i2 = i + stride;
+    const bool two = i2 < n;
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+    for (int j = 0; j < nv; ++j) {
+      const cf cj = cs[j];
+      const cf v = V[j * ldv + i];
+      ax = fmaf(cj.x, v.x, fmaf(-cj.y, v.y, ax));
+      ay = fmaf(cj.x, v.y, fmaf(cj.y, v.x, ay));
+      if (two) {
+        const cf u = V[j * ldv + i2];
+        bx = fmaf(cj.x, u.x, fmaf(-cj.y, u.y, bx));
+        by = fmaf(cj.x, u.y, fmaf(cj.y, u.x, by));
+      }
+    }
+    const cd o = w[i];
+    const cd r = mkc(o.x + (double)ax, o.y + (double)ay);
+    w[i] = r;
+    nn = fma(r.x, r.x, fma(r.y, r.y, nn));
+    if (two) {
+      const cd o2 = w[i2];
+      const cd r2 = mkc(o2.x + (double)bx, o2.y + (double)by);
+      w[i2] = r2;
+      nn = fma(r2.x, r2.x, fma(r2.y, r2.y, nn));
+    }
+  }
+  nn = warp_sum(nn);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2];
+    partial[blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(cnt, 1u);
+  __syncthreads();
+  if (s_ticket == gridDim.x - 1 && threadIdx.x < 32) {
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(partial + b);
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+      nrm_out[0] = sqrt(t);
+      cnt[0] = 0u;
+    }
   }
 }
 
@@ -519,11 +671,31 @@ vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long lo
 }
 
 vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
-                         long long n, cudaStream_t st) {
+                         long long n, cudaStream_t st, cf *w32) {
   if (nv <= 0 || n == 0) return VB_OK;
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
   multi_axpy_kernel<<<grid_for((n + 1) / 2, 256), 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr, nullptr,
-                                                                 nullptr);
+                                                                 nullptr, w32);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cf *w, long long n, cd *out, cd *partial,
+                          int n_part, cudaStream_t st, unsigned int *cnt) {
+  if (nv <= 0) return VB_OK;
+  if (nv > 128 || (long long)n_part * nv > 512LL * 128 || !cnt)
+    return fail(VB_EINVAL, "multi_dot32: too many vectors or no counters");
+  multi_dot32_part<<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial, cnt, out);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
+                                double *out, double *partial, cudaStream_t st, unsigned int *cnt) {
+  if (nv > 128 || !cnt) return fail(VB_EINVAL, "multi_axpy32: more than 128 vectors or no counter");
+  if (nv <= 0 || n == 0) return vec_norm2(w, n, out, partial, reduce_parts(n), st);
+  const int blocks = (int)std::min<long long>(512, std::max<long long>(1, (n + 511) / 512));
+  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
@@ -533,7 +705,7 @@ vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, d
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
   if (nv <= 0 || n == 0) return vec_norm2(w, n, out, partial, reduce_parts(n), st);
   const int blocks = (int)std::min<long long>(512, std::max<long long>(1, (n + 511) / 512));
-  multi_axpy_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out);
+  multi_axpy_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out, nullptr);
   VB_CHECK_LAUNCH();
   if (!cnt) {
     norm2_final<<<1, 32, 0, st>>>(partial, blocks, out);
@@ -552,9 +724,9 @@ vb_status vec_norm2(const cd *x, long long n, double *out, double *partial, int 
 }
 
 vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, double *keep, const cd *c,
-                        const cd *c2, double *alpha_k) {
+                        const cd *c2, double *alpha_k, cf *shadow) {
   if (n == 0) return VB_OK;
-  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm, keep, c, c2, alpha_k);
+  scale_inv_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, nrm, keep, c, c2, alpha_k, shadow);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

@@ -26,6 +26,8 @@ struct Prof {
   double ms[PH_COUNT] = {0};
   long long calls[PH_COUNT] = {0};
   long long sampled[PH_COUNT] = {0};
+  double pflops[PH_COUNT] = {0};
+  double pbytes[PH_COUNT] = {0};
   double flops[2] = {0, 0};
   double krylov_flops = 0;
 } g_prof;
@@ -59,8 +61,10 @@ void prof_begin(int phase, cudaStream_t st) {
   g_prof.open_start[phase] = e;
 }
 
-void prof_end(int phase, cudaStream_t st, double flops) {
+void prof_end(int phase, cudaStream_t st, double flops, double bytes) {
   if (!g_prof.every) return;
+  g_prof.pflops[phase] += flops;
+  g_prof.pbytes[phase] += bytes;
   if (phase < 2) g_prof.flops[phase] += flops;
   if (phase == PH_KRYLOV) g_prof.krylov_flops += flops;
   if (g_prof.open_start.size() < PH_COUNT || !g_prof.open_start[phase]) return;
@@ -109,6 +113,8 @@ vb_status vb_profile_read(vb_profile *out, int reset) {
     const long long c = vb::g_prof.calls[i], k = vb::g_prof.sampled[i];
     out->ms[i] = k > 0 ? vb::g_prof.ms[i] * ((double)c / (double)k) : 0.0;
     out->calls[i] = c;
+    out->flops[i] = vb::g_prof.pflops[i];
+    out->bytes[i] = vb::g_prof.pbytes[i];
   }
   out->heff_flops[0] = vb::g_prof.flops[0];
   out->heff_flops[1] = vb::g_prof.flops[1];
@@ -119,6 +125,8 @@ vb_status vb_profile_read(vb_profile *out, int reset) {
       vb::g_prof.calls[i] = 0;
       vb::g_prof.sampled[i] = 0;
       vb::g_prof.seq[i] = 0;
+      vb::g_prof.pflops[i] = 0;
+      vb::g_prof.pbytes[i] = 0;
     }
     vb::g_prof.flops[0] = vb::g_prof.flops[1] = 0;
     vb::g_prof.krylov_flops = 0;

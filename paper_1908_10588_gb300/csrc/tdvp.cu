@@ -224,6 +224,7 @@ struct vb_mps {
   std::vector<int> bcap;   // capacity per bond
   std::vector<cd *> A, L, R;
   cd *theta = nullptr, *V = nullptr, *T1 = nullptr, *T2 = nullptr, *rho = nullptr, *Z = nullptr;
+  cf *V32 = nullptr, *w32 = nullptr;  // mixed form: FP32 copies of the Krylov vectors and of w
   void *eigw = nullptr;
   void *mixw = nullptr;
   size_t mixw_bytes = 0;
@@ -440,6 +441,20 @@ vb_status heff0_fp64(const vb_mpo *mpo, int site, int ma, int mb, const cd *L, c
   return zgemm(h, st);
 }
 
+// Reads the flag a mixed-form tensor-core kernel raises when one of its
+// bounded waits runs out, and clears it once reported, so that the error is
+// neither lost nor blamed on a later call. Synchronises the handle's stream.
+vb_status take_wait_flag(vb_mps *s, const char *who) {
+  if (s->dtype != VB_MIXED) return VB_OK;
+  int flag = 0;
+  VB_TRY_CUDA(cudaMemcpyAsync(&flag, s->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  if (!flag) return VB_OK;
+  VB_TRY_CUDA(cudaMemsetAsync(s->d_tcerr, 0, sizeof(int), s->st));
+  VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  return fail(VB_ETIMEOUT, std::string(who) + ": a tensor-core kernel's wait ran out (results invalid)");
+}
+
 vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
   if (op.two_site < 0)  // zero-site (bond) Hamiltonian: FP64 in both forms
     return heff0_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->inter_cap, s->q_ws, s->q_ws_elems,
@@ -474,10 +489,12 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
   cd *V = s->V;
   kmax = (int)std::min<long long>(std::min(kmax, s->kcap), N);
   const double tau = dt_fs / HBAR_EV_FS;
+  const bool mixed = s->dtype == VB_MIXED;
+  cf *V32 = mixed ? s->V32 : nullptr;
   prof_begin(PH_KRYLOV, st);
   VB_TRY(vec_norm2(x, N, s->d_nrm, s->d_part, np, st));
   VB_TRY(vec_copy_scaled(x, V, N, st));
-  VB_TRY(vec_scale_inv(V, N, s->d_nrm, st));
+  VB_TRY(vec_scale_inv(V, N, s->d_nrm, st, nullptr, nullptr, nullptr, nullptr, V32));
   // algorithmic FP64 flops: a complex multiply-add counts 8, |z|^2 counts 4
   const double Nd = (double)N;
   prof_end(PH_KRYLOV, st, 4.0 * Nd + 2.0 * Nd);
@@ -487,26 +504,36 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     cd *w = V + (k + 1) * ldv;
     VB_TRY(apply_heff(s, op, V + k * ldv, w));
     prof_begin(PH_KRYLOV, st);
-    if (s->dtype == VB_MIXED) {
-      // first pass against v_{k-1}, v_k only (the three-term recurrence),
+    double kbytes = 0.0;
+    if (mixed) {
+      // first pass against v_{k-1}, v_k only (the three-term recurrence, FP64),
       // then one full pass: the full pass then removes components that are
-      // already small, so it loses no orthogonality to cancellation
+      // already small (of the size of the FP32 error of the H_eff product),
+      // so it loses no orthogonality to cancellation and runs on the FP32
+      // copies of the vectors (FP32 products, FP64 sums and update)
       const int j0 = k > 0 ? k - 1 : 0;
-      VB_TRY(vec_multi_dot(V + j0 * ldv, ldv, k + 1 - j0, w, N, s->d_c + j0, s->d_partc, np, st, s->d_cnt));
-      VB_TRY(vec_multi_axpy(V + j0 * ldv, ldv, k + 1 - j0, s->d_c + j0, -1.0, w, N, st));
+      const int n1 = k + 1 - j0;
+      VB_TRY(vec_multi_dot(V + j0 * ldv, ldv, n1, w, N, s->d_c + j0, s->d_partc, np, st, s->d_cnt));
+      VB_TRY(vec_multi_axpy(V + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, st, s->w32));
+      VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
+      VB_TRY(vec_multi_axpy32_norm(V32, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st,
+                                   s->d_cnt + 32));
+      // algorithmic bytes: FP64 pass (read v's and w twice, write w and its
+      // FP32 copy), FP32 pass (read the copies twice, w32 once, w read and written)
+      kbytes = (double)N * (16.0 * (2 * n1 + 3) + 8.0 + 8.0 * (2 * (k + 1) + 1) + 32.0);
     } else {
       VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st, s->d_cnt));
       VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
+      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
+      VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st, s->d_cnt + 32));
     }
-    VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
-    VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st, s->d_cnt + 32));
 
     const bool check = k + 1 >= check_from || k + 1 == kmax;
     if (check)
       VB_TRY(tridiag_expm(s->d_c, s->d_c2, s->d_alpha, s->d_beta, k + 1, tau, s->d_bnext, s->d_u, s->d_flag, st));
     {
-      const double nv1 = s->dtype == VB_MIXED ? (double)(k > 0 ? 2 : 1) : (double)(k + 1);
-      prof_end(PH_KRYLOV, st, Nd * (16.0 * (nv1 + k + 1) + 4.0));
+      const double nv1 = mixed ? (double)(k > 0 ? 2 : 1) : (double)(k + 1);
+      prof_end(PH_KRYLOV, st, Nd * (16.0 * (nv1 + k + 1) + 4.0), kbytes);
     }
     kdim = k + 1;
     if (check) {
@@ -520,7 +547,8 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     }
     prof_begin(PH_KRYLOV, st);
     // v_{k+1} = w / beta_{k+1}; also records beta_{k+1} and alpha_k
-    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k, s->d_c + k, s->d_c2 + k, s->d_alpha + k));
+    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k, s->d_c + k, s->d_c2 + k, s->d_alpha + k,
+                         mixed ? V32 + (k + 1) * ldv : nullptr));
     prof_end(PH_KRYLOV, st, 2.0 * Nd);
   }
   *iters = kdim;
@@ -1030,6 +1058,10 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
     A2((void **)&s->R[n], sizeof(cd));
     A2((void **)&s->theta, s->theta_cap * sizeof(cd));
     A2((void **)&s->V, (size_t)(kcap + 1) * s->theta_cap * sizeof(cd));
+    if (s->dtype == VB_MIXED) {
+      A2((void **)&s->V32, (size_t)(kcap + 1) * s->theta_cap * sizeof(cf));
+      A2((void **)&s->w32, (size_t)s->theta_cap * sizeof(cf));
+    }
     A2((void **)&s->T1, s->inter_cap * sizeof(cd));
     A2((void **)&s->T2, s->inter_cap * sizeof(cd));
     const int nr = (int)s->nrho_cap;
@@ -1392,6 +1424,26 @@ vb_status mps_get_site(const vb_mps *s, int site, double *host_out) {
   return VB_OK;
 }
 
+vb_status mps_get_tensor(const vb_mps *s, int site, double *dev_out, void *stream) {
+  if (!s || !dev_out || site < 0 || site >= s->n) return fail(VB_EINVAL, "mps_get_tensor: bad argument");
+  VB_TRY(set_device_of(const_cast<vb_mps *>(s)));
+  size_t el = (size_t)s->bond[site] * s->dims[site] * s->bond[site + 1];
+  cudaStream_t dst = (cudaStream_t)stream;
+  VB_TRY_CUDA(cudaMemcpyAsync(dev_out, s->A[site], el * sizeof(cd), cudaMemcpyDeviceToDevice, s->st));
+  if (dst != s->st) VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  return VB_OK;
+}
+
+vb_status vb_test_raise_wait_flag(vb_mps *s) {
+  if (!s) return fail(VB_EINVAL, "vb_test_raise_wait_flag: null argument");
+  if (s->dtype != VB_MIXED) return fail(VB_EINVAL, "vb_test_raise_wait_flag: only mixed-form handles have the flag");
+  VB_TRY(set_device_of(s));
+  const int one = 1;
+  VB_TRY_CUDA(cudaMemcpyAsync(s->d_tcerr, &one, sizeof(int), cudaMemcpyHostToDevice, s->st));
+  VB_TRY_CUDA(cudaStreamSynchronize(s->st));
+  return VB_OK;
+}
+
 vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *o,
                       vb_sweep_stats *stats) {
   if (!s || !mpo || !o) return fail(VB_EINVAL, "tdvp2_sweep: null argument");
@@ -1467,11 +1519,7 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
   }
   VB_TRY_CUDA(cudaStreamSynchronize(s->st));
   prof_collect();
-  if (s->dtype == VB_MIXED) {
-    int tcerr = 0;
-    VB_TRY_CUDA(cudaMemcpy(&tcerr, s->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tcerr) return fail(VB_ETIMEOUT, "tdvp2_sweep: a tensor-core kernel's wait ran out (results invalid)");
-  }
+  VB_TRY(take_wait_flag(s, "tdvp2_sweep"));
   for (int b = 1; b < n; ++b) st.max_bond = std::max(st.max_bond, s->bond[b]);
   if (stats) *stats = st;
   return VB_OK;
@@ -1555,6 +1603,7 @@ vb_status tdvp1_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
     VB_TRY_CUDA(cudaMemcpyAsync(s->A[i - 1], s->theta, n0 * mL * sizeof(cd), cudaMemcpyDeviceToDevice, st));
   }
   VB_TRY_CUDA(cudaStreamSynchronize(st));
+  VB_TRY(take_wait_flag(s, "tdvp1_sweep"));
   ss.max_bond = 1;
   for (int b = 1; b < n; ++b) ss.max_bond = std::max(ss.max_bond, s->bond[b]);
   if (stats) *stats = ss;

@@ -112,3 +112,22 @@ def test_mixed_sweeps_product_state_rank_deficient_splits(P):
     assert max(24 * d for d in dims) > 192
     errs = _run(P, m, 8, 0.5, 24, eps=0.0)
     assert max(errs) < POP_TOL_MIXED
+
+
+def test_wait_flag_reported_and_cleared_by_both_sweeps(P):
+    # the failure path of a bounded tensor-core wait, made on the host: the
+    # flag such a wait raises is set through the test hook (no kernel times
+    # out, nothing faults); each sweep form must report VB_ETIMEOUT once and
+    # clear the flag, so the following sweep succeeds
+    m = vm.model_small_2state(n_modes=3, levels=6)
+    mpo = P.Mpo(m)
+    mps = P.Mps(mpo, vm.product_state_indices(m), m_cap=16, dtype=P.VB_MIXED)
+    mps.sweep(0.5, m_max=16)
+    for run in (lambda: mps.sweep1(0.5), lambda: mps.sweep(0.5, m_max=16)):
+        mps.raise_wait_flag()
+        with pytest.raises(P.VbError) as e:
+            run()
+        assert e.value.code == P.binding.VB_ETIMEOUT
+        mps2 = P.Mps(mpo, vm.product_state_indices(m), m_cap=16, dtype=P.VB_MIXED)
+        mps2.sweep(0.5, m_max=16)  # a fresh handle is unaffected
+        run()  # the flag was cleared when it was reported

@@ -108,3 +108,35 @@ def test_checkpoint_round_trip(P, tmp_path):
         a.sweep(0.5, m_max=16)
         b.sweep(0.5, m_max=16)
     assert np.max(np.abs(a.populations() - b.populations())) < 1e-13
+
+
+def test_spectrum_of_gpu_autocorrelation(P):
+    # Sec. 3.1 spectra: C(t) from GPU 2TDVP (mps_overlap after every step)
+    # Fourier transformed with damping on the GPU (vb_spectrum), against the
+    # oracle's transform of the same samples and the Poisson closed form of
+    # the independent-boson model (tests/test_oracle_spectrum.py)
+    from oracle import spectrum as ospec
+    from test_oracle_spectrum import _poisson_lines, _trapezoid_closed_form
+    m = vm.model_independent_boson(n_modes=2, levels=12, s_max=0.3)
+    idx = vm.product_state_indices(m, 0)
+    mpo = P.Mpo(m)
+    psi0 = P.Mps(mpo, idx, m_cap=4)
+    psi = P.Mps(mpo, idx, m_cap=4)
+    dt, n_t, tau = 1.0, 120, 30.0
+    c = [psi0.overlap(psi)]
+    for _ in range(n_t - 1):
+        psi.sweep(dt, m_max=4)
+        c.append(psi0.overlap(psi))
+    c = np.array(c)
+    ws, es = _poisson_lines(m, 0)
+    E = np.linspace(es.min() - 0.1, es.max() + 0.1, 151)
+    c_d = torch.from_numpy(c).cuda()
+    E_d = torch.from_numpy(E).cuda()
+    out = torch.zeros(E.size, dtype=torch.float64, device="cuda")
+    P.vb_spectrum(c_d, n_t, dt, tau, E_d, E.size, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    same = ospec.spectrum(c, dt, tau, E)
+    assert np.max(np.abs(got - same)) < 1e-12 * np.max(np.abs(same))
+    ref = _trapezoid_closed_form(ws, es, n_t, dt, tau, E)
+    assert np.max(np.abs(got - ref)) < 1e-8 * np.max(np.abs(ref))

@@ -58,7 +58,9 @@ def _noalloc(P, rho, k_want, k_vec):
 def test_noalloc_eigensolver_matches_regular_twice_in_a_row(P):
     # two different matrices, one after the other: the second call must not
     # depend on what the first one left in the shared array
-    for seed, n, k_want, k_vec in ((3, 200, 65, 64), (4, 96, 33, 20)):
+    # n = 200 and 96 take the cooperative reduction (bounded grid barrier,
+    # whose error word the call reads back), n = 48 the per-column path
+    for seed, n, k_want, k_vec in ((3, 200, 65, 64), (4, 96, 33, 20), (5, 48, 20, 12)):
         rho = _rho(seed, n)
         ev_r, Z_r = _regular(P, rho, k_want, k_vec)
         ev_n, Z_n = _noalloc(P, rho, k_want, k_vec)
