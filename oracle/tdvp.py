@@ -305,34 +305,13 @@ class Tdvp2:
         """The time step of `step` as a generator that yields after every
         two-site update (2 (n - 1) of them), so that a caller can time the
         sweep in consecutive slices; the step is complete once it is exhausted."""
-        A, W, L, R = self.mps.A, self.W, self.L, self.R
         n = self.mps.n
         tau = 0.5 * dt_fs
-        # left to right
-        for i in range(n - 1):
-            theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
-            Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
-            theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
-            A[i], C, disc = split_left(theta, self.opts)
-            st.discarded += disc
-            L[i + 1] = env_left_update(L[i], A[i], W[i])
-            if i < n - 2:
-                L1, W1, R1 = L[i + 1], W[i + 1], R[i + 2]
-                C = self._evolve(lambda x: heff1_apply(L1, W1, R1, x), C, -tau, st)
-            A[i + 1] = C
+        for i in range(n - 1):  # left to right
+            self.update_left_to_right(i, tau, st)
             yield i
-        # right to left
-        for i in range(n - 2, -1, -1):
-            theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
-            Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
-            theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
-            C, A[i + 1], disc = split_right(theta, self.opts)
-            st.discarded += disc
-            R[i + 1] = env_right_update(R[i + 2], A[i + 1], W[i + 1])
-            if i > 0:
-                L0, W0, R0 = L[i], W[i], R[i + 1]
-                C = self._evolve(lambda x: heff1_apply(L0, W0, R0, x), C, -tau, st)
-            A[i] = C
+        for i in range(n - 2, -1, -1):  # right to left
+            self.update_right_to_left(i, tau, st)
             if i == 0:
                 self.mps.center = 0
                 st.max_bond = max(self.mps.bond_dims())
@@ -341,6 +320,39 @@ class Tdvp2:
         if n < 2:
             st.max_bond = 1
             self.time += dt_fs
+
+    def update_left_to_right(self, i: int, tau: float, st: StepStats):
+        """The two-site update at pair (i, i+1) of the left-to-right half
+        sweep (center on site i, L[i] and R[i+2] current): merge, forward
+        exponential, split with A_i left-orthonormal, grow L, and the backward
+        one-site step of the new center unless i + 1 is the last site."""
+        A, W, L, R = self.mps.A, self.W, self.L, self.R
+        n = self.mps.n
+        theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
+        Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
+        theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
+        A[i], C, disc = split_left(theta, self.opts)
+        st.discarded += disc
+        L[i + 1] = env_left_update(L[i], A[i], W[i])
+        if i < n - 2:
+            L1, W1, R1 = L[i + 1], W[i + 1], R[i + 2]
+            C = self._evolve(lambda x: heff1_apply(L1, W1, R1, x), C, -tau, st)
+        A[i + 1] = C
+
+    def update_right_to_left(self, i: int, tau: float, st: StepStats):
+        """The mirror of update_left_to_right at pair (i, i+1) of the
+        right-to-left half sweep (center on site i+1)."""
+        A, W, L, R = self.mps.A, self.W, self.L, self.R
+        theta = np.einsum("asx,xtb->astb", A[i], A[i + 1], optimize=True)
+        Li, Wi, Wj, Rj = L[i], W[i], W[i + 1], R[i + 2]
+        theta = self._evolve(lambda x: heff2_apply(Li, Wi, Wj, Rj, x), theta, tau, st)
+        C, A[i + 1], disc = split_right(theta, self.opts)
+        st.discarded += disc
+        R[i + 1] = env_right_update(R[i + 2], A[i + 1], W[i + 1])
+        if i > 0:
+            L0, W0, R0 = L[i], W[i], R[i + 1]
+            C = self._evolve(lambda x: heff1_apply(L0, W0, R0, x), C, -tau, st)
+        A[i] = C
 
 
 class Tdvp1:

@@ -326,161 +326,6 @@ vb_status wapply_planar(const MpoSite &S, const float *X, long long xplane, WStr
   return VB_OK;
 }
 
-// Both sparse MPO legs of the two-site product in one kernel (FP32 planar):
-//   T2[a', s', w1, t, b] = sum_{w0, s} W_i[w0, s', s, w1] T1[a', w0, s, t, b]
-//   T3[a', s', t', w2, b] = sum_{w1, t} W_{i+1}[w1, t', t, w2] T2[a', s', w1, t, b]
-// A CTA owns one (a', s') pair and a chunk of FB consecutive b: it builds
-// that slice of T2 (all w1, all t) in shared memory from T1 and turns it into
-// the slice of T3, so T2 (w_M |theta| elements) never reaches global memory
-// and each leg's HBM traffic is one read of T1 and one write of T3. CTAs are
-// ordered with s' fastest, so the d_i CTAs of one (a', chunk) run together and
-// share their T1 rows (the operator rows of neighbouring s' overlap) in L2.
-// Within a warp, FB consecutive threads take consecutive b of one row (one
-// coalesced FB * 4-byte segment per row); the nonzero lists depend only on
-// (s', w1) in the first leg, so its loops are uniform across the CTA.
-constexpr int FB = 16;
-constexpr int FUSED_THREADS = 256;
-__global__ void __launch_bounds__(FUSED_THREADS) wapply2_fused_kernel(
-    const int *__restrict__ rp1, const int *__restrict__ col1, const float *__restrict__ val1,
-    const int *__restrict__ ptr1, const int *__restrict__ ent1, const int *__restrict__ rp2,
-    const int *__restrict__ col2, const float *__restrict__ val2, const int *__restrict__ ptr2,
-    const int *__restrict__ ent2, int d1, int d2, int wL, int wM, int wR, int mR, int nchunk,
-    const float *__restrict__ T1, long long plane1, const float *__restrict__ unused, float *__restrict__ T3,
-    long long kr, long long ld3) {
-  extern __shared__ float t2s[];  // [2 planes][wM][d2][FB]
-  (void)unused;
-  int bid = blockIdx.x;
-  const int so = bid % d1;
-  bid /= d1;
-  const int chunk = bid % nchunk;
-  const int ap = bid / nchunk;
-  const int b0 = chunk * FB;
-  const int nb = min(FB, mR - b0);
-  const int bq = threadIdx.x % FB, rg = threadIdx.x / FB;
-  constexpr int RG = FUSED_THREADS / FB;
-  const long long sstr = (long long)d2 * mR;     // stride of s in T1
-  const long long NL = (long long)d1 * sstr;     // stride of w0
-  const long long planeS = (long long)wM * d2 * FB;
-  const bool live = bq < nb;
-  const float *x = T1 + (long long)ap * wL * NL + b0 + (live ? bq : 0);
-  // first leg: T2 slice of (a', s') in shared memory
-  for (int w1 = 0; w1 < wM; ++w1) {
-    const int e0 = ptr1[w1], e1 = ptr1[w1 + 1];
-    for (int t = rg; t < d2; t += 2 * RG) {
-      const int t2 = t + RG;
-      const bool two = t2 < d2;
-      float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-      if (live) {
-        for (int e = e0; e < e1; ++e) {
-          const int w0 = ent1[3 * e], ident = ent1[3 * e + 1], off = ent1[3 * e + 2];
-          const float *xw = x + w0 * NL + (long long)t * mR;
-          const long long dt2 = (long long)RG * mR;
-          if (ident) {
-            const float *xr = xw + so * sstr;
-            ar += xr[0];
-            ai += xr[plane1];
-            if (two) {
-              br += xr[dt2];
-              bi += xr[dt2 + plane1];
-            }
-          } else {
-            const int k1 = rp1[off + so + 1];
-            for (int k = rp1[off + so]; k < k1; ++k) {
-              const float c = val1[k];
-              const float *xr = xw + col1[k] * sstr;
-              ar = fmaf(c, xr[0], ar);
-              ai = fmaf(c, xr[plane1], ai);
-              if (two) {
-                br = fmaf(c, xr[dt2], br);
-                bi = fmaf(c, xr[dt2 + plane1], bi);
-              }
-            }
-          }
-        }
-      }
-      float *o = t2s + ((long long)w1 * d2 + t) * FB + bq;
-      o[0] = ar;
-      o[planeS] = ai;
-      if (two) {
-        o[RG * FB] = br;
-        o[planeS + RG * FB] = bi;
-      }
-    }
-  }
-  __syncthreads();
-  // second leg: T3 rows (a', s', t'), columns (w2, b) of both planes
-  float *y = T3 + ((long long)ap * d1 + so) * d2 * ld3 + b0 + bq;
-  for (int w2 = 0; w2 < wR; ++w2) {
-    const int e0 = ptr2[w2], e1 = ptr2[w2 + 1];
-    for (int tp = rg; tp < d2; tp += RG) {
-      float ar = 0.f, ai = 0.f;
-      for (int e = e0; e < e1; ++e) {
-        const int w1 = ent2[3 * e], ident = ent2[3 * e + 1], off = ent2[3 * e + 2];
-        const float *tw = t2s + (long long)w1 * d2 * FB + bq;
-        if (ident) {
-          ar += tw[tp * FB];
-          ai += tw[planeS + tp * FB];
-        } else {
-          const int k1 = rp2[off + tp + 1];
-          for (int k = rp2[off + tp]; k < k1; ++k) {
-            const float c = val2[k];
-            const int t = col2[k];
-            ar = fmaf(c, tw[t * FB], ar);
-            ai = fmaf(c, tw[planeS + t * FB], ai);
-          }
-        }
-      }
-      if (live) {
-        float *yr = y + (long long)tp * ld3 + (long long)w2 * mR;
-        yr[0] = ar;
-        yr[kr] = ai;
-      }
-    }
-  }
-}
-
-size_t fused_smem_bytes(int wM, int d2) { return (size_t)2 * wM * d2 * FB * sizeof(float); }
-
-// both legs at once when the T2 slice fits in shared memory; false = use
-// the two separate legs
-vb_status wapply2_fused(const MpoSite &S1, const MpoSite &S2, int mL, int mR, const float *T1, long long plane1,
-                        long long t1_size, float *T3, long long kr, long long ld3, long long t3_size,
-                        cudaStream_t st, bool *done) {
-  *done = false;
-  const int d1 = S1.d, d2 = S2.d, wL = S1.wl, wM = S1.wr, wR = S2.wr;
-  const size_t smem = fused_smem_bytes(wM, d2);
-  if (smem > 200 * 1024) return VB_OK;
-  const long long nchunk = (mR + FB - 1) / FB;
-  const long long blocks = (long long)mL * nchunk * d1;
-  if (blocks == 0) {
-    *done = true;
-    return VB_OK;
-  }
-  if (blocks > INT_MAX) return VB_OK;
-  // the largest offsets the kernel forms
-  const long long NL = (long long)d1 * d2 * mR;
-  const long long x_max = (long long)(mL - 1) * wL * NL + (long long)(wL - 1) * NL + (long long)(d1 - 1) * d2 * mR +
-                          (long long)(d2 - 1) * mR + (mR - 1) + plane1;
-  const long long y_max = (((long long)(mL - 1) * d1 + d1 - 1) * d2 + d2 - 1) * ld3 + (long long)(wR - 1) * mR +
-                          (mR - 1) + kr;
-  if (x_max >= t1_size || y_max >= t3_size) return fail(VB_EINVAL, "wapply2_fused: view exceeds its buffer");
-  static bool attr_set[64] = {false};
-  int dev = 0;
-  VB_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "wapply2_fused: device ordinal out of range");
-  if (!attr_set[dev]) {
-    VB_TRY_CUDA(cudaFuncSetAttribute(wapply2_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set[dev] = true;
-  }
-  wapply2_fused_kernel<<<(unsigned)blocks, FUSED_THREADS, smem, st>>>(
-      S1.d_csr_ptr, S1.d_csr_col, S1.d_csr_val32, S1.d_fwd_ptr, S1.d_fwd_ent, S2.d_csr_ptr, S2.d_csr_col,
-      S2.d_csr_val32, S2.d_fwd_ptr, S2.d_fwd_ent, d1, d2, wL, wM, wR, mR, (int)nchunk, T1, plane1, nullptr, T3, kr,
-      ld3);
-  VB_CHECK_LAUNCH();
-  *done = true;
-  return VB_OK;
-}
-
 struct TcLayout {
   long long ML, KL, ldL, NL;  // L leg: (2 ML) x ldL times NL x ldL
   long long MR, KR, ld3;      // R leg: MR x ld3 times (2 mR) x ld3
@@ -569,8 +414,8 @@ vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, in
   prep_right_env<<<grid_for(2LL * mR * lay.ld3), 256, 0, st>>>(R, mR, lay.KR, lay.ld3, BR, BRlo);
   VB_CHECK_LAUNCH();
   prof_end(PH_PREP, st, 0.0);
-  // L leg: T1 planar (2 ML) x NL
-  // both operands were split by the prep kernels
+  // L leg: T1 planar (2 ML) x NL (both operands split by the prep kernels;
+  // K = 2 mL <= 128 takes the resident-B form of the GEMM)
   prof_begin(PH_TC, st);
   VB_TRY(tc_gemm_tf32(AL, lay.ldL, BX, lay.ldL, (int)(2 * lay.ML), (int)lay.NL, (int)lay.ldL, 0, T1, lay.NL,
                       nullptr, 0, err, st, true, nullptr, 0, ALlo, BXlo));
@@ -580,24 +425,17 @@ vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, in
     const MpoSite &S2 = mpo->sites[site + 1];
     const long long d1 = S.d, d2 = S2.d, wL = S.wl, wM = S.wr, Q1 = d2 * mR;
     const long long P2 = lay.nT2 / 2;
-    // both legs in one kernel (T2 in shared memory) where its slice fits
-    bool fused = false;
+    // T2[a'][s'][w1][(t b)] planar
     prof_begin(PH_WLEG, st);
-    VB_TRY(wapply2_fused(S, S2, mL, mR, T1, P1, lay.nT1, T3, lay.KR, lay.ld3, lay.MR * lay.ld3, st, &fused));
-    if (fused) {
-      prof_end(PH_WLEG, st, 0.0, 4.0 * (double)(lay.nT1 + 2 * lay.MR * lay.KR));
-    } else {
-      // T2[a'][s'][w1][(t b)] planar
-      VB_TRY(wapply_planar(S, T1, P1, WS(/*p*/ wL * d1 * Q1, /*w*/ d1 * Q1, /*s*/ Q1, /*q*/ 1), lay.nT1, T2, P2,
-                           WS(/*p*/ d1 * wM * Q1, /*w*/ Q1, /*s*/ wM * Q1, /*q*/ 1), lay.nT2, mL, (int)Q1, st));
-      prof_end(PH_WLEG, st, 0.0, 4.0 * (double)(lay.nT1 + lay.nT2));
-      // T3 row (a' s' t'): [Re (w2 b) | Im (w2 b) | 0]
-      prof_begin(PH_WLEG, st);
-      VB_TRY(wapply_planar(S2, T2, P2, WS(/*p*/ wM * d2 * mR, /*w*/ d2 * mR, /*s*/ mR, /*q*/ 1), lay.nT2, T3,
-                           lay.KR, WS(/*p*/ d2 * lay.ld3, /*w*/ mR, /*s*/ lay.ld3, /*q*/ 1), lay.MR * lay.ld3,
-                           (int)(mL * d1), mR, st));
-      prof_end(PH_WLEG, st, 0.0, 4.0 * (double)(lay.nT2 + 2 * lay.MR * lay.KR));
-    }
+    VB_TRY(wapply_planar(S, T1, P1, WS(/*p*/ wL * d1 * Q1, /*w*/ d1 * Q1, /*s*/ Q1, /*q*/ 1), lay.nT1, T2, P2,
+                         WS(/*p*/ d1 * wM * Q1, /*w*/ Q1, /*s*/ wM * Q1, /*q*/ 1), lay.nT2, mL, (int)Q1, st));
+    prof_end(PH_WLEG, st, 0.0, 4.0 * (double)(lay.nT1 + lay.nT2));
+    // T3 row (a' s' t'): [Re (w2 b) | Im (w2 b) | 0]
+    prof_begin(PH_WLEG, st);
+    VB_TRY(wapply_planar(S2, T2, P2, WS(/*p*/ wM * d2 * mR, /*w*/ d2 * mR, /*s*/ mR, /*q*/ 1), lay.nT2, T3,
+                         lay.KR, WS(/*p*/ d2 * lay.ld3, /*w*/ mR, /*s*/ lay.ld3, /*q*/ 1), lay.MR * lay.ld3,
+                         (int)(mL * d1), mR, st));
+    prof_end(PH_WLEG, st, 0.0, 4.0 * (double)(lay.nT2 + 2 * lay.MR * lay.KR));
   } else {
     const long long d = S.d, wL = S.wl;
     prof_begin(PH_WLEG, st);

@@ -22,6 +22,10 @@
 // k-step, A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated in FP32. The lo*lo
 // term and the tf32 rounding of lo leave a relative error of about 2^-21.
 //
+// Short K with both operands split beforehand (the L leg, K = 2 mL <= 128)
+// takes tc_gemm_bres_kernel instead: the B block of one N tile stays in
+// shared memory for a group of M tiles and tiles are written by TMA stores.
+//
 // Every wait on an mbarrier is bounded: when a wait runs out the CTA raises
 // the caller's error flag, waits (bounded) for its own copies in flight,
 // frees its TMEM and returns.
@@ -146,6 +150,75 @@ struct Epi {
   int nh;          // mode 1: number of complex columns (2*nh <= TC_BN)
   long long ws_stride;  // split-K: elements between the partial products of consecutive K slices
 };
+
+// Stores one accumulator tile (this warp's TMEM lane quarter q, all TC_BN
+// columns) in the sink's format. wb: this warp's 32 x 33 transpose buffer,
+// Dout: the fp32 sink of this tile.
+__device__ __forceinline__ void store_tile(const Epi &epi, uint32_t tbase, int m0, int n0, int M, int N, int q,
+                                           int lane, float *wb, float *Dout) {
+  const int m = m0 + q * 32 + lane;
+  // each 32 x 32 block goes through shared memory (transposed) so that a
+  // warp store covers one contiguous row segment
+  float v[32];
+  if (epi.mode == 0) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      tmem_ld32(tbase + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
+      __syncwarp();
+      const int col = n0 + c0 + lane;
+      if (col < N) {
+        for (int rr = 0; rr < 32; ++rr) {
+          const int mr = m0 + q * 32 + rr;
+          if (mr < M) Dout[(long long)mr * epi.ldd + col] = wb[rr * 33 + lane];
+        }
+      }
+      __syncwarp();
+    }
+  } else if (n0 == 0 && epi.nh % 32 == 0 && 2 * epi.nh <= TC_BN) {
+    // complex output, real parts in columns [0, nh), imaginary in [nh, 2 nh):
+    // chunk c0 and chunk c0 + nh give 32 complex values of each row
+#pragma unroll 1
+    for (int c0 = 0; c0 < epi.nh; c0 += 32) {
+      float re[32];
+      tmem_ld32(tbase + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
+      __syncwarp();
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) re[rr] = wb[rr * 33 + lane];
+      __syncwarp();
+      tmem_ld32(tbase + (uint32_t)(c0 + epi.nh), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
+      __syncwarp();
+      const int col = c0 + lane;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        const int mr = m0 + q * 32 + rr;
+        if (mr < M)
+          *reinterpret_cast<double2 *>(epi.Y + ((long long)mr * epi.nh + col) * 2) =
+              make_double2((double)re[rr], (double)wb[rr * 33 + lane]);
+      }
+      __syncwarp();
+    }
+  } else {
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      tmem_ld32(tbase + (uint32_t)c0, v);
+      if (m < M) {
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < epi.nh)
+            epi.Y[((long long)m * epi.nh + col) * 2] = (double)v[j];
+          else if (col < 2 * epi.nh)
+            epi.Y[((long long)m * epi.nh + (col - epi.nh)) * 2 + 1] = (double)v[j];
+        }
+      }
+    }
+  }
+}
 
 // SA, SB: how each operand enters the product. 0: one tf32 product (no
 // split); 1: split into hi / lo in shared memory as it lands; 2: split
@@ -332,13 +405,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else {
     // epilogue warps: TMEM lane quarter = warp % 4, all 128 columns
     const int q = warp & 3;
-    const int row = q * 32 + lane;
     for (int lt = 0; lt < my_tiles; ++lt) {
       const int b = lt & 1;
       const uint32_t use = (uint32_t)((lt >> 1) & 1);
       int m0, n0, kb0, kb1, slice;
       item_of(lt, m0, n0, kb0, kb1, slice);
-      const int m = m0 + row;
       float *Dout = epi.D + (long long)slice * epi.ws_stride;
       if (*abort_flag || !mbar_wait(&tfull[b], use)) {
         *abort_flag = 1;
@@ -346,73 +417,252 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN);
-      // each 32 x 32 block goes through shared memory (transposed) so that a
-      // warp store covers one contiguous row segment
-      float *wb = ebuf + (warp - 2 - TC_SPLIT_WARPS) * 32 * 33;
-      float v[32];
-      if (epi.mode == 0) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-          tmem_ld32(tbase + (uint32_t)c0, v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
-          __syncwarp();
-          const int col = n0 + c0 + lane;
-          if (col < N) {
-            for (int rr = 0; rr < 32; ++rr) {
-              const int mr = m0 + q * 32 + rr;
-              if (mr < M) Dout[(long long)mr * epi.ldd + col] = wb[rr * 33 + lane];
-            }
-          }
-          __syncwarp();
-        }
-      } else if (n0 == 0 && epi.nh % 32 == 0 && 2 * epi.nh <= TC_BN) {
-        // complex output, real parts in columns [0, nh), imaginary in [nh, 2 nh):
-        // chunk c0 and chunk c0 + nh give 32 complex values of each row
-#pragma unroll 1
-        for (int c0 = 0; c0 < epi.nh; c0 += 32) {
-          float re[32];
-          tmem_ld32(tbase + (uint32_t)c0, v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
-          __syncwarp();
-#pragma unroll
-          for (int rr = 0; rr < 32; ++rr) re[rr] = wb[rr * 33 + lane];
-          __syncwarp();
-          tmem_ld32(tbase + (uint32_t)(c0 + epi.nh), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) wb[lane * 33 + j] = v[j];
-          __syncwarp();
-          const int col = c0 + lane;
-#pragma unroll
-          for (int rr = 0; rr < 32; ++rr) {
-            const int mr = m0 + q * 32 + rr;
-            if (mr < M)
-              *reinterpret_cast<double2 *>(epi.Y + ((long long)mr * epi.nh + col) * 2) =
-                  make_double2((double)re[rr], (double)wb[rr * 33 + lane]);
-          }
-          __syncwarp();
-        }
-      } else {
-#pragma unroll 1
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-          tmem_ld32(tbase + (uint32_t)c0, v);
-          if (m < M) {
-            for (int j = 0; j < 32; ++j) {
-              const int col = n0 + c0 + j;
-              if (col < epi.nh)
-                epi.Y[((long long)m * epi.nh + col) * 2] = (double)v[j];
-              else if (col < 2 * epi.nh)
-                epi.Y[((long long)m * epi.nh + (col - epi.nh)) * 2 + 1] = (double)v[j];
-            }
-          }
-        }
-      }
+      store_tile(epi, tbase, m0, n0, M, N, q, lane, ebuf + (warp - 2 - TC_SPLIT_WARPS) * 32 * 33, Dout);
       // accumulator b is read out: the MMA thread may reuse it
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
     }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Short-K form (K <= 128, both operands split beforehand): the L leg of the
+// H_eff products has K = 2 mL and one operand row block (B, the two-site
+// tensor) shared by every M tile. The generic kernel stages A and B (hi and
+// lo) for every tile, 256 KB per 128 x 128 tile through L2, and is bound by
+// that traffic. Here a CTA takes a group of up to BRES_GROUP M tiles of one N
+// tile: the N tile's B block (all of K, hi and lo, <= 128 KB) is loaded once
+// into shared memory and stays there, only A streams through a two-stage
+// ring, which halves the operand traffic. Warp 0 issues the TMA copies, warp
+// 1 the MMAs, warps 2..5 (TMEM lane quarters 2, 3, 0, 1) are the epilogue;
+// the accumulators alternate between two TMEM buffers as in the generic
+// kernel. B is reloaded for the next group only after the MMAs of the group
+// have drained (bfree). Every wait is bounded as in the generic kernel.
+constexpr int BRES_ASTAGES = 2;
+constexpr int BRES_MAX_KB = 4;  // K <= 4 * TC_BK
+constexpr int BRES_GROUP = 8;
+constexpr int BRES_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr uint32_t BRES_STAGE_OUT = 32 * 128;  // one 32 x 32 fp32 block, 128-byte rows
+constexpr size_t BRES_OUT_BYTES = (size_t)TC_EPI_WARPS * 2 * BRES_STAGE_OUT;  // two per epilogue warp
+static_assert(BRES_OUT_BYTES >= TC_EPI_WARPS * 32 * 33 * 4, "staging holds the store_tile buffers");
+constexpr size_t BRES_SMEM =
+    1024 + (size_t)BRES_MAX_KB * 2 * TC_STAGE_B + (size_t)BRES_ASTAGES * 2 * TC_STAGE_A + BRES_OUT_BYTES + 512;
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(BRES_THREADS, 1)
+    tc_gemm_bres_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                        const __grid_constant__ CUtensorMap talo, const __grid_constant__ CUtensorMap tblo,
+                        const __grid_constant__ CUtensorMap td, int use_td, int M, int N, int K, int tiles_m,
+                        int tiles_n, int group, Epi epi, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sB = smem;                                       // [kb] hi
+  uint8_t *sBlo = sB + BRES_MAX_KB * TC_STAGE_B;            // [kb] lo
+  uint8_t *sA = sBlo + BRES_MAX_KB * TC_STAGE_B;            // [stage] hi
+  uint8_t *sAlo = sA + BRES_ASTAGES * TC_STAGE_A;           // [stage] lo
+  uint8_t *sOut = sAlo + BRES_ASTAGES * TC_STAGE_A;         // [warp][2] output blocks (1024-byte aligned)
+  uint64_t *full = reinterpret_cast<uint64_t *>(sOut + BRES_OUT_BYTES);
+  uint64_t *empty = full + BRES_ASTAGES;
+  uint64_t *tfull = empty + BRES_ASTAGES;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *bfull = tempty + 2;
+  uint64_t *bfree = bfull + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bfree + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = K / TC_BK;
+  const int gpn = (tiles_m + group - 1) / group;  // groups per N tile
+  const int ngroups = gpn * tiles_n;
+  // group gi: N tile gi / gpn, M tiles [mt0, mt1)
+  auto group_of = [&](int gi, int &n0, int &mt0, int &mt1) {
+    n0 = (gi / gpn) * TC_BN;
+    mt0 = (gi % gpn) * group;
+    mt1 = min(tiles_m, mt0 + group);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < BRES_ASTAGES; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], TC_EPI_WARPS);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(bfree, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;  // A stages issued
+      int grp = 0;      // groups whose B was issued
+      for (int gi = (int)blockIdx.x; gi < ngroups && !*abort_flag; gi += (int)gridDim.x) {
+        int n0, mt0, mt1;
+        group_of(gi, n0, mt0, mt1);
+        // the previous group's MMAs must be done with the resident B
+        if (grp > 0 && !mbar_wait(bfree, (uint32_t)((grp - 1) & 1))) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(bfull, (uint32_t)(nkb * 2 * TC_STAGE_B));
+        for (int kb = 0; kb < nkb; ++kb) {
+          tma_load_2d(sB + kb * TC_STAGE_B, &tb, bfull, kb * TC_BK, n0);
+          tma_load_2d(sBlo + kb * TC_STAGE_B, &tblo, bfull, kb * TC_BK, n0);
+        }
+        ++grp;
+        bool ok = true;
+        for (int mt = mt0; mt < mt1 && ok; ++mt) {
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int st = (int)(g % BRES_ASTAGES);
+            const uint32_t ph = (uint32_t)((g / BRES_ASTAGES) & 1);
+            if (*abort_flag || !mbar_wait(&empty[st], ph ^ 1u)) {
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&full[st], 2 * TC_STAGE_A);
+            tma_load_2d(sA + st * TC_STAGE_A, &ta, &full[st], kb * TC_BK, mt * TC_BM);
+            tma_load_2d(sAlo + st * TC_STAGE_A, &talo, &full[st], kb * TC_BK, mt * TC_BM);
+          }
+        }
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the shared memory goes away
+        if (grp > 0) mbar_wait(bfull, (uint32_t)((grp - 1) & 1));
+        for (long long q = (g > BRES_ASTAGES ? g - BRES_ASTAGES : 0); q < g; ++q)
+          mbar_wait(&full[q % BRES_ASTAGES], (uint32_t)((q / BRES_ASTAGES) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc();
+      long long g = 0;
+      int lt = 0, grp = 0;
+      bool ok = true;
+      for (int gi = (int)blockIdx.x; gi < ngroups && ok && !*abort_flag; gi += (int)gridDim.x, ++grp) {
+        int n0, mt0, mt1;
+        group_of(gi, n0, mt0, mt1);
+        if (!mbar_wait(bfull, (uint32_t)(grp & 1))) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int mt = mt0; mt < mt1 && ok; ++mt, ++lt) {
+          const int b = lt & 1;
+          const uint32_t use = (uint32_t)((lt >> 1) & 1);
+          if (!mbar_wait(&tempty[b], use ^ 1u)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dt = tmem + (uint32_t)(b * TC_BN);
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int st = (int)(g % BRES_ASTAGES);
+            const uint32_t ph = (uint32_t)((g / BRES_ASTAGES) & 1);
+            if (*abort_flag || !mbar_wait(&full[st], ph)) {
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t ad = smem_desc(smem_u32(sA + st * TC_STAGE_A));
+            const uint64_t adl = smem_desc(smem_u32(sAlo + st * TC_STAGE_A));
+            const uint64_t bd = smem_desc(smem_u32(sB + kb * TC_STAGE_B));
+            const uint64_t bdl = smem_desc(smem_u32(sBlo + kb * TC_STAGE_B));
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 8; ++kk) {
+              mma_tf32(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb != 0 || kk != 0) ? 1u : 0u);
+              mma_tf32(dt, ad + (uint64_t)(2 * kk), bdl + (uint64_t)(2 * kk), idesc, 1);
+              mma_tf32(dt, adl + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, 1);
+            }
+            mma_commit(&empty[st]);
+          }
+          if (ok) mma_commit(&tfull[b]);
+        }
+        // arrives once every MMA of the group (the last readers of B) is done
+        if (ok) mma_commit(bfree);
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter warp % 4
+    const int q = warp & 3;
+    const int ew = warp - 2;
+    int lt = 0;
+    long long nout = 0;  // output blocks stored by this warp
+    bool ok = true;
+    for (int gi = (int)blockIdx.x; gi < ngroups && ok; gi += (int)gridDim.x) {
+      int n0, mt0, mt1;
+      group_of(gi, n0, mt0, mt1);
+      for (int mt = mt0; mt < mt1; ++mt, ++lt) {
+        const int b = lt & 1;
+        const uint32_t use = (uint32_t)((lt >> 1) & 1);
+        if (*abort_flag || !mbar_wait(&tfull[b], use)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN);
+        if (use_td) {
+          // each 32 x 32 block: registers (one row per lane) -> 128-byte-swizzled
+          // shared block -> one TMA store; two blocks per warp alternate
+          for (int c0 = 0; c0 < TC_BN; c0 += 32, ++nout) {
+            uint8_t *blk = sOut + (size_t)(ew * 2 + (nout & 1)) * BRES_STAGE_OUT;
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            __syncwarp();
+            float v[32];
+            tmem_ld32(tbase + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<float4 *>(blk + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                  make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&td, blk, n0 + c0, mt * TC_BM + q * 32);
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+          }
+        } else {
+          store_tile(epi, tbase, mt * TC_BM, n0, M, N, q, lane, reinterpret_cast<float *>(sOut) + ew * 32 * 33, epi.D);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
+      }
+    }
+    // the stores in flight must be done before the CTA's shared memory goes away
+    if (use_td && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -544,6 +794,35 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
     }
   }
   Epi e = ks > 1 ? Epi{0, ws, N, nullptr, 0, (long long)M * N} : Epi{mode, D, ldd, Y, nh, 0};
+  if (ks == 1 && Alo && Blo && nkb <= BRES_MAX_KB && mode == 0) {
+    // short K: the B block of an N tile stays resident for a group of M tiles
+    static bool bres_set[64] = {false};
+    if (!bres_set[dev]) {
+      VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_bres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BRES_SMEM));
+      bres_set[dev] = true;
+    }
+    const int group = (int)std::min<long long>(tm, BRES_GROUP);
+    const long long ngroups = (tm + group - 1) / group * tn;
+    const int grid_b = (int)std::min<long long>(ngroups, sms);
+    // plain fp32 output with 16-byte aligned rows: stored by TMA in 32 x 32 blocks
+    CUtensorMap td = ta;
+    int use_td = 0;
+    if (mode == 0 && (reinterpret_cast<uintptr_t>(D) & 15) == 0 && (ldd * 4) % 16 == 0 && N % 4 == 0) {
+      cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+      cuuint64_t strides[1] = {(cuuint64_t)(ldd * 4)};
+      cuuint32_t box[2] = {32, 32};
+      cuuint32_t estr[2] = {1, 1};
+      if (g_encode(&td, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, D, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        use_td = 1;
+    }
+    tc_gemm_bres_kernel<<<grid_b, BRES_THREADS, BRES_SMEM, st>>>(ta, tb, talo, tblo, td, use_td, M, N, K, (int)tm,
+                                                                 (int)tn, group, e, err);
+    VB_CHECK_LAUNCH();
+    return VB_OK;
+  }
   const int items = tiles * ks;
   const int grid = std::min(items, sms);
   const size_t smem = split ? TcCfg<true>::SMEM : TcCfg<false>::SMEM;
