@@ -626,6 +626,63 @@ def _order_growth(args, P, model, cands, sweep_kw, st, dtype):
     return 0
 
 
+def run_gradient_case(args):
+    """The differentiation configuration: dP_upper(50 fs)/d kappa_I for the 24
+    diagonal linear couplings of the upper state in the two-state model
+    family of the plain configuration extended to 24 modes (d = 8, seed
+    1005), bond cap 64, 100 steps of 0.5 fs, from the product state
+    (tdvp2_population_gradient: forward sweeps, costate sweeps backwards,
+    step checkpointing every 10 steps). With --fd-params k, central finite
+    differences (h = 1e-5 eV) of the same-form propagation for the first k
+    couplings, and their relative difference to the adjoint gradient."""
+    import torch
+    from paper_1908_10588_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1908_10588_gb300 as P
+    dtype = P.VB_MIXED if args.dtype == "mixed" else P.VB_FP64
+    m = vm.model_small_2state(seed=1005, n_modes=24, levels=8)
+    up = vm.upper_state_index(m)
+    idx = vm.product_state_indices(m)
+    params = [(I, up, up) for I in range(24)]
+    steps, dt, m_max = 100, 0.5, 64
+    st = torch.cuda.current_stream()
+    mps = P.Mps(P.Mpo(m), idx, m_cap=m_max, dtype=dtype, stream=st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pops, grad = mps.population_gradient(dt, steps, params, up, m_max, checkpoint_every=10)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    bonds = mps.bond_dims()
+    mps.close()
+    out = {"case": "gradient", "model": "model_small_2state(seed=1005, n_modes=24, levels=8)", "m_max": m_max,
+           "dt_fs": dt, "steps": steps, "t_fs": steps * dt, "dtype": args.dtype, "params": "kappa_I = g^I_upper,upper",
+           "wall_s": wall, "population_upper": float(pops[up]), "max_bond_at_t": max(bonds),
+           "gradient": [float(x) for x in grad]}
+    if args.fd_params > 0:
+        h = 1e-5
+        fd = []
+        t0 = time.perf_counter()
+        for (I, i, j) in params[: args.fd_params]:
+            vals = []
+            for sgn in (1.0, -1.0):
+                mm = dict(m)
+                g = np.array(m["g1"], dtype=float)
+                g[I, i, j] += sgn * h
+                mm["g1"] = g
+                q = P.Mps(P.Mpo(mm), idx, m_cap=m_max, dtype=dtype, stream=st)
+                for _ in range(steps):
+                    q.sweep(dt, m_max=m_max)
+                vals.append(q.populations()[up])
+                q.close()
+            fd.append((vals[0] - vals[1]) / (2 * h))
+        fd = np.array(fd)
+        rel = np.abs(grad[: len(fd)] - fd) / np.max(np.abs(fd))
+        out.update({"fd_h_ev": h, "fd": [float(x) for x in fd], "fd_wall_s": time.perf_counter() - t0,
+                    "max_rel_diff_adjoint_vs_fd": float(np.max(rel))})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -644,9 +701,13 @@ def main():
     ap.add_argument("--kernel-case", default=None, choices=[None, "heff2"])
     ap.add_argument("--order-case", action="store_true")
     ap.add_argument("--order-growth", type=int, default=0)
+    ap.add_argument("--gradient-case", action="store_true")
+    ap.add_argument("--fd-params", type=int, default=0)
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.gradient_case:
+        return run_gradient_case(args)
     if args.order_case:
         return run_order_case(args)
     if args.impl == "reference":

@@ -167,6 +167,33 @@ vb_status tdvp2_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdv
 vb_status tdvp1_sweep(vb_mps *mps, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts,
                       vb_sweep_stats *stats /* nullable */);
 
+/* ---- differentiation: dP_k(t)/dg for linear vibronic couplings g^I_ij
+ * (Eq. Helvib_2; the parameters of the model, Sec. 2.2), t = n_steps * dt.
+ * psi is propagated by n_steps tdvp2_sweep calls (opts, dt_fs) and left at t;
+ * pop_out [n_el] (host) receives the populations at t, grad_out [n_param]
+ * (host) dP_{el_state}/dg for every parameter r = (mode param_mode[r],
+ * states param_i[r], param_j[r]); for i != j the parameter moves g_ij and
+ * g_ji together (H stays Hermitian), dH/dg = q_I (|i><j| + |j><i|).
+ * Method (Duhamel): dP_k/dg = (2/hbar) Im int_0^t <lambda(s)| dH/dg |psi(s)> ds,
+ * lambda(s) = exp(-iH(s - t)) |k><k| psi(t): the costate is propagated back
+ * with tdvp2_sweep(-dt) on a second state (the adjoint of a unitary local
+ * step is the step backwards; H_eff is Hermitian), the integrand at every step
+ * is a transfer-matrix contraction with q_I inserted, and the time integral
+ * uses composite closed Newton-Cotes rules on the step grid (Boole's rule on
+ * panels of four steps, Simpson / 3/8 / trapezoid for the remainder). With
+ * full bonds the propagation is exact and the gradient is exact up to the
+ * quadrature; with truncated bonds it is the gradient of the exact dynamics
+ * evaluated on the 2TDVP states. Step checkpointing: the state is stored
+ * every c = checkpoint_every steps and each segment but the last is recomputed
+ * once in the backward pass (two extra handles and about n_steps/c + c + 1
+ * state copies from psi's allocator; c = n_steps keeps every state and
+ * recomputes nothing). Needs the electronic site at position 0 and the center
+ * on site 0. Cost: 3 - c/n_steps sweeps per step. */
+vb_status tdvp2_population_gradient(vb_mps *psi, const vb_mpo *mpo, double dt_fs, int n_steps,
+                                    const vb_tdvp_opts *opts, int el_state, int n_param, const int *param_mode,
+                                    const int *param_i, const int *param_j, int checkpoint_every,
+                                    double *pop_out, double *grad_out);
+
 /* Electronic populations P_k = <psi| |k><k| |psi> / <psi|psi> (Sec. 3.1).
  * Needs the center on site 0 (where every sweep leaves it). The electronic
  * site may sit anywhere on the chain: at position e > 0 the transfer matrix

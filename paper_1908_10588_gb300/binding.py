@@ -27,7 +27,7 @@ EXPORTED = [
     "vb_env_work_elems", "vb_herm_eig_top", "vb_eig_work_bytes", "vb_kernel_launches",
     "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc", "mps_overlap", "mps_energy",
     "tdvp2_sweep_batched", "tdvp1_sweep", "vb_site_order_cost", "vb_site_order_search", "vb_site_order_rule",
-    "mps_get_tensor", "vb_test_raise_wait_flag", "vb_spectrum",
+    "mps_get_tensor", "vb_test_raise_wait_flag", "vb_spectrum", "tdvp2_population_gradient",
 ]
 
 
@@ -113,6 +113,7 @@ def lib():
         "mps_get_tensor": (i, [vp, i, vp, vp]),
         "vb_test_raise_wait_flag": (i, [vp]),
         "vb_spectrum": (i, [vp, i, d, d, vp, i, vp, vp]),
+        "tdvp2_population_gradient": (i, [vp, vp, d, i, C.POINTER(vb_tdvp_opts), i, i, vp, vp, vp, i, vp, vp]),
         "tdvp2_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
         "measure_populations": (i, [vp, vp]),
         "tdvp1_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
@@ -323,6 +324,23 @@ class Mps:
         st = vb_sweep_stats()
         check(lib().tdvp1_sweep(self.h, self.mpo.h, float(dt_fs), C.byref(o), C.byref(st)))
         return st
+
+    def population_gradient(self, dt_fs: float, n_steps: int, params, el_state: int, m_max: int,
+                            eps: float = 0.0, zero_floor: float = 1e-14, krylov_max: int = 30,
+                            krylov_tol: float = 1e-13, checkpoint_every: int = 10):
+        """Propagate n_steps 2TDVP steps and return (populations at t,
+        dP_el_state/dg for params [(mode, i, j), ...]) (tdvp2_population_gradient)."""
+        o = vb_tdvp_opts(m_max, eps, zero_floor, krylov_max, krylov_tol, 0)
+        pm = np.ascontiguousarray([p[0] for p in params], dtype=np.int32)
+        pi = np.ascontiguousarray([p[1] for p in params], dtype=np.int32)
+        pj = np.ascontiguousarray([p[2] for p in params], dtype=np.int32)
+        pops = np.zeros(self.mpo.n_el)
+        grad = np.zeros(max(1, len(params)))
+        check(lib().tdvp2_population_gradient(self.h, self.mpo.h, float(dt_fs), int(n_steps), C.byref(o),
+                                              int(el_state), len(params), pm.ctypes.data, pi.ctypes.data,
+                                              pj.ctypes.data, int(checkpoint_every), pops.ctypes.data,
+                                              grad.ctypes.data))
+        return pops, grad[: len(params)]
 
     def populations(self) -> np.ndarray:
         out = np.zeros(self.mpo.n_el)

@@ -208,6 +208,7 @@ struct vb_mpo {
   int n_el = 0;
   int el_pos = 0;
   std::vector<int> dims;
+  std::vector<int> pos_of_mode;  // chain position of every vibrational mode
   std::vector<vb::MpoSite> sites;
   int max_w = 0;
   int max_d = 0;

@@ -213,6 +213,7 @@ vb_status mpo_build(const vb_model *m, vb_mpo **out) {
   mpo->n_el = n_el;
   mpo->el_pos = el_pos;
   mpo->dims = dims;
+  mpo->pos_of_mode = pos_of_mode;
   mpo->sites.resize(n);
   for (int p = 0; p < n; ++p) {
     const std::map<Key, int> &cin = chan[p], &cout = chan[p + 1];

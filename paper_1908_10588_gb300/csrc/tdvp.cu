@@ -1827,3 +1827,390 @@ vb_status vb_herm_eig_top(int n, double *rho, int k_want, int k_vec, double *eva
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Gradient of an electronic population with respect to linear vibronic
+// couplings (the differentiable form of the 2TDVP path).
+//
+// For H(g) with dH/dg^I_ij = q_I (|i><j| + |j><i|) (Eq. Helvib_2; one term
+// for i = j) and P_k(t) = <psi(t)| |k><k| |psi(t)>, the Duhamel formula gives
+//   dP_k/dg = (2/hbar) Im int_0^t <lambda(s)| dH/dg |psi(s)> ds,
+//   lambda(s) = U(s, t) |k><k| psi(t)        (the costate, propagated back),
+// psi(s) the forward 2TDVP trajectory. The adjoint of the H_eff products and
+// of the local exponentials of a unitary step is the same step run backwards
+// (H_eff is Hermitian), so lambda comes from 2TDVP sweeps with -dt on a second
+// state; the coupling derivative enters only through <lambda|q_I x |i><j||psi>,
+// a transfer-matrix contraction with one operator inserted per parameter.
+// The integral over the step grid s_k = k dt uses composite closed
+// Newton-Cotes rules (Boole's 5-point rule on as many panels of four steps as
+// fit, Simpson or the 3/8 rule for the rest, a trapezoid for a single step).
+// Step checkpointing: the forward states are kept at every c-th step; the
+// backward pass recomputes each segment of c steps from its checkpoint (the
+// split's random-fill counter and the Krylov start hints are restored, so
+// the recomputed states equal the first ones) and consumes it in reverse;
+// the last segment is kept from the forward pass. About 3 - c/n_steps sweeps
+// per step in all.
+// ===========================================================================
+namespace vb {
+namespace {
+
+// site tensors of a state in one device buffer, laid out at the handle's
+// capacities, plus the host-side state needed to resume sweeps from it
+struct Snap {
+  std::vector<int> bond;
+  unsigned long long split_calls = 0;
+  std::vector<int> khint;
+  char *buf = nullptr;
+};
+
+size_t snap_bytes(const vb_mps *s) {
+  size_t b = 0;
+  for (int p = 0; p < s->n; ++p) b += (size_t)s->bcap[p] * s->dims[p] * s->bcap[p + 1] * sizeof(cd);
+  return b;
+}
+
+vb_status snap_save(const vb_mps *s, Snap &sn) {
+  sn.bond = s->bond;
+  sn.split_calls = s->split_calls;
+  sn.khint = s->khint;
+  char *o = sn.buf;
+  for (int p = 0; p < s->n; ++p) {
+    const size_t el = (size_t)s->bond[p] * s->dims[p] * s->bond[p + 1];
+    VB_TRY_CUDA(cudaMemcpyAsync(o, s->A[p], el * sizeof(cd), cudaMemcpyDeviceToDevice, s->st));
+    o += (size_t)s->bcap[p] * s->dims[p] * s->bcap[p + 1] * sizeof(cd);
+  }
+  return VB_OK;
+}
+
+// restore a state (center on site 0) and, when envs, its right environments
+vb_status snap_load(vb_mps *s, const Snap &sn, bool envs = true) {
+  s->bond = sn.bond;
+  s->split_calls = sn.split_calls;
+  s->khint = sn.khint;
+  const char *o = sn.buf;
+  for (int p = 0; p < s->n; ++p) {
+    const size_t el = (size_t)s->bond[p] * s->dims[p] * s->bond[p + 1];
+    VB_TRY_CUDA(cudaMemcpyAsync(s->A[p], o, el * sizeof(cd), cudaMemcpyDeviceToDevice, s->st));
+    o += (size_t)s->bcap[p] * s->dims[p] * s->bcap[p + 1] * sizeof(cd);
+  }
+  s->center = 0;
+  return envs ? build_right_envs(s) : VB_OK;
+}
+
+// A[x, s', y] <- sum_s O[s', s] A[x, s, y] for site p (O: d x d complex on the
+// device), through the handle's theta buffer
+__global__ void site_op_kernel(const cd *__restrict__ A, int ml, int d, int mr, const cd *__restrict__ O,
+                               cd *__restrict__ out) {
+  const long long tot = (long long)ml * d * mr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(e % mr);
+    const long long t = e / mr;
+    const int sp = (int)(t % d);
+    const long long x = t / d;
+    cd acc = mkc(0.0, 0.0);
+    for (int s = 0; s < d; ++s) acc = cadd(acc, cmul(O[sp * d + s], A[(x * d + s) * mr + y]));
+    out[e] = acc;
+  }
+}
+
+vb_status apply_site_op(vb_mps *s, int p, const cd *O) {
+  const long long el = (long long)s->bond[p] * s->dims[p] * s->bond[p + 1];
+  if (el > s->theta_cap) return fail(VB_EINVAL, "site operator: tensor larger than the two-site buffer");
+  const int blocks = (int)std::min<long long>((el + 255) / 256, 152LL * 16);
+  site_op_kernel<<<std::max(1, blocks), 256, 0, s->st>>>(s->A[p], s->bond[p], s->dims[p], s->bond[p + 1], O,
+                                                          s->theta);
+  VB_CHECK_LAUNCH();
+  VB_TRY_CUDA(cudaMemcpyAsync(s->A[p], s->theta, el * sizeof(cd), cudaMemcpyDeviceToDevice, s->st));
+  return VB_OK;
+}
+
+// out[j * out_stride] = <bra| O_j at site sites[j] |ket> for n_ops
+// single-site operators (ops: device, operator j at ops + j * dmax * dmax,
+// row-major d x d), by left transfer matrices E_p of sites < p and right ones
+// F_p of sites >= p (all kept, computed once for all operators), complex FP64
+// GEMMs on bra's stream; out: device
+// transfer matrices and temporaries of expect_site_ops, sized once for two
+// states with the bond capacities of `s`
+struct ExpectWork {
+  std::vector<cd *> E, F;
+  cd *X = nullptr, *Y = nullptr;
+  long long x_cap = 1;
+  vb_status init(const vb_mps *s, Scratch &sc) {
+    const int n = s->n;
+    E.assign(n + 1, nullptr);
+    F.assign(n + 1, nullptr);
+    for (int p = 0; p <= n; ++p) {
+      const long long sz = (long long)s->bcap[p] * s->bcap[p];
+      VB_TRY(sc.get((void **)&E[p], sz * sizeof(cd)));
+      VB_TRY(sc.get((void **)&F[p], sz * sizeof(cd)));
+    }
+    for (int p = 0; p < n; ++p) x_cap = std::max<long long>(x_cap, (long long)s->bcap[p] * s->dims[p] * s->bcap[p + 1]);
+    VB_TRY(sc.get((void **)&X, x_cap * sizeof(cd)));
+    VB_TRY(sc.get((void **)&Y, x_cap * sizeof(cd)));
+    return VB_OK;
+  }
+};
+
+vb_status expect_site_ops(const vb_mps *bra, const vb_mps *ket, int n_ops, const int *sites, const cd *ops,
+                          int dmax, cd *out, long long out_stride, ExpectWork &ew) {
+  const int n = bra->n;
+  cudaStream_t st = bra->st;
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  std::vector<cd *> &E = ew.E, &F = ew.F;
+  const long long x_cap = ew.x_cap;
+  cd *X = ew.X, *Y = ew.Y;
+  VB_TRY_CUDA(cudaMemcpyAsync(E[0], &one, sizeof(cd), cudaMemcpyHostToDevice, st));
+  VB_TRY_CUDA(cudaMemcpyAsync(F[n], &one, sizeof(cd), cudaMemcpyHostToDevice, st));
+  // E_{p+1}[y', y] = sum conj(bra[x', s, y']) E_p[x', x] ket[x, s, y]
+  for (int p = 0; p < n; ++p) {
+    const int xa = bra->bond[p], ya = bra->bond[p + 1], xb = ket->bond[p], yb = ket->bond[p + 1], d = bra->dims[p];
+    GemmArgs g{};
+    g.M = xa; g.N = d * yb; g.K = xb; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = E[p]; g.lda = xb; g.B = ket->A[p]; g.ldb = (long long)d * yb; g.C = X; g.ldc = (long long)d * yb;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)xa * xb; g.b_size = (long long)xb * d * yb; g.c_size = x_cap;
+    VB_TRY(zgemm(g, st));
+    GemmArgs h{};
+    h.M = ya; h.N = yb; h.K = xa * d; h.batch = 1; h.opA = OP_C; h.opB = OP_N;
+    h.A = bra->A[p]; h.lda = ya; h.B = X; h.ldb = yb; h.C = E[p + 1]; h.ldc = yb;
+    h.alpha = one; h.beta = zero;
+    h.a_size = (long long)xa * d * ya; h.b_size = x_cap; h.c_size = (long long)ya * yb;
+    VB_TRY(zgemm(h, st));
+  }
+  // F_p[x', x] = sum conj(bra[x', s, y']) ket[x, s, y] F_{p+1}[y', y]
+  for (int p = n - 1; p >= 0; --p) {
+    const int xa = bra->bond[p], ya = bra->bond[p + 1], xb = ket->bond[p], yb = ket->bond[p + 1], d = bra->dims[p];
+    GemmArgs g{};  // X[(x s), y'] = ket[(x s), y] F^T[y, y']
+    g.M = xb * d; g.N = ya; g.K = yb; g.batch = 1; g.opA = OP_N; g.opB = OP_T;
+    g.A = ket->A[p]; g.lda = yb; g.B = F[p + 1]; g.ldb = yb; g.C = X; g.ldc = ya;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)xb * d * yb; g.b_size = (long long)ya * yb; g.c_size = x_cap;
+    VB_TRY(zgemm(g, st));
+    GemmArgs h{};  // F[x', x] = conj(bra)[x', (s y')] X[x, (s y')]^T
+    h.M = xa; h.N = xb; h.K = d * ya; h.batch = 1; h.opA = OP_R; h.opB = OP_T;
+    h.A = bra->A[p]; h.lda = (long long)d * ya; h.B = X; h.ldb = (long long)d * ya; h.C = F[p]; h.ldc = xb;
+    h.alpha = one; h.beta = zero;
+    h.a_size = (long long)xa * d * ya; h.b_size = x_cap; h.c_size = (long long)xa * xb;
+    VB_TRY(zgemm(h, st));
+  }
+  // value_j = sum E_p[x', x] conj(bra[x', s', y']) O[s', s] ket[x, s, y] F_{p+1}[y', y]
+  for (int j = 0; j < n_ops; ++j) {
+    const int p = sites[j];
+    const int xa = bra->bond[p], ya = bra->bond[p + 1], xb = ket->bond[p], yb = ket->bond[p + 1], d = bra->dims[p];
+    GemmArgs g{};  // X[x, s', y] = O[s', s] ket[x, s, y]  (batched over x)
+    g.M = d; g.N = yb; g.K = d; g.batch = xb; g.opA = OP_N; g.opB = OP_N;
+    g.A = ops + (size_t)j * dmax * dmax; g.lda = d; g.sA = 0;
+    g.B = ket->A[p]; g.ldb = yb; g.sB = (long long)d * yb;
+    g.C = X; g.ldc = yb; g.sC = (long long)d * yb;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)d * d; g.b_size = (long long)xb * d * yb; g.c_size = x_cap;
+    VB_TRY(zgemm(g, st));
+    GemmArgs h{};  // Y[x', (s' y)] = E_p[x', x] X[x, (s' y)]
+    h.M = xa; h.N = d * yb; h.K = xb; h.batch = 1; h.opA = OP_N; h.opB = OP_N;
+    h.A = E[p]; h.lda = xb; h.B = X; h.ldb = (long long)d * yb; h.C = Y; h.ldc = (long long)d * yb;
+    h.alpha = one; h.beta = zero;
+    h.a_size = (long long)xa * xb; h.b_size = x_cap; h.c_size = x_cap;
+    VB_TRY(zgemm(h, st));
+    GemmArgs k{};  // X[(x' s'), y'] = Y[(x' s'), y] F_{p+1}^T[y, y']
+    k.M = xa * d; k.N = ya; k.K = yb; k.batch = 1; k.opA = OP_N; k.opB = OP_T;
+    k.A = Y; k.lda = yb; k.B = F[p + 1]; k.ldb = yb; k.C = X; k.ldc = ya;
+    k.alpha = one; k.beta = zero;
+    k.a_size = x_cap; k.b_size = (long long)ya * yb; k.c_size = x_cap;
+    VB_TRY(zgemm(k, st));
+    // <bra_p, X> = sum conj(bra[x', s', y']) X[x', s', y']
+    VB_TRY(vec_multi_dot(bra->A[p], 0, 1, X, (long long)xa * d * ya, out + j * out_stride, bra->d_partc,
+                         reduce_parts((long long)xa * d * ya), st));
+  }
+  return VB_OK;
+}
+
+// weights of the composite closed Newton-Cotes rule on k_steps + 1 equally
+// spaced samples (spacing h)
+std::vector<double> quad_weights(int k_steps, double h) {
+  std::vector<double> w(k_steps + 1, 0.0);
+  int a = 0, rest = k_steps;
+  auto panel = [&](int len, std::initializer_list<double> c, double scale) {
+    int o = 0;
+    for (double x : c) w[a + o++] += x * scale * h;
+    a += len;
+    rest -= len;
+  };
+  while (rest >= 4 && (rest % 4 == 0 || rest - 4 >= 2)) panel(4, {7, 32, 12, 32, 7}, 2.0 / 45.0);
+  if (rest == 3) panel(3, {1, 3, 3, 1}, 3.0 / 8.0);
+  if (rest == 2) panel(2, {1, 4, 1}, 1.0 / 3.0);
+  if (rest == 1) panel(1, {1, 1}, 0.5);
+  return w;
+}
+
+// q = (b + b^+)/sqrt(2) on d levels, row-major
+std::vector<cd> position_operator(int d) {
+  std::vector<cd> q((size_t)d * d, mkc(0.0, 0.0));
+  for (int k = 0; k + 1 < d; ++k) {
+    const double v = std::sqrt((double)(k + 1) / 2.0);
+    q[(size_t)k * d + k + 1] = mkc(v, 0.0);
+    q[(size_t)(k + 1) * d + k] = mkc(v, 0.0);
+  }
+  return q;
+}
+
+}  // namespace
+}  // namespace vb
+
+extern "C" vb_status tdvp2_population_gradient(vb_mps *psi, const vb_mpo *mpo, double dt_fs, int n_steps,
+                                               const vb_tdvp_opts *opts, int el_state, int n_param,
+                                               const int *param_mode, const int *param_i, const int *param_j,
+                                               int checkpoint_every, double *pop_out, double *grad_out) {
+  using namespace vb;
+  if (!psi || !mpo || !opts || !pop_out || (n_param > 0 && (!param_mode || !param_i || !param_j || !grad_out)))
+    return fail(VB_EINVAL, "tdvp2_population_gradient: null argument");
+  if (mpo != psi->mpo) return fail(VB_EINVAL, "tdvp2_population_gradient: MPS was created for another MPO");
+  if (n_steps < 1 || checkpoint_every < 1 || n_param < 0)
+    return fail(VB_EINVAL, "tdvp2_population_gradient: n_steps, checkpoint_every must be >= 1");
+  if (mpo->el_pos != 0) return fail(VB_EINVAL, "tdvp2_population_gradient: the electronic site must be site 0");
+  const int n_el = mpo->n_el;
+  if (el_state < 0 || el_state >= n_el) return fail(VB_EINVAL, "tdvp2_population_gradient: el_state out of range");
+  const int n_modes = (int)mpo->pos_of_mode.size();
+  for (int r = 0; r < n_param; ++r)
+    if (param_mode[r] < 0 || param_mode[r] >= n_modes || param_i[r] < 0 || param_i[r] >= n_el || param_j[r] < 0 ||
+        param_j[r] >= n_el)
+      return fail(VB_EINVAL, "tdvp2_population_gradient: parameter out of range");
+  if (psi->center != 0) return fail(VB_ESTATE, "tdvp2_population_gradient: center is not on site 0");
+  VB_TRY(set_device_of(psi));
+  cudaStream_t st = psi->st;
+  vb::Alloc al = psi->alloc;
+  Scratch sc(&al);
+  // second handle for the costate and a scratch handle for the recomputed states
+  vb_mps_opts o{};
+  o.m_cap = psi->m_cap;
+  o.dtype = psi->dtype;
+  o.krylov_cap = psi->kcap;
+  o.cuda_stream = st;
+  o.alloc = psi->alloc.user;
+  vb_mps *lam = nullptr, *work = nullptr;
+  VB_TRY(mps_setup(mpo, &o, &lam));
+  struct Own {
+    vb_mps *a, **b;
+    ~Own() {
+      if (a) mps_destroy(a);
+      if (*b) mps_destroy(*b);
+    }
+  } own{lam, &work};
+  VB_TRY(mps_setup(mpo, &o, &work));
+  // operators: the electronic ones |i><j| (+ |j><i|) of every parameter group,
+  // and q of every parameter's mode (padded to dmax x dmax)
+  int dmax = 1;
+  for (int d : mpo->dims) dmax = std::max(dmax, d);
+  std::vector<std::pair<int, int>> groups;
+  std::vector<int> group_of(n_param);
+  for (int r = 0; r < n_param; ++r) {
+    const int a = std::min(param_i[r], param_j[r]), b = std::max(param_i[r], param_j[r]);
+    auto it = std::find(groups.begin(), groups.end(), std::make_pair(a, b));
+    group_of[r] = (int)(it - groups.begin());
+    if (it == groups.end()) groups.emplace_back(a, b);
+  }
+  const int ng = (int)groups.size();
+  std::vector<cd> h_el((size_t)(ng + 1) * n_el * n_el, mkc(0.0, 0.0));
+  for (int g = 0; g < ng; ++g) {
+    cd *E = h_el.data() + (size_t)g * n_el * n_el;
+    E[groups[g].first * n_el + groups[g].second] = mkc(1.0, 0.0);
+    E[groups[g].second * n_el + groups[g].first] = mkc(1.0, 0.0);
+  }
+  h_el[(size_t)ng * n_el * n_el + el_state * n_el + el_state] = mkc(1.0, 0.0);  // the projector |k><k|
+  // q operators and sites in group order: the parameters of group g are
+  // order[gstart[g] .. gstart[g + 1])
+  std::vector<int> order, gstart(ng + 1, 0);
+  for (int g = 0; g < ng; ++g) {
+    gstart[g] = (int)order.size();
+    for (int r = 0; r < n_param; ++r)
+      if (group_of[r] == g) order.push_back(r);
+  }
+  gstart[ng] = (int)order.size();
+  std::vector<cd> h_q((size_t)std::max(1, n_param) * dmax * dmax, mkc(0.0, 0.0));
+  std::vector<int> sites(std::max(1, n_param));
+  for (int u = 0; u < n_param; ++u) {
+    const int p = mpo->pos_of_mode[param_mode[order[u]]];
+    sites[u] = p;
+    const std::vector<cd> q = position_operator(mpo->dims[p]);
+    std::copy(q.begin(), q.end(), h_q.begin() + (size_t)u * dmax * dmax);
+  }
+  cd *d_el = nullptr, *d_q = nullptr, *d_f = nullptr;
+  VB_TRY(sc.get((void **)&d_el, h_el.size() * sizeof(cd)));
+  VB_TRY(sc.get((void **)&d_q, h_q.size() * sizeof(cd)));
+  const int n_samples = n_steps + 1;
+  VB_TRY(sc.get((void **)&d_f, (size_t)std::max(1, n_param) * n_samples * sizeof(cd)));
+  VB_TRY_CUDA(cudaMemcpyAsync(d_el, h_el.data(), h_el.size() * sizeof(cd), cudaMemcpyHostToDevice, st));
+  VB_TRY_CUDA(cudaMemcpyAsync(d_q, h_q.data(), h_q.size() * sizeof(cd), cudaMemcpyHostToDevice, st));
+  // checkpoints every c steps (and the segment being replayed)
+  const int c = std::min(checkpoint_every, n_steps);
+  const int n_ckpt = (n_steps - 1) / c + 1;  // states 0, c, 2c, ... < n_steps
+  const size_t sb = snap_bytes(psi);
+  std::vector<Snap> ckpt(n_ckpt), seg(c + 1);
+  for (Snap &x : ckpt) VB_TRY(sc.get((void **)&x.buf, sb));
+  for (Snap &x : seg) VB_TRY(sc.get((void **)&x.buf, sb));
+  // forward pass; the states of the last segment go straight into the
+  // segment buffer, which the backward pass consumes first without a replay
+  const int a_last = (n_ckpt - 1) * c;
+  for (int k = 0; k < n_steps; ++k) {
+    if (k % c == 0) VB_TRY(snap_save(psi, ckpt[k / c]));
+    if (k >= a_last) VB_TRY(snap_save(psi, seg[k - a_last]));
+    VB_TRY(tdvp2_sweep(psi, mpo, dt_fs, opts, nullptr));
+  }
+  VB_TRY(snap_save(psi, seg[n_steps - a_last]));
+  VB_TRY(measure_populations(psi, pop_out));
+  // costate at t: |k><k| psi(t), normalised (the sweeps keep unit norm); its
+  // norm sqrt(P_k) scales the integrand back
+  VB_TRY(snap_load(lam, seg[n_steps - a_last]));
+  const double pk = pop_out[el_state];
+  if (pk <= 0.0) {
+    for (int r = 0; r < n_param; ++r) grad_out[r] = 0.0;
+    return VB_OK;
+  }
+  VB_TRY(apply_site_op(lam, 0, d_el + (size_t)ng * n_el * n_el));
+  {
+    // rescale the center (site 0) to unit norm
+    const long long el0 = (long long)lam->bond[0] * lam->dims[0] * lam->bond[1];
+    const double sc0 = 1.0 / std::sqrt(pk);
+    std::vector<cd> h0(el0);
+    VB_TRY_CUDA(cudaMemcpyAsync(h0.data(), lam->A[0], el0 * sizeof(cd), cudaMemcpyDeviceToHost, st));
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    for (cd &z : h0) z = mkc(z.x * sc0, z.y * sc0);
+    VB_TRY_CUDA(cudaMemcpyAsync(lam->A[0], h0.data(), el0 * sizeof(cd), cudaMemcpyHostToDevice, st));
+    VB_TRY(build_right_envs(lam));
+  }
+  // backward pass over the segments, last first; d_f row u = parameter order[u]
+  ExpectWork ew;
+  VB_TRY(ew.init(psi, sc));
+  for (int sgm = n_ckpt - 1; sgm >= 0; --sgm) {
+    const int a = sgm * c, b = std::min(n_steps, a + c);
+    if (sgm != n_ckpt - 1) {  // replay the segment from its checkpoint
+      VB_TRY(snap_load(work, ckpt[sgm]));
+      for (int k = a; k <= b; ++k) {
+        VB_TRY(snap_save(work, seg[k - a]));
+        if (k < b) VB_TRY(tdvp2_sweep(work, mpo, dt_fs, opts, nullptr));
+      }
+    }
+    for (int k = b; k >= a; --k) {
+      if (k == b && sgm != n_ckpt - 1) continue;  // sample b was taken with the later segment
+      // integrand at s_k: <lambda| q_I x |i><j| |psi(s_k)> for every parameter
+      for (int g = 0; g < ng; ++g) {
+        VB_TRY(snap_load(work, seg[k - a], false));
+        VB_TRY(apply_site_op(work, 0, d_el + (size_t)g * n_el * n_el));
+        const int u0 = gstart[g], nu = gstart[g + 1] - gstart[g];
+        VB_TRY(expect_site_ops(lam, work, nu, sites.data() + u0, d_q + (size_t)u0 * dmax * dmax, dmax,
+                               d_f + (size_t)u0 * n_samples + k, n_samples, ew));
+      }
+      if (k > 0) VB_TRY(tdvp2_sweep(lam, mpo, -dt_fs, opts, nullptr));
+    }
+  }
+  std::vector<cd> f((size_t)std::max(1, n_param) * n_samples);
+  VB_TRY_CUDA(cudaMemcpyAsync(f.data(), d_f, f.size() * sizeof(cd), cudaMemcpyDeviceToHost, st));
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  const std::vector<double> w = quad_weights(n_steps, dt_fs);
+  const double scale = 2.0 / HBAR_EV_FS * std::sqrt(pk);
+  for (int u = 0; u < n_param; ++u) {
+    double acc = 0.0;
+    for (int k = 0; k < n_samples; ++k) acc += w[k] * f[(size_t)u * n_samples + k].y;
+    grad_out[order[u]] = scale * acc;
+  }
+  return VB_OK;
+}
