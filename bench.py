@@ -626,6 +626,75 @@ def _order_growth(args, P, model, cands, sweep_kw, st, dtype):
     return 0
 
 
+def run_sf_case(args):
+    """The singlet-fission-like configuration at its stated size: 3 electronic
+    states (LE, TT, CT), each linearly coupled to its own 100-mode Debye bath
+    (lambda 0.05 eV, omega_c 0.1 eV), 10 levels per mode, 301 sites, bond cap
+    128, DBSS 1e-8, dt 1 fs. (a) steady state at the cap (random
+    right-canonical state, every bond at min(128, full)): --steps timed steps
+    of the mixed form after one warm-up, one FP64-form step; (b) from the
+    product state |LE> x |0...0>: --sf-steps steps of both forms, the largest
+    population difference between them along the way."""
+    import torch
+    from paper_1908_10588_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1908_10588_gb300 as P
+    m = vm.model_singlet_fission()
+    dims = vm.local_dims(m)
+    mmax = 128
+    kw = dict(m_max=mmax, eps=1e-8, zero_floor=1e-14, krylov_max=30, krylov_tol=1e-13)
+    st = torch.cuda.current_stream()
+    mpo = P.Mpo(m)
+    ts = vm.random_right_canonical_mps(STATE_SEED, dims, mmax)
+    out = {"case": "singlet_fission", "model": "model_singlet_fission(seed=1003, n_bath=100, levels=10)",
+           "n_sites": len(dims), "m_max": mmax, "eps": 1e-8, "dt_fs": 1.0}
+    for name, dtype, nsteps in (("mixed", P.VB_MIXED, args.steps), ("fp64", P.VB_FP64, 1)):
+        mps = P.Mps(mpo, m_cap=mmax, dtype=dtype, stream=st, tensors=ts)
+        if name == "mixed":
+            mps.sweep(1.0, **kw)
+        torch.cuda.synchronize()
+        P.vb_profile_read(reset=True)
+        P.vb_profile_enable(True, every=PROF_EVERY)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(nsteps):
+            mps.sweep(1.0, **kw)
+        e1.record(st)
+        torch.cuda.synchronize()
+        P.vb_profile_enable(False)
+        pr = P.vb_profile_read(reset=True)
+        ms = e0.elapsed_time(e1) / nsteps
+        hms = pr["heff2"]["ms"] + pr["heff1"]["ms"]
+        hfl = pr["heff2"]["flops"] + pr["heff1"]["flops"]
+        out[f"steady_{name}"] = {"ms_per_step": ms, "sweeps_per_s": 1e3 / ms, "steps_timed": nsteps,
+                                 "heff_tflops": hfl / (hms / 1e3) / 1e12 if hms > 0 else None,
+                                 "phases_ms_per_step": {k: round(pr[k]["ms"] / nsteps, 2) for k in
+                                                        ("heff2", "heff1", "krylov", "split", "env", "merge")},
+                                 "max_bond": max(mps.bond_dims())}
+        if name == "mixed":
+            tc = pr["heff_tc_legs"]
+            out[f"steady_{name}"]["tc_legs_tflops"] = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
+        mps.close()
+    idx = vm.product_state_indices(m)
+    runs = {}
+    for name, dtype in (("mixed", P.VB_MIXED), ("fp64", P.VB_FP64)):
+        mps = P.Mps(mpo, idx, m_cap=mmax, dtype=dtype, stream=st)
+        pops, t0 = [], time.perf_counter()
+        for _ in range(args.sf_steps):
+            mps.sweep(1.0, **kw)
+            pops.append(mps.populations())
+        runs[name] = (np.array(pops), time.perf_counter() - t0, max(mps.bond_dims()))
+        mps.close()
+    err = np.max(np.abs(runs["mixed"][0] - runs["fp64"][0]), axis=1)
+    out["from_product_state"] = {"steps": args.sf_steps, "max_pop_err_mixed_vs_fp64": float(err.max()),
+                                 "pop_err_last_step": float(err[-1]),
+                                 "wall_s": {k: round(v[1], 2) for k, v in runs.items()},
+                                 "max_bond": {k: v[2] for k, v in runs.items()},
+                                 "populations_last_step_fp64": [float(x) for x in runs["fp64"][0][-1]]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_gradient_case(args):
     """The differentiation configuration: dP_upper(50 fs)/d kappa_I for the 24
     diagonal linear couplings of the upper state in the two-state model
@@ -702,12 +771,16 @@ def main():
     ap.add_argument("--order-case", action="store_true")
     ap.add_argument("--order-growth", type=int, default=0)
     ap.add_argument("--gradient-case", action="store_true")
+    ap.add_argument("--sf-case", action="store_true")
+    ap.add_argument("--sf-steps", type=int, default=20)
     ap.add_argument("--fd-params", type=int, default=0)
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
     if args.gradient_case:
         return run_gradient_case(args)
+    if args.sf_case:
+        return run_sf_case(args)
     if args.order_case:
         return run_order_case(args)
     if args.impl == "reference":

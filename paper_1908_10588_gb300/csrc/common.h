@@ -255,13 +255,15 @@ struct SubspaceWork {
   cf *ws;         // split-K workspace of the Gram product
   long long ws_elems;
 };
+// largest subspace of the mixed split (m_max + 9 rows for bond caps up to 135)
+constexpr int SUBSPACE_MAX_R = 144;
 size_t subspace_chol_smem(int r);
 // Q (r x n, FP32 rows): rows j < m_warm copied from the old bond tensor (left:
 // n x m_old, row j = column j; right: m_old x n, row j = row j), the others
 // drawn from a counter-based generator keyed by seed
 vb_status subspace_init(cf *Q, int r, int n, const cd *warm, int m_old, int m_warm, bool left,
                         unsigned long long seed, cudaStream_t st);
-// orthonormalise the rows of Q (r <= 128) in place: row-scaled Cholesky QR,
+// orthonormalise the rows of Q (r <= SUBSPACE_MAX_R) in place: row-scaled Cholesky QR,
 // twice; rows found dependent are refilled at random before the second pass
 vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned long long seed, cudaStream_t st);
 // k largest eigenpairs of a small Hermitian S (2 <= n <= 112) by a one-CTA

@@ -361,13 +361,14 @@ static vb_status orth_pass(const cf *A, cf *T, int r, int n, const SubspaceWork 
 }
 
 vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned long long seed, cudaStream_t st) {
-  if (r < 1 || r > 128 || n < r) return fail(VB_EINVAL, "subspace_orth: needs 1 <= r <= min(n, 128)");
+  if (r < 1 || r > SUBSPACE_MAX_R || n < r)
+    return fail(VB_EINVAL, "subspace_orth: needs 1 <= r <= min(n, " + std::to_string(SUBSPACE_MAX_R) + ")");
   static int smem_set[64] = {0};
   int dev = 0;
   VB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !smem_set[dev]) {
     VB_TRY_CUDA(cudaFuncSetAttribute(chol_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)subspace_chol_smem(128)));
+                                     (int)subspace_chol_smem(SUBSPACE_MAX_R)));
     smem_set[dev] = 1;
   }
   VB_TRY(orth_pass(Q, w.T, r, n, w, seed, st));

@@ -761,7 +761,7 @@ vb_status split(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int m_old,
 
 // Mixed form of the split (Sec. 2.1.1 truncation). The kept Schmidt
 // directions are found in FP32: subspace iteration on theta for the
-// r = min(n, m_max + 9, 128) leading eigenvectors of rho, then a
+// r = min(n, m_max + 9, 144) leading eigenvectors of rho, then a
 // Rayleigh-Ritz step on their span (S = Q^* rho Q^T diagonalised in FP32) for
 // the kws = min(r, m_max + 1) leading Ritz vectors. Everything that defines
 // the new tensors is FP64: the Ritz basis is re-orthonormalised (one Lowdin
@@ -1098,7 +1098,7 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
       s->mixw_bytes = mb;
       A2(&s->mixw, mb);
       const long long nr2 = s->nrho_cap;
-      s->rcap = (int)std::min<long long>(nr2, std::min(opts->m_cap + 1 + 32, 128));
+      s->rcap = (int)std::min<long long>(nr2, std::min(opts->m_cap + 1 + 32, SUBSPACE_MAX_R));
       const long long rc = std::max(s->rcap, 1);
       A2((void **)&s->M32, s->theta_cap * sizeof(cf));
       A2((void **)&s->subZ, (size_t)rc * nr2 * sizeof(cf));

@@ -13,7 +13,9 @@ directions of the split, FP64 everything else).
     64, DBSS 1e-8) from the bond-saturated state: whole steps of both forms;
   - a reduced internal-conversion model (8 modes, d 10..30, bond 64, DBSS
     1e-8) from the product state over the whole stored trajectory: the mixed
-    form must not drift away from the oracle as the bonds grow and saturate.
+    form must not drift away from the oracle as the bonds grow and saturate;
+  - the singlet-fission-like model at its stated size (301 sites, bond 128):
+    mixed form against the FP64 form (the oracle is far too slow there).
 """
 import json
 import os
@@ -150,3 +152,22 @@ def test_ic8_trajectory_fp64_first_steps(P):
         mps.sweep(g["dt_fs"], **kw)
         assert float(np.max(np.abs(mps.populations() - np.array(g["populations"][k])))) < POP_TOL_FP64, k
         assert mps.bond_dims() == g["bonds"][k], k
+
+
+def test_singlet_fission_full_size_mixed_vs_fp64(P):
+    # 3 states x 100-mode Debye baths, 10 levels, 301 sites, bond cap 128:
+    # the mixed form (subspace split of m_max + 9 = 137 rows) follows the
+    # FP64 form from the product state
+    m = vm.model_singlet_fission()
+    mpo = P.Mpo(m)
+    idx = vm.product_state_indices(m)
+    kw = dict(m_max=128, eps=1e-8, zero_floor=1e-14, krylov_max=30, krylov_tol=1e-13)
+    a = P.Mps(mpo, idx, m_cap=128, dtype=P.VB_FP64)
+    b = P.Mps(mpo, idx, m_cap=128, dtype=P.VB_MIXED)
+    worst = 0.0
+    for _ in range(6):
+        a.sweep(1.0, **kw)
+        b.sweep(1.0, **kw)
+        worst = max(worst, float(np.max(np.abs(a.populations() - b.populations()))))
+    print(f"SF 301 sites: mixed vs FP64 over 6 steps {worst:.2e}, bonds {max(a.bond_dims())}/{max(b.bond_dims())}")
+    assert worst < POP_TOL_MIXED
