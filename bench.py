@@ -695,6 +695,53 @@ def run_sf_case(args):
     return 0
 
 
+def run_batch_case(args):
+    """The batched configuration: 64 independent two-state models (mode counts
+    8..40, bond caps 16..96 drawn per instance, all couplings scaled 0.5..2x
+    across the batch; vibmodels.batch_models, seed 1004), --batch-steps steps
+    of dt = 0.5 fs from the product state. Timed two ways with the same
+    states: one instance after another on one stream, and all instances at
+    once with tdvp2_sweep_batched (one host thread and one stream per
+    instance). Reports instance-steps per second and checks that both give
+    the same populations."""
+    import torch
+    from paper_1908_10588_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1908_10588_gb300 as P
+    dtype = P.VB_MIXED if args.dtype == "mixed" else P.VB_FP64
+    batch = vm.batch_models(seed=1004, n=64)
+    mpos = [P.Mpo(m) for m, _ in batch]
+    out = {"case": "batch", "instances": len(batch), "steps": args.batch_steps, "dtype": args.dtype,
+           "mode_counts": [len(m["omega"]) for m, _ in batch], "m_max": [mm for _, mm in batch]}
+    res = {}
+    for how in ("one_stream", "batched"):
+        streams = [torch.cuda.Stream() for _ in batch] if how == "batched" else [torch.cuda.current_stream()] * len(batch)
+        states = [P.Mps(mpo, vm.product_state_indices(m), m_cap=mm, dtype=dtype, stream=st)
+                  for (m, mm), mpo, st in zip(batch, mpos, streams)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.batch_steps):
+            if how == "batched":
+                P.sweep_batched(states, 0.5, m_max=max(mm for _, mm in batch), eps=0.0)
+            else:
+                for q, (_, mm) in zip(states, batch):
+                    q.sweep(0.5, m_max=mm, eps=0.0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        res[how] = ([q.populations() for q in states], wall, [max(q.bond_dims()) for q in states])
+        for q in states:
+            q.close()
+    diff = max(float(np.max(np.abs(a - b))) for a, b in zip(res["one_stream"][0], res["batched"][0]))
+    n_is = len(batch) * args.batch_steps
+    out.update({"one_stream": {"wall_s": res["one_stream"][1], "instance_steps_per_s": n_is / res["one_stream"][1]},
+                "batched": {"wall_s": res["batched"][1], "instance_steps_per_s": n_is / res["batched"][1]},
+                "speedup_batched": res["one_stream"][1] / res["batched"][1],
+                "max_pop_diff_batched_vs_one_stream": diff,
+                "max_bond_at_end": res["batched"][2]})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_gradient_case(args):
     """The differentiation configuration: dP_upper(50 fs)/d kappa_I for the 24
     diagonal linear couplings of the upper state in the two-state model
@@ -772,6 +819,8 @@ def main():
     ap.add_argument("--order-growth", type=int, default=0)
     ap.add_argument("--gradient-case", action="store_true")
     ap.add_argument("--sf-case", action="store_true")
+    ap.add_argument("--batch-case", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--sf-steps", type=int, default=20)
     ap.add_argument("--fd-params", type=int, default=0)
     args = ap.parse_args()
@@ -781,6 +830,8 @@ def main():
         return run_gradient_case(args)
     if args.sf_case:
         return run_sf_case(args)
+    if args.batch_case:
+        return run_batch_case(args)
     if args.order_case:
         return run_order_case(args)
     if args.impl == "reference":

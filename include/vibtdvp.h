@@ -194,6 +194,33 @@ vb_status tdvp2_population_gradient(vb_mps *psi, const vb_mpo *mpo, double dt_fs
                                     const int *param_i, const int *param_j, int checkpoint_every,
                                     double *pop_out, double *grad_out);
 
+/* ---- global Krylov step (Sec. 2.1.2, Eqs. Krylov subspace and global
+ * Krylov): psi <- exp(-iH dt/hbar) psi in the Krylov space spanned by the
+ * MPSs k_0 = psi/|psi|, k_{j+1} = compress(H k_j)/|.|, H applied as the MPO
+ * directly (Sec. 2.1.1, Eqs. direct app 1/2: bond dimensions multiply) and
+ * compressed with the 2TDVP split's truncation rule (opts: m_max, eps,
+ * zero_floor; Sec. 2.1.1). The basis is orthonormalised through its Gram
+ * matrix S_ij = <k_i|k_j> in Krylov order (Cholesky), H is projected as
+ * <k_i|H k_j> with the uncompressed H k_j, the propagator is exact in the
+ * span, and the state becomes sum_j c_j k_j, compressed and scaled back to
+ * |psi|. Stops when the newest orthonormal direction's coefficient is below
+ * tol, when a new vector lies in the span (smallest eigenvalue of S <= 1e-13
+ * of its largest), or at r_max vectors (<= 40). The result must fit the
+ * handle's bond capacities (VB_EINVAL otherwise; psi unchanged then). Used
+ * for pre-steps that grow the bonds of a product state before tdvp1_sweep
+ * (Sec. 2.1.2, one-site TDVP paragraph). All contractions are complex FP64
+ * GEMMs on the device; the Krylov vectors (bonds up to w x m_max) are held in
+ * temporaries from psi's allocator for the duration of the call. */
+typedef struct {
+  int r;                /* Krylov vectors beyond k_0 that were kept */
+  int converged;        /* 1: stopped on tol or an invariant space */
+  double disc_basis;    /* summed discarded weight of the basis compressions */
+  double disc_final;    /* discarded weight of the final compression */
+  int max_bond_basis;   /* largest bond of a compressed basis vector */
+} vb_krylov_info;
+vb_status global_krylov_step(vb_mps *psi, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts, int r_max,
+                             double tol, vb_krylov_info *info /* nullable */);
+
 /* Electronic populations P_k = <psi| |k><k| |psi> / <psi|psi> (Sec. 3.1).
  * Needs the center on site 0 (where every sweep leaves it). The electronic
  * site may sit anywhere on the chain: at position e > 0 the transfer matrix
@@ -239,7 +266,8 @@ vb_status mps_energy(const vb_mps *mps, double *out_host /* [1] */);
  * receives one entry per instance. On failure the error of the first failing
  * instance (in index order) is returned and its message is available from
  * vb_last_error(); the other instances have completed their sweep. An
- * instance may not appear twice. */
+ * instance may not appear twice. Instances of uneven size share opts except
+ * for the bond cap, which is min(opts->m_max, the instance's m_cap). */
 vb_status tdvp2_sweep_batched(vb_mps *const *mps, const vb_mpo *const *mpo, int count, double dt_fs,
                               const vb_tdvp_opts *opts, vb_sweep_stats *stats /* [count], nullable */);
 
@@ -370,6 +398,17 @@ vb_status vb_herm_eig_top_noalloc(int n, double *rho, int k_want, int k_vec, dou
  * next tdvp2_sweep / tdvp1_sweep must then return VB_ETIMEOUT and clear it.
  * VB_EINVAL for an FP64-form handle. */
 vb_status vb_test_raise_wait_flag(vb_mps *mps);
+
+/* ---- autotuner of the tensor-core tiles (the paper has no counterpart).
+ * The L leg of the mixed H_eff products (a resident-B tcgen05 GEMM) groups
+ * up to G M tiles per resident B block; on the first call for a GEMM shape
+ * (device, M, N, K) the candidates G in {2, 4, 8, 12, 24} (<= the M tiles)
+ * are each timed once with CUDA events (every candidate writes the same
+ * result, so the output is unaffected) and the fastest is kept for that
+ * shape. enable: 1 on (default), 0 off (G = 8 for new shapes), -1 unchanged;
+ * reset != 0 clears the table. n_entries (nullable) receives the table size,
+ * text (nullable, text_len bytes) one line per shape "M= N= K= group= ms=". */
+vb_status vb_autotune(int enable, int reset, int *n_entries, char *text, int text_len);
 
 /* ---- measurement (not part of the method; the paper has no counterpart).
  * Number of CUDA kernels this library has launched since it was loaded. */

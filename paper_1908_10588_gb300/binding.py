@@ -28,6 +28,7 @@ EXPORTED = [
     "vb_profile_enable", "vb_profile_read", "vb_herm_eig_top_noalloc", "mps_overlap", "mps_energy",
     "tdvp2_sweep_batched", "tdvp1_sweep", "vb_site_order_cost", "vb_site_order_search", "vb_site_order_rule",
     "mps_get_tensor", "vb_test_raise_wait_flag", "vb_spectrum", "tdvp2_population_gradient",
+    "global_krylov_step", "vb_autotune",
 ]
 
 
@@ -80,6 +81,11 @@ class vb_order_cost(C.Structure):
                 ("coupling_dist", C.c_double), ("objective", C.c_double), ("max_w", C.c_int)]
 
 
+class vb_krylov_info(C.Structure):
+    _fields_ = [("r", C.c_int), ("converged", C.c_int), ("disc_basis", C.c_double), ("disc_final", C.c_double),
+                ("max_bond_basis", C.c_int)]
+
+
 class vb_sweep_stats(C.Structure):
     _fields_ = [("max_bond", C.c_int), ("discarded_weight", C.c_double), ("krylov_iters_max", C.c_int),
                 ("krylov_iters_total", C.c_int), ("noconv", C.c_int)]
@@ -114,6 +120,8 @@ def lib():
         "vb_test_raise_wait_flag": (i, [vp]),
         "vb_spectrum": (i, [vp, i, d, d, vp, i, vp, vp]),
         "tdvp2_population_gradient": (i, [vp, vp, d, i, C.POINTER(vb_tdvp_opts), i, i, vp, vp, vp, i, vp, vp]),
+        "global_krylov_step": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), i, d, C.POINTER(vb_krylov_info)]),
+        "vb_autotune": (i, [i, i, C.POINTER(i), C.c_char_p, i]),
         "tdvp2_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
         "measure_populations": (i, [vp, vp]),
         "tdvp1_sweep": (i, [vp, vp, d, C.POINTER(vb_tdvp_opts), C.POINTER(vb_sweep_stats)]),
@@ -342,6 +350,15 @@ class Mps:
                                               grad.ctypes.data))
         return pops, grad[: len(params)]
 
+    def global_krylov(self, dt_fs: float, m_max: int, eps: float = 0.0, zero_floor: float = 1e-14,
+                      r_max: int = 20, tol: float = 1e-12):
+        """One global Krylov step (global_krylov_step); returns its info."""
+        o = vb_tdvp_opts(m_max, eps, zero_floor, 30, 1e-13, 0)
+        inf = vb_krylov_info()
+        check(lib().global_krylov_step(self.h, self.mpo.h, float(dt_fs), C.byref(o), int(r_max), float(tol),
+                                       C.byref(inf)))
+        return inf
+
     def populations(self) -> np.ndarray:
         out = np.zeros(self.mpo.n_el)
         check(lib().measure_populations(self.h, out.ctypes.data))
@@ -441,6 +458,15 @@ def vb_spectrum(c_t, n_t, dt_fs, tau_fs, energies, n_e, out, stream=None):
     energies float64 [n_e], out float64 [n_e])."""
     check(lib().vb_spectrum(_ptr(c_t), int(n_t), float(dt_fs), float(tau_fs), _ptr(energies), int(n_e),
                             _ptr(out), _stream_ptr(stream)))
+
+
+def vb_autotune(enable: int = -1, reset: bool = False):
+    """Autotuner of the tensor-core tile grouping (vb_autotune): switch it
+    (1 / 0, -1 unchanged), optionally clear it; returns its table lines."""
+    n = C.c_int()
+    buf = C.create_string_buffer(1 << 16)
+    check(lib().vb_autotune(int(enable), int(bool(reset)), C.byref(n), buf, len(buf)))
+    return [x for x in buf.value.decode().splitlines() if x]
 
 
 def vb_kernel_launches() -> int:

@@ -209,6 +209,17 @@ struct vb_mpo {
   int el_pos = 0;
   std::vector<int> dims;
   std::vector<int> pos_of_mode;  // chain position of every vibrational mode
+  // channels of bond b - 1 (b = 0 .. n; the left block L[b] and the right
+  // block R[b] carry them): the one with no operator placed yet (START, the
+  // right block's complete Hamiltonian) and the finished one (DONE, the left
+  // block's complete Hamiltonian); -1 where absent
+  std::vector<int> ch_start, ch_done;
+  // zero-point energy sum_I hbar omega_I / 2 (Eq. Hvib_2), a constant the MPO
+  // carries as an identity term on site 0. The FP32 operators of the mixed
+  // form leave it out (their rounding errors then scale with the spread of
+  // H, not with this offset, which for a 300-mode bath is ~30 eV); a mixed
+  // sweep restores it as the exact global phase exp(-i e_zpe dt / hbar).
+  double e_zpe = 0.0;
   std::vector<vb::MpoSite> sites;
   int max_w = 0;
   int max_d = 0;

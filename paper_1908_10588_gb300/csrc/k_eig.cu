@@ -927,7 +927,8 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
   typedef cplx<R> C_;
   (void)rho;
   if (k_vec < 1 || k_vec > k_want) return fail(VB_EINVAL, "eig_vectors: bad k_vec");
-  if (k_vec > 128) return fail(VB_EINVAL, "eig_vectors: at most 128 vectors");
+  // the panelled Gram-Schmidt keeps p0 * b <= 128 * 16 coefficients (off_part)
+  if (k_vec > 144) return fail(VB_EINVAL, "eig_vectors: at most 144 vectors");
   EigLayout lay(n, k_want, sizeof(R));
   char *w = static_cast<char *>(work);
   C_ *vref = reinterpret_cast<C_ *>(w + lay.off_vref);
@@ -950,7 +951,7 @@ vb_status eig_vectors(int n, const cplx<R> *rho, int k_want, int k_vec, const R 
       cgs2_rows<R><<<1, 512, 0, st>>>(Y, n, k_vec);
       VB_CHECK_LAUNCH();
     } else {
-      R *C = reinterpret_cast<R *>(w + lay.off_part);  // 2048 reals; p0 * b <= 128 * 16
+      R *C = reinterpret_cast<R *>(w + lay.off_part);  // 2048 reals; p0 * b <= 128 * 16 for k_vec <= 144
       for (int p0 = 0; p0 < k_vec; p0 += BGS_PANEL) {
         const int b = std::min(BGS_PANEL, k_vec - p0);
         if (p0 > 0) {

@@ -33,7 +33,10 @@
 #include <cudaTypedefs.h>
 
 #include <climits>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.h"
 
@@ -696,6 +699,35 @@ __global__ void tc_splitk_reduce(const float *__restrict__ ws, int ks, int M, in
   }
 }
 
+// ---- autotuner of the resident-B GEMM: best group size per (device, M, N, K)
+struct AutotuneKey {
+  int dev, M, N, K;
+  bool operator<(const AutotuneKey &o) const {
+    return std::tie(dev, M, N, K) < std::tie(o.dev, o.M, o.N, o.K);
+  }
+};
+struct AutotuneEntry {
+  int group;
+  float ms;  // time of the chosen candidate (-1: not timed)
+};
+std::mutex g_tune_mu;
+std::map<AutotuneKey, AutotuneEntry> g_tune;
+bool g_tune_on = true;
+
+int autotune_lookup(const AutotuneKey &k) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(k);
+  return it == g_tune.end() ? 0 : it->second.group;
+}
+void autotune_store(const AutotuneKey &k, int group, float ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[k] = AutotuneEntry{group, ms};
+}
+bool autotune_enabled() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune_on;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 
@@ -802,9 +834,6 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
                                        (int)BRES_SMEM));
       bres_set[dev] = true;
     }
-    const int group = (int)std::min<long long>(tm, BRES_GROUP);
-    const long long ngroups = (tm + group - 1) / group * tn;
-    const int grid_b = (int)std::min<long long>(ngroups, sms);
     // plain fp32 output with 16-byte aligned rows: stored by TMA in 32 x 32 blocks
     CUtensorMap td = ta;
     int use_td = 0;
@@ -818,10 +847,51 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
         use_td = 1;
     }
-    tc_gemm_bres_kernel<<<grid_b, BRES_THREADS, BRES_SMEM, st>>>(ta, tb, talo, tblo, td, use_td, M, N, K, (int)tm,
-                                                                 (int)tn, group, e, err);
-    VB_CHECK_LAUNCH();
-    return VB_OK;
+    auto launch = [&](int group) -> vb_status {
+      const long long ngroups = (tm + group - 1) / group * tn;
+      const int grid_b = (int)std::min<long long>(ngroups, sms);
+      tc_gemm_bres_kernel<<<grid_b, BRES_THREADS, BRES_SMEM, st>>>(ta, tb, talo, tblo, td, use_td, M, N, K,
+                                                                   (int)tm, (int)tn, group, e, err);
+      VB_CHECK_LAUNCH();
+      return VB_OK;
+    };
+    // the group size (M tiles per resident B block) comes from the autotuner:
+    // on the first call for a shape each candidate is timed once (they write
+    // the same D) and the fastest is kept for the shape from then on
+    const AutotuneKey key{dev, M, N, K};
+    int group = autotune_lookup(key);
+    if (group <= 0) {
+      std::vector<int> cand;
+      for (int g : {2, 4, 8, 12, 24})
+        if (g <= tm) cand.push_back(g);
+      if (cand.empty() || tm <= 2 || !autotune_enabled()) cand.assign(1, (int)std::min<long long>(tm, BRES_GROUP));
+      if (cand.size() == 1) {
+        group = cand[0];
+      } else {
+        cudaEvent_t e0, e1;
+        VB_TRY_CUDA(cudaEventCreate(&e0));
+        VB_TRY_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        for (int g : cand) {
+          VB_TRY_CUDA(cudaEventRecord(e0, st));
+          VB_TRY(launch(g));
+          VB_TRY_CUDA(cudaEventRecord(e1, st));
+          VB_TRY_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          VB_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            group = g;
+          }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        autotune_store(key, group, best);
+        return VB_OK;  // D holds the product (every trial computed it)
+      }
+      autotune_store(key, group, -1.f);
+    }
+    return launch(group);
   }
   const int items = tiles * ks;
   const int grid = std::min(items, sms);
@@ -846,3 +916,23 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
 }
 
 }  // namespace vb
+
+// ---- autotuner control and table (C ABI)
+extern "C" vb_status vb_autotune(int enable, int reset, int *n_entries, char *text, int text_len) {
+  using namespace vb;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (enable >= 0) g_tune_on = enable != 0;
+  if (reset) g_tune.clear();
+  if (n_entries) *n_entries = (int)g_tune.size();
+  if (text && text_len > 0) {
+    std::string t;
+    for (const auto &kv : g_tune)
+      t += "M=" + std::to_string(kv.first.M) + " N=" + std::to_string(kv.first.N) + " K=" +
+           std::to_string(kv.first.K) + " group=" + std::to_string(kv.second.group) + " ms=" +
+           std::to_string(kv.second.ms) + "\n";
+    const size_t c = std::min<size_t>(t.size(), (size_t)text_len - 1);
+    std::memcpy(text, t.data(), c);
+    text[c] = 0;
+  }
+  return VB_OK;
+}

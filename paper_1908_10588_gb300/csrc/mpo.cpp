@@ -214,6 +214,17 @@ vb_status mpo_build(const vb_model *m, vb_mpo **out) {
   mpo->el_pos = el_pos;
   mpo->dims = dims;
   mpo->pos_of_mode = pos_of_mode;
+  mpo->ch_start.assign(n + 1, -1);
+  mpo->ch_done.assign(n + 1, -1);
+  for (int b = 0; b <= n; ++b) {
+    auto it = chan[b].find(K_START);
+    if (it != chan[b].end()) mpo->ch_start[b] = it->second;
+    it = chan[b].find(K_DONE);
+    if (it != chan[b].end()) mpo->ch_done[b] = it->second;
+  }
+  mpo->e_zpe = 0.0;
+  if (m->include_zpe)
+    for (int k = 0; k < nm; ++k) mpo->e_zpe += 0.5 * m->omega[k];
   mpo->sites.resize(n);
   for (int p = 0; p < n; ++p) {
     const std::map<Key, int> &cin = chan[p], &cout = chan[p + 1];
@@ -351,6 +362,16 @@ vb_status mpo_upload(const vb_mpo *cmpo) {
     VB_TRY(up(S.csr_col.data(), S.csr_col.size() * sizeof(int), (void **)&S.d_csr_col));
     VB_TRY(up(S.csr_val.data(), S.csr_val.size() * sizeof(double), (void **)&S.d_csr_val));
     std::vector<float> val32(S.csr_val.begin(), S.csr_val.end());
+    if (&S == &mpo->sites[0] && mpo->e_zpe != 0.0 && mpo->n > 1) {
+      // the mixed form's operators without the zero-point constant: site 0's
+      // local block (first channel in, DONE channel out) loses e_zpe on its diagonal
+      const int done = mpo->ch_done[1];
+      for (const MpoBlock &B : S.blocks)
+        if (B.win == 0 && B.wout == done && !B.ident)
+          for (int r = 0; r < S.d; ++r)
+            for (int k = S.csr_ptr[B.op_off + r]; k < S.csr_ptr[B.op_off + r + 1]; ++k)
+              if (S.csr_col[k] == r) val32[k] = (float)(S.csr_val[k] - mpo->e_zpe);
+    }
     VB_TRY(up(val32.data(), val32.size() * sizeof(float), (void **)&S.d_csr_val32));
     for (int dir = 0; dir < 2; ++dir) {
       int np = dir == 0 ? S.wr : S.wl;

@@ -10,6 +10,7 @@
 // bcap_b = min(m_cap, full dimension of bond b) bounds every bond.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -60,6 +61,20 @@ __global__ void transpose_kernel(const cd *src, int k, int n, cd *dst) {
     int i = (int)(e / k), a = (int)(e % k);
     dst[e] = src[(long long)a * n + i];
   }
+}
+
+// y += a x (a real)
+__global__ void add_scaled_kernel(cd *__restrict__ y, const cd *__restrict__ x, double a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = mkc(y[i].x + a * x[i].x, y[i].y + a * x[i].y);
+}
+
+// x *= exp(-i phi)
+__global__ void phase_kernel(cd *x, long long n, double phi) {
+  double sn, cs;
+  sincos(phi, &sn, &cs);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = mkc(cs * x[i].x + sn * x[i].y, cs * x[i].y - sn * x[i].x);
 }
 
 __global__ void conj_copy_kernel(const cd *src, long long n, cd *dst) {
@@ -439,6 +454,17 @@ vb_status heff0_fp64(const vb_mpo *mpo, int site, int ma, int mb, const cd *L, c
   h.a_size = t_cap; h.b_size = (long long)mb * w * mb; h.c_size = (long long)ma * mb;
   h.ws = ws; h.ws_elems = ws_elems;  // one output tile, K = w m: split-K
   return zgemm(h, st);
+}
+
+// The mixed form's FP32 operators leave out the zero-point constant e_zpe of
+// the Hamiltonian (vb_mpo::e_zpe); a mixed sweep of length dt restores it as
+// the exact global phase exp(-i e_zpe dt / hbar) on the center (site 0).
+vb_status zero_point_phase(vb_mps *s, double dt_fs) {
+  if (s->dtype != VB_MIXED || s->mpo->e_zpe == 0.0) return VB_OK;
+  const long long el = (long long)s->bond[0] * s->dims[0] * s->bond[1];
+  phase_kernel<<<grid1(el), 256, 0, s->st>>>(s->A[0], el, s->mpo->e_zpe * dt_fs / HBAR_EV_FS);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
 }
 
 // Reads the flag a mixed-form tensor-core kernel raises when one of its
@@ -1517,6 +1543,7 @@ vb_status tdvp2_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
       VB_TRY(evolve(op1, s->A[i], (long long)mL * d1 * k, -tau));
     }
   }
+  VB_TRY(zero_point_phase(s, dt_fs));
   VB_TRY_CUDA(cudaStreamSynchronize(s->st));
   prof_collect();
   VB_TRY(take_wait_flag(s, "tdvp2_sweep"));
@@ -1602,6 +1629,7 @@ vb_status tdvp1_sweep(vb_mps *s, const vb_mpo *mpo, double dt_fs, const vb_tdvp_
     VB_TRY(zgemm(g, st));
     VB_TRY_CUDA(cudaMemcpyAsync(s->A[i - 1], s->theta, n0 * mL * sizeof(cd), cudaMemcpyDeviceToDevice, st));
   }
+  VB_TRY(zero_point_phase(s, dt_fs));
   VB_TRY_CUDA(cudaStreamSynchronize(st));
   VB_TRY(take_wait_flag(s, "tdvp1_sweep"));
   ss.max_bond = 1;
@@ -1664,7 +1692,9 @@ vb_status tdvp2_sweep_batched(vb_mps *const *mps, const vb_mpo *const *mpo, int 
   std::vector<std::string> msg(count);
   auto run = [&](int i) {
     vb_sweep_stats st{};
-    rc[i] = tdvp2_sweep(mps[i], mpo[i], dt_fs, opts, &st);
+    vb_tdvp_opts oi = *opts;  // the bond cap of each instance: min(m_max, its m_cap)
+    oi.m_max = std::min(opts->m_max, mps[i]->m_cap);
+    rc[i] = tdvp2_sweep(mps[i], mpo[i], dt_fs, &oi, &st);
     if (rc[i] != VB_OK) msg[i] = vb_last_error();
     if (stats) stats[i] = st;
   };
@@ -1748,6 +1778,11 @@ vb_status vb_heff2_apply(const vb_mpo *mpo, int i, int mL, int mR, const double 
     VB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     VB_TRY(heff_mixed_apply(mpo, i, 1, mL, mR, (const cd *)L, (const cd *)R, (const cd *)theta, (cd *)y, work,
                             vb_heff_work_elems(mpo, i, mL, mR, 1) * sizeof(cd), err, st));
+    if (i == 0 && mpo->e_zpe != 0.0) {  // site 0's FP32 operator leaves out the zero-point constant
+      const long long el = (long long)mL * mpo->dims[0] * mpo->dims[1] * mR;
+      add_scaled_kernel<<<grid1(el), 256, 0, st>>>((cd *)y, (const cd *)theta, mpo->e_zpe, el);
+      VB_CHECK_LAUNCH();
+    }
     int h = 0;
     VB_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     VB_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1772,6 +1807,11 @@ vb_status vb_heff1_apply(const vb_mpo *mpo, int j, int mL, int mR, const double 
     VB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     VB_TRY(heff_mixed_apply(mpo, j, 0, mL, mR, (const cd *)L, (const cd *)R, (const cd *)C, (cd *)y, work,
                             vb_heff_work_elems(mpo, j, mL, mR, 0) * sizeof(cd), err, st));
+    if (j == 0 && mpo->e_zpe != 0.0) {  // site 0's FP32 operator leaves out the zero-point constant
+      const long long el = (long long)mL * mpo->dims[0] * mR;
+      add_scaled_kernel<<<grid1(el), 256, 0, st>>>((cd *)y, (const cd *)C, mpo->e_zpe, el);
+      VB_CHECK_LAUNCH();
+    }
     int h = 0;
     VB_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     VB_TRY_CUDA(cudaStreamSynchronize(st));
@@ -2212,5 +2252,546 @@ extern "C" vb_status tdvp2_population_gradient(vb_mps *psi, const vb_mpo *mpo, d
     for (int k = 0; k < n_samples; ++k) acc += w[k] * f[(size_t)u * n_samples + k].y;
     grad_out[order[u]] = scale * acc;
   }
+  return VB_OK;
+}
+
+// ===========================================================================
+// Global Krylov step (Sec. 2.1.2, Eqs. Krylov subspace and global Krylov),
+// with the direct MPO application (Sec. 2.1.1, Eqs. direct app 1/2), the
+// compression and the MPS sums it needs, on the GPU. Used for a few
+// pre-steps that grow the bonds of a product state before one-site TDVP.
+//   k_0 = psi/|psi|, k_{j+1} = compress(H k_j)/|.|   (Krylov vectors as MPSs)
+//   S_ij = <k_i|k_j>, H_ij = <k_i|H k_j>             (H k_j uncompressed)
+//   S = L L^+, X = L^{-+}: Krylov-ordered orthonormal basis u = k X,
+//   H_r = X^+ H X, b = X^+ S e_0, c = X exp(-i H_r dt/hbar) b
+//   psi(t + dt) = compress(sum_j c_j k_j) scaled to |psi|.
+// The Krylov vectors live in device tensors of their own (bond dimensions
+// are not bounded by the handle's caps while the basis is built); only the
+// result must fit the handle. Compression: Gram matrices of the left parts
+// (G_{p+1} = sum_s A_p[s]^+ G_p A_p[s]), then right to left the site matrix
+// M (the site times what was carried from the right) gives the reduced
+// density matrix rho = M^+ G_p M of its left bond, whose leading eigenvectors
+// (FP64 eigensolver, the 2TDVP split's truncation rule) become the new
+// right-orthonormal site and M V_k is carried left. All contractions are
+// complex FP64 GEMMs; the r x r algebra runs on the host in double.
+// ===========================================================================
+namespace vb {
+namespace {
+
+struct DevMps {
+  std::vector<int> bond;  // [n + 1], bond[0] = bond[n] = 1
+  std::vector<cd *> A;    // device [bond[p]][d_p][bond[p + 1]]
+};
+
+vb_status dm_alloc(DevMps &m, const std::vector<int> &bond, const std::vector<int> &dims, Scratch &sc) {
+  const int n = (int)dims.size();
+  m.bond = bond;
+  m.A.assign(n, nullptr);
+  for (int p = 0; p < n; ++p)
+    VB_TRY(sc.get((void **)&m.A[p], (size_t)bond[p] * dims[p] * bond[p + 1] * sizeof(cd)));
+  return VB_OK;
+}
+
+// out[(w a), s, (v b)] = sum_t W[w, s, t, v] A[a, t, b]  (W real)
+__global__ void apply_mpo_site_kernel(const double *__restrict__ W, int wl, int d, int wr, const cd *__restrict__ A,
+                                      int ml, int mr, cd *__restrict__ out) {
+  const long long tot = (long long)wl * ml * d * wr * mr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    long long t = e;
+    const int b = (int)(t % mr);
+    t /= mr;
+    const int v = (int)(t % wr);
+    t /= wr;
+    const int s = (int)(t % d);
+    t /= d;
+    const int a = (int)(t % ml);
+    const int w = (int)(t / ml);
+    const double *Wr = W + ((long long)(w * d + s) * d) * wr + v;
+    cd acc = mkc(0.0, 0.0);
+    for (int u = 0; u < d; ++u) {
+      const double c = Wr[(long long)u * wr];
+      if (c != 0.0) {
+        const cd x = A[((long long)a * d + u) * mr + b];
+        acc = mkc(acc.x + c * x.x, acc.y + c * x.y);
+      }
+    }
+    out[e] = acc;
+  }
+}
+
+int grid_of_elems(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+
+vb_status dm_apply_mpo(const vb_mpo *mpo, const std::vector<double *> &Wd, const DevMps &in, DevMps &out,
+                       Scratch &sc, cudaStream_t st) {
+  const int n = mpo->n;
+  std::vector<int> bond(n + 1, 1);
+  for (int p = 0; p <= n; ++p) {
+    const int w = p == 0 ? 1 : (p == n ? 1 : mpo->sites[p].wl);
+    bond[p] = in.bond[p] * w;
+  }
+  VB_TRY(dm_alloc(out, bond, mpo->dims, sc));
+  for (int p = 0; p < n; ++p) {
+    const MpoSite &S = mpo->sites[p];
+    const long long tot = (long long)S.wl * in.bond[p] * S.d * S.wr * in.bond[p + 1];
+    apply_mpo_site_kernel<<<grid_of_elems(tot), 256, 0, st>>>(Wd[p], S.wl, S.d, S.wr, in.A[p], in.bond[p],
+                                                              in.bond[p + 1], out.A[p]);
+    VB_CHECK_LAUNCH();
+  }
+  return VB_OK;
+}
+
+// <a|b> on the device (out: one complex)
+vb_status dm_overlap(const DevMps &a, const DevMps &b, const std::vector<int> &dims, cd *out, Scratch &sc,
+                     cudaStream_t st) {
+  const int n = (int)dims.size();
+  long long e_cap = 1, x_cap = 1;
+  for (int p = 0; p <= n; ++p) e_cap = std::max<long long>(e_cap, (long long)a.bond[p] * b.bond[p]);
+  for (int p = 0; p < n; ++p) x_cap = std::max<long long>(x_cap, (long long)a.bond[p] * dims[p] * b.bond[p + 1]);
+  cd *E0 = nullptr, *E1 = nullptr, *X = nullptr;
+  VB_TRY(sc.get((void **)&E0, e_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&E1, e_cap * sizeof(cd)));
+  VB_TRY(sc.get((void **)&X, x_cap * sizeof(cd)));
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  VB_TRY_CUDA(cudaMemcpyAsync(E0, &one, sizeof(cd), cudaMemcpyHostToDevice, st));
+  for (int p = 0; p < n; ++p) {
+    const int xa = a.bond[p], ya = a.bond[p + 1], xb = b.bond[p], yb = b.bond[p + 1], d = dims[p];
+    GemmArgs g{};
+    g.M = xa; g.N = d * yb; g.K = xb; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = E0; g.lda = xb; g.B = b.A[p]; g.ldb = (long long)d * yb; g.C = X; g.ldc = (long long)d * yb;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)xa * xb; g.b_size = (long long)xb * d * yb; g.c_size = x_cap;
+    VB_TRY(zgemm(g, st));
+    GemmArgs h{};
+    h.M = ya; h.N = yb; h.K = xa * d; h.batch = 1; h.opA = OP_C; h.opB = OP_N;
+    h.A = a.A[p]; h.lda = ya; h.B = X; h.ldb = yb; h.C = E1; h.ldc = yb;
+    h.alpha = one; h.beta = zero;
+    h.a_size = (long long)xa * d * ya; h.b_size = x_cap; h.c_size = e_cap;
+    VB_TRY(zgemm(h, st));
+    std::swap(E0, E1);
+  }
+  VB_TRY_CUDA(cudaMemcpyAsync(out, E0, sizeof(cd), cudaMemcpyDeviceToDevice, st));
+  return VB_OK;
+}
+
+__global__ void scale_kernel(cd *x, long long n, cd c) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = cmul(x[i], c);
+}
+
+// compress `in` into a right-canonical `out` (norm on site 0) with the 2TDVP
+// split's truncation rule; *disc = summed relative discarded weight
+vb_status dm_compress(const DevMps &in, const std::vector<int> &dims, const TruncOpts &o, DevMps &out, double *disc,
+                      Scratch &sc, cudaStream_t st) {
+  const int n = (int)dims.size();
+  const cd one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  *disc = 0.0;
+  // Gram matrices of the left parts: G[p] (bond[p] x bond[p]), sites < p
+  std::vector<cd *> G(n, nullptr);
+  long long x_cap = 1;
+  for (int p = 0; p < n; ++p) x_cap = std::max<long long>(x_cap, (long long)in.bond[p] * dims[p] * in.bond[p + 1]);
+  cd *X = nullptr, *T = nullptr;
+  VB_TRY(sc.get((void **)&X, x_cap * sizeof(cd)));
+  for (int p = 0; p < n; ++p) VB_TRY(sc.get((void **)&G[p], (size_t)in.bond[p] * in.bond[p] * sizeof(cd)));
+  VB_TRY_CUDA(cudaMemcpyAsync(G[0], &one, sizeof(cd), cudaMemcpyHostToDevice, st));
+  for (int p = 0; p + 1 < n; ++p) {
+    const int x = in.bond[p], y = in.bond[p + 1], d = dims[p];
+    GemmArgs g{};  // X[x', (s y)] = G[x', x] A[x, (s y)]
+    g.M = x; g.N = d * y; g.K = x; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = G[p]; g.lda = x; g.B = in.A[p]; g.ldb = (long long)d * y; g.C = X; g.ldc = (long long)d * y;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)x * x; g.b_size = (long long)x * d * y; g.c_size = x_cap;
+    VB_TRY(zgemm(g, st));
+    GemmArgs h{};  // G'[y', y] = sum conj(A[(x' s), y']) X[(x' s), y]
+    h.M = y; h.N = y; h.K = x * d; h.batch = 1; h.opA = OP_C; h.opB = OP_N;
+    h.A = in.A[p]; h.lda = y; h.B = X; h.ldb = y; h.C = G[p + 1]; h.ldc = y;
+    h.alpha = one; h.beta = zero;
+    h.a_size = (long long)x * d * y; h.b_size = x_cap; h.c_size = (long long)y * y;
+    VB_TRY(zgemm(h, st));
+  }
+  // right to left: carried matrix C (bond[p + 1] x k), new sites into out
+  std::vector<int> nb(n + 1, 1);
+  std::vector<cd *> B(n, nullptr);
+  cd *C = nullptr;
+  VB_TRY(sc.get((void **)&C, sizeof(cd)));
+  VB_TRY_CUDA(cudaMemcpyAsync(C, &one, sizeof(cd), cudaMemcpyHostToDevice, st));
+  int kprev = 1;
+  double *d_ev = nullptr, *d_tr = nullptr;
+  VB_TRY(sc.get((void **)&d_tr, sizeof(double)));
+  for (int p = n - 1; p >= 1; --p) {
+    const int ml = in.bond[p], mr = in.bond[p + 1], d = dims[p];
+    const int nr = d * kprev;  // columns of M
+    cd *M = nullptr, *rho = nullptr, *evec = nullptr, *Cn = nullptr;
+    VB_TRY(sc.get((void **)&M, (size_t)ml * nr * sizeof(cd)));
+    VB_TRY(sc.get((void **)&T, (size_t)ml * nr * sizeof(cd)));
+    VB_TRY(sc.get((void **)&rho, (size_t)nr * nr * sizeof(cd)));
+    GemmArgs g{};  // M[(x s), j] = A[(x s), y] C[y, j]
+    g.M = ml * d; g.N = kprev; g.K = mr; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = in.A[p]; g.lda = mr; g.B = C; g.ldb = kprev; g.C = M; g.ldc = kprev;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)ml * d * mr; g.b_size = (long long)mr * kprev; g.c_size = (long long)ml * nr;
+    VB_TRY(zgemm(g, st));
+    GemmArgs h{};  // T = G M  (ml x nr)
+    h.M = ml; h.N = nr; h.K = ml; h.batch = 1; h.opA = OP_N; h.opB = OP_N;
+    h.A = G[p]; h.lda = ml; h.B = M; h.ldb = nr; h.C = T; h.ldc = nr;
+    h.alpha = one; h.beta = zero;
+    h.a_size = (long long)ml * ml; h.b_size = (long long)ml * nr; h.c_size = (long long)ml * nr;
+    VB_TRY(zgemm(h, st));
+    GemmArgs r{};  // rho = M^+ T  (nr x nr)
+    r.M = nr; r.N = nr; r.K = ml; r.batch = 1; r.opA = OP_C; r.opB = OP_N;
+    r.A = M; r.lda = nr; r.B = T; r.ldb = nr; r.C = rho; r.ldc = nr;
+    r.alpha = one; r.beta = zero;
+    r.a_size = (long long)ml * nr; r.b_size = (long long)ml * nr; r.c_size = (long long)nr * nr;
+    VB_TRY(zgemm(r, st));
+    trace_kernel<<<1, 256, 0, st>>>(rho, nr, d_tr);
+    VB_CHECK_LAUNCH();
+    const int kw = std::min(nr, o.m_max + 1);
+    void *work = nullptr;
+    VB_TRY(sc.get(&work, EigWork::bytes(nr, kw)));
+    VB_TRY(sc.get((void **)&d_ev, (size_t)kw * sizeof(double)));
+    VB_TRY(eig_values(nr, rho, kw, d_ev, work, st));
+    std::vector<double> lam(kw);
+    double tot = 0.0;
+    VB_TRY_CUDA(cudaMemcpyAsync(lam.data(), d_ev, kw * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VB_TRY_CUDA(cudaMemcpyAsync(&tot, d_tr, sizeof(double), cudaMemcpyDeviceToHost, st));
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    VB_TRY(EigWork::check(nr, kw, sizeof(double), work, st));
+    for (double &x : lam) x = std::max(x, 0.0);
+    // the Schmidt rank is also bounded by the full dimension of the sites to
+    // the left (the input's own bond may be far larger, e.g. w m after H)
+    long long left_full = 1;
+    for (int q = 0; q < p && left_full < (1LL << 30); ++q) left_full *= dims[q];
+    const int rank_bound = (int)std::min<long long>(std::min(ml, nr), left_full);
+    double dd = 0.0;
+    const int k = choose_rank(lam, nr, tot, rank_bound, o, &dd);
+    *disc += dd;
+    VB_TRY(sc.get((void **)&evec, (size_t)k * nr * sizeof(cd)));
+    VB_TRY(eig_vectors(nr, rho, kw, k, d_ev, evec, work, st));
+    // new site: rows conj(v_j) (k x d x kprev), right-orthonormal
+    VB_TRY(sc.get((void **)&B[p], (size_t)k * nr * sizeof(cd)));
+    conj_copy_kernel<<<grid_of_elems((long long)k * nr), 256, 0, st>>>(evec, (long long)k * nr, B[p]);
+    VB_CHECK_LAUNCH();
+    // carried: C' = M V_k  (ml x k), V_k[(s j'), j] = evec[j][(s j')]
+    VB_TRY(sc.get((void **)&Cn, (size_t)ml * k * sizeof(cd)));
+    GemmArgs c{};
+    c.M = ml; c.N = k; c.K = nr; c.batch = 1; c.opA = OP_N; c.opB = OP_T;
+    c.A = M; c.lda = nr; c.B = evec; c.ldb = nr; c.C = Cn; c.ldc = k;
+    c.alpha = one; c.beta = zero;
+    c.a_size = (long long)ml * nr; c.b_size = (long long)k * nr; c.c_size = (long long)ml * k;
+    VB_TRY(zgemm(c, st));
+    C = Cn;
+    kprev = k;
+    nb[p] = k;
+  }
+  // site 0 absorbs the carried matrix
+  {
+    const int d = dims[0], mr = in.bond[1];
+    VB_TRY(sc.get((void **)&B[0], (size_t)d * kprev * sizeof(cd)));
+    GemmArgs g{};
+    g.M = d; g.N = kprev; g.K = mr; g.batch = 1; g.opA = OP_N; g.opB = OP_N;
+    g.A = in.A[0]; g.lda = mr; g.B = C; g.ldb = kprev; g.C = B[0]; g.ldc = kprev;
+    g.alpha = one; g.beta = zero;
+    g.a_size = (long long)d * mr; g.b_size = (long long)mr * kprev; g.c_size = (long long)d * kprev;
+    VB_TRY(zgemm(g, st));
+  }
+  out.bond = nb;
+  out.A = B;
+  return VB_OK;
+}
+
+// sum_j c_j |k_j> (block tensors: site 0 side by side with the c_j, the
+// last site stacked, the others block-diagonal)
+__global__ void put_block_kernel(const cd *__restrict__ src, int sl, int d, int sr, cd *__restrict__ dst, int dl,
+                                 int dr, int r0, int c0, cd scale) {
+  const long long tot = (long long)sl * d * sr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(e % sr);
+    const long long t = e / sr;
+    const int s = (int)(t % d);
+    const int x = (int)(t / d);
+    dst[((long long)(r0 + x) * d + s) * dr + c0 + y] = cmul(src[e], scale);
+  }
+}
+
+vb_status dm_sum(const std::vector<std::complex<double>> &c, const std::vector<DevMps> &K, const std::vector<int> &dims,
+                 DevMps &out, Scratch &sc, cudaStream_t st) {
+  const int n = (int)dims.size(), m = (int)c.size();
+  std::vector<int> bond(n + 1, 1);
+  for (int p = 1; p < n; ++p) {
+    bond[p] = 0;
+    for (int j = 0; j < m; ++j) bond[p] += K[j].bond[p];
+  }
+  VB_TRY(dm_alloc(out, bond, dims, sc));
+  for (int p = 0; p < n; ++p)
+    VB_TRY_CUDA(cudaMemsetAsync(out.A[p], 0, (size_t)bond[p] * dims[p] * bond[p + 1] * sizeof(cd), st));
+  std::vector<int> r0(n + 1, 0);
+  for (int j = 0; j < m; ++j) {
+    for (int p = 0; p < n; ++p) {
+      const int sl = K[j].bond[p], sr = K[j].bond[p + 1];
+      const int ro = p == 0 ? 0 : r0[p], co = p == n - 1 ? 0 : r0[p + 1];
+      const cd scale = p == 0 ? mkc(c[j].real(), c[j].imag()) : mkc(1.0, 0.0);
+      put_block_kernel<<<grid_of_elems((long long)sl * dims[p] * sr), 256, 0, st>>>(
+          K[j].A[p], sl, dims[p], sr, out.A[p], bond[p], bond[p + 1], ro, co, scale);
+      VB_CHECK_LAUNCH();
+    }
+    for (int p = 1; p < n; ++p) r0[p] += K[j].bond[p];
+  }
+  return VB_OK;
+}
+
+// ---- small dense complex Hermitian algebra on the host (r <= 64)
+typedef std::complex<double> zc;
+
+// cyclic Jacobi: A (r x r Hermitian, row-major) -> eigenvalues lam, eigenvectors as columns of V
+void herm_jacobi(std::vector<zc> A, int r, std::vector<double> &lam, std::vector<zc> &V) {
+  V.assign((size_t)r * r, zc(0.0, 0.0));
+  for (int i = 0; i < r; ++i) V[(size_t)i * r + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int p = 0; p < r; ++p)
+      for (int q = 0; q < r; ++q) (p == q ? dia : off) += std::norm(A[(size_t)p * r + q]);
+    if (off <= 1e-30 * std::max(dia, 1e-300)) break;
+    for (int p = 0; p < r; ++p)
+      for (int q = p + 1; q < r; ++q) {
+        const zc apq = A[(size_t)p * r + q];
+        const double g = std::abs(apq);
+        if (g == 0.0) continue;
+        const double app = A[(size_t)p * r + p].real(), aqq = A[(size_t)q * r + q].real();
+        const double theta = 0.5 * std::atan2(2.0 * g, aqq - app);
+        const double cs = std::cos(theta), sn = std::sin(theta);
+        const zc ph = apq / g;  // e^{i phi}
+        // rotation: columns p, q of A and V: a_p' = cs a_p - sn conj(ph) a_q ... (unitary J)
+        for (int k = 0; k < r; ++k) {
+          const zc akp = A[(size_t)k * r + p], akq = A[(size_t)k * r + q];
+          A[(size_t)k * r + p] = cs * akp - sn * std::conj(ph) * akq;
+          A[(size_t)k * r + q] = sn * ph * akp + cs * akq;
+        }
+        for (int k = 0; k < r; ++k) {
+          const zc apk = A[(size_t)p * r + k], aqk = A[(size_t)q * r + k];
+          A[(size_t)p * r + k] = cs * apk - sn * ph * aqk;
+          A[(size_t)q * r + k] = sn * std::conj(ph) * apk + cs * aqk;
+        }
+        for (int k = 0; k < r; ++k) {
+          const zc vkp = V[(size_t)k * r + p], vkq = V[(size_t)k * r + q];
+          V[(size_t)k * r + p] = cs * vkp - sn * std::conj(ph) * vkq;
+          V[(size_t)k * r + q] = sn * ph * vkp + cs * vkq;
+        }
+      }
+  }
+  lam.resize(r);
+  for (int i = 0; i < r; ++i) lam[i] = A[(size_t)i * r + i].real();
+}
+
+// Cholesky S = L L^+ (lower); false when S is not positive definite
+bool herm_cholesky(const std::vector<zc> &S, int r, std::vector<zc> &L) {
+  L.assign((size_t)r * r, zc(0.0, 0.0));
+  for (int j = 0; j < r; ++j) {
+    double dgl = S[(size_t)j * r + j].real();
+    for (int k = 0; k < j; ++k) dgl -= std::norm(L[(size_t)j * r + k]);
+    if (!(dgl > 0.0)) return false;
+    const double ljj = std::sqrt(dgl);
+    L[(size_t)j * r + j] = ljj;
+    for (int i = j + 1; i < r; ++i) {
+      zc s = S[(size_t)i * r + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * r + k] * std::conj(L[(size_t)j * r + k]);
+      L[(size_t)i * r + j] = s / ljj;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+}  // namespace vb
+
+extern "C" vb_status global_krylov_step(vb_mps *psi, const vb_mpo *mpo, double dt_fs, const vb_tdvp_opts *opts,
+                                        int r_max, double tol, vb_krylov_info *info) {
+  using namespace vb;
+  if (!psi || !mpo || !opts) return fail(VB_EINVAL, "global_krylov_step: null argument");
+  if (mpo != psi->mpo) return fail(VB_EINVAL, "global_krylov_step: MPS was created for another MPO");
+  if (psi->center != 0) return fail(VB_ESTATE, "global_krylov_step: center is not on site 0");
+  if (r_max < 1 || r_max > 40 || !(tol > 0.0) || opts->m_max < 1 || opts->m_max > psi->m_cap)
+    return fail(VB_EINVAL, "global_krylov_step: r_max in 1..40, tol > 0, m_max in 1..m_cap");
+  if (psi->n < 2) return fail(VB_EINVAL, "global_krylov_step: needs at least two sites");
+  VB_TRY(set_device_of(psi));
+  cudaStream_t st = psi->st;
+  vb::Alloc al = psi->alloc;
+  Scratch sc(&al);
+  const int n = psi->n;
+  const std::vector<int> &dims = psi->dims;
+  const TruncOpts to{opts->m_max, opts->eps, opts->zero_floor};
+  vb_krylov_info inf{};
+  // dense MPO tensors on the device
+  std::vector<double *> Wd(n, nullptr);
+  for (int p = 0; p < n; ++p) {
+    const MpoSite &S = mpo->sites[p];
+    VB_TRY(sc.get((void **)&Wd[p], S.dense.size() * sizeof(double)));
+    VB_TRY_CUDA(cudaMemcpyAsync(Wd[p], S.dense.data(), S.dense.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  cd *d_z = nullptr;
+  VB_TRY(sc.get((void **)&d_z, sizeof(cd)));
+  auto overlap = [&](const DevMps &a, const DevMps &b, zc *v) -> vb_status {
+    VB_TRY(dm_overlap(a, b, dims, d_z, sc, st));
+    cd h;
+    VB_TRY_CUDA(cudaMemcpyAsync(&h, d_z, sizeof(cd), cudaMemcpyDeviceToHost, st));
+    VB_TRY_CUDA(cudaStreamSynchronize(st));
+    *v = zc(h.x, h.y);
+    return VB_OK;
+  };
+  auto scale0 = [&](DevMps &a, zc c) {
+    const long long el = (long long)a.bond[0] * dims[0] * a.bond[1];
+    scale_kernel<<<grid_of_elems(el), 256, 0, st>>>(a.A[0], el, mkc(c.real(), c.imag()));
+  };
+  // k_0 = psi / |psi| (its own copy)
+  DevMps k0;
+  VB_TRY(dm_alloc(k0, psi->bond, dims, sc));
+  for (int p = 0; p < n; ++p)
+    VB_TRY_CUDA(cudaMemcpyAsync(k0.A[p], psi->A[p], (size_t)psi->bond[p] * dims[p] * psi->bond[p + 1] * sizeof(cd),
+                                cudaMemcpyDeviceToDevice, st));
+  zc nn0;
+  VB_TRY(overlap(k0, k0, &nn0));
+  const double nrm = std::sqrt(std::abs(nn0.real()));
+  if (nrm == 0.0) return fail(VB_EINVAL, "global_krylov_step: zero state");
+  scale0(k0, zc(1.0 / nrm, 0.0));
+  VB_CHECK_LAUNCH();
+  std::vector<DevMps> K{k0}, HK;
+  std::vector<zc> S(1, zc(1.0, 0.0)), Hm;
+  std::vector<zc> cvec;
+  auto solve = [&](int m, std::vector<zc> &c, std::vector<zc> &ub) -> bool {
+    std::vector<zc> L;
+    if (!herm_cholesky(S, m, L)) return false;
+    // X = L^{-+}: solve L^+ X = I (upper triangular)
+    std::vector<zc> X((size_t)m * m, zc(0.0, 0.0));
+    for (int col = 0; col < m; ++col)
+      for (int i = m - 1; i >= 0; --i) {
+        zc s = (i == col) ? zc(1.0, 0.0) : zc(0.0, 0.0);
+        for (int k = i + 1; k < m; ++k) s -= std::conj(L[(size_t)k * m + i]) * X[(size_t)k * m + col];
+        X[(size_t)i * m + col] = s / std::conj(L[(size_t)i * m + i]);
+      }
+    std::vector<zc> Hr((size_t)m * m, zc(0.0, 0.0)), T((size_t)m * m, zc(0.0, 0.0));
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        for (int k = 0; k < m; ++k) T[(size_t)i * m + j] += Hm[(size_t)i * m + k] * X[(size_t)k * m + j];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        for (int k = 0; k < m; ++k) Hr[(size_t)i * m + j] += std::conj(X[(size_t)k * m + i]) * T[(size_t)k * m + j];
+    for (int i = 0; i < m; ++i)
+      for (int j = i; j < m; ++j) {
+        const zc a = 0.5 * (Hr[(size_t)i * m + j] + std::conj(Hr[(size_t)j * m + i]));
+        Hr[(size_t)i * m + j] = a;
+        Hr[(size_t)j * m + i] = std::conj(a);
+      }
+    std::vector<double> lam;
+    std::vector<zc> V;
+    herm_jacobi(Hr, m, lam, V);
+    std::vector<zc> b(m, zc(0.0, 0.0));
+    for (int i = 0; i < m; ++i)
+      for (int k = 0; k < m; ++k) b[i] += std::conj(X[(size_t)k * m + i]) * S[(size_t)k * m + 0];
+    std::vector<zc> y(m, zc(0.0, 0.0));
+    for (int a = 0; a < m; ++a) {
+      zc s(0.0, 0.0);
+      for (int i = 0; i < m; ++i) s += std::conj(V[(size_t)i * m + a]) * b[i];
+      y[a] = std::exp(zc(0.0, -lam[a] * dt_fs / HBAR_EV_FS)) * s;
+    }
+    ub.assign(m, zc(0.0, 0.0));
+    for (int i = 0; i < m; ++i)
+      for (int a = 0; a < m; ++a) ub[i] += V[(size_t)i * m + a] * y[a];
+    c.assign(m, zc(0.0, 0.0));
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) c[i] += X[(size_t)i * m + j] * ub[j];
+    return true;
+  };
+  // H_00 through H k_0 (the first uncompressed vector)
+  {
+    DevMps hk;
+    VB_TRY(dm_apply_mpo(mpo, Wd, K[0], hk, sc, st));
+    HK.push_back(hk);
+    zc h;
+    VB_TRY(overlap(K[0], HK[0], &h));
+    Hm.assign(1, h);
+  }
+  std::vector<zc> ub;
+  if (!solve(1, cvec, ub)) return fail(VB_ECUDA, "global_krylov_step: Gram matrix not positive");
+  for (int r = 1; r <= r_max; ++r) {
+    DevMps nxt;
+    double dd = 0.0;
+    VB_TRY(dm_compress(HK.back(), dims, to, nxt, &dd, sc, st));
+    zc nn;
+    VB_TRY(overlap(nxt, nxt, &nn));
+    if (nn.real() <= 0.0) {
+      inf.converged = 1;
+      break;
+    }
+    scale0(nxt, zc(1.0 / std::sqrt(nn.real()), 0.0));
+    VB_CHECK_LAUNCH();
+    const int m = (int)K.size() + 1;
+    std::vector<zc> S2((size_t)m * m);
+    for (int i = 0; i < m - 1; ++i)
+      for (int j = 0; j < m - 1; ++j) S2[(size_t)i * m + j] = S[(size_t)i * (m - 1) + j];
+    for (int i = 0; i < m - 1; ++i) {
+      zc v;
+      VB_TRY(overlap(K[i], nxt, &v));
+      S2[(size_t)i * m + m - 1] = v;
+      S2[(size_t)(m - 1) * m + i] = std::conj(v);
+    }
+    S2[(size_t)(m - 1) * m + m - 1] = zc(1.0, 0.0);
+    std::vector<double> ev;
+    std::vector<zc> Vs;
+    herm_jacobi(S2, m, ev, Vs);
+    const double emin = *std::min_element(ev.begin(), ev.end()), emax = *std::max_element(ev.begin(), ev.end());
+    if (emin <= 1e-13 * emax) {  // the new vector lies in the span: the space is invariant
+      inf.converged = 1;
+      break;
+    }
+    K.push_back(nxt);
+    S = S2;
+    inf.disc_basis += dd;
+    int mb = 1;
+    for (int p = 1; p < n; ++p) mb = std::max(mb, nxt.bond[p]);
+    inf.max_bond_basis = std::max(inf.max_bond_basis, mb);
+    // H k_{m-1} (uncompressed) and the new row / column of H
+    DevMps hk;
+    VB_TRY(dm_apply_mpo(mpo, Wd, K.back(), hk, sc, st));
+    HK.push_back(hk);
+    std::vector<zc> H2((size_t)m * m);
+    for (int i = 0; i < m - 1; ++i)
+      for (int j = 0; j < m - 1; ++j) H2[(size_t)i * m + j] = Hm[(size_t)i * (m - 1) + j];
+    for (int i = 0; i < m; ++i) {
+      zc v;
+      VB_TRY(overlap(K[i], HK[m - 1], &v));
+      H2[(size_t)i * m + m - 1] = v;
+      if (i < m - 1) {
+        zc w;
+        VB_TRY(overlap(K[m - 1], HK[i], &w));
+        H2[(size_t)(m - 1) * m + i] = w;
+      }
+    }
+    Hm = H2;
+    if (!solve(m, cvec, ub)) return fail(VB_ECUDA, "global_krylov_step: Gram matrix not positive");
+    inf.r = r;
+    if (std::abs(ub.back()) < tol) {
+      inf.converged = 1;
+      break;
+    }
+  }
+  // the new state: sum_j c_j k_j, compressed, scaled to |psi|
+  DevMps sum, out;
+  VB_TRY(dm_sum(cvec, std::vector<DevMps>(K.begin(), K.begin() + cvec.size()), dims, sum, sc, st));
+  double dd = 0.0;
+  VB_TRY(dm_compress(sum, dims, to, out, &dd, sc, st));
+  inf.disc_final = dd;
+  zc on;
+  VB_TRY(overlap(out, out, &on));
+  for (int p = 1; p < n; ++p)
+    if (out.bond[p] > psi->bcap[p])
+      return fail(VB_EINVAL, "global_krylov_step: result bond exceeds the handle's capacity");
+  scale0(out, zc(nrm / std::sqrt(on.real()), 0.0));
+  VB_CHECK_LAUNCH();
+  for (int p = 0; p < n; ++p)
+    VB_TRY_CUDA(cudaMemcpyAsync(psi->A[p], out.A[p], (size_t)out.bond[p] * dims[p] * out.bond[p + 1] * sizeof(cd),
+                                cudaMemcpyDeviceToDevice, st));
+  psi->bond = out.bond;
+  psi->center = 0;
+  VB_TRY(build_right_envs(psi));
+  VB_TRY_CUDA(cudaStreamSynchronize(st));
+  if (info) *info = inf;
   return VB_OK;
 }

@@ -131,3 +131,33 @@ def test_wait_flag_reported_and_cleared_by_both_sweeps(P):
         mps2 = P.Mps(mpo, vm.product_state_indices(m), m_cap=16, dtype=P.VB_MIXED)
         mps2.sweep(0.5, m_max=16)  # a fresh handle is unaffected
         run()  # the flag was cleared when it was reported
+
+
+def test_autotuner_picks_a_group_and_keeps_the_result(P):
+    # the L leg's resident-B GEMM at the largest pair of the internal-conversion
+    # workload (24 M tiles): the tuned group size changes only the schedule,
+    # never the arithmetic of a tile (bit-equal products)
+    m = vm.model_internal_conversion()
+    mpo = P.Mpo(m)
+    i, mL, mR = 15, 64, 64
+    wl, d1, _ = mpo.site_dims(i)
+    _, d2, wr = mpo.site_dims(i + 1)
+    rng = np.random.Generator(np.random.PCG64(901))
+    L = _dev(vm.random_hermitian_env(rng, mL, wl))
+    R = _dev(vm.random_hermitian_env(rng, mR, wr))
+    x = _dev(vm.random_complex(rng, (mL, d1, d2, mR)))
+    work = torch.zeros(P.vb_heff_work_elems(mpo, i, mL, mR, True), dtype=torch.complex128, device="cuda")
+    ys, tables = [], []
+    for enable in (1, 0):
+        P.vb_autotune(enable, reset=True)
+        y = torch.zeros_like(x)
+        for _ in range(2):  # the first call tunes, the second uses the table
+            P.vb_heff2_apply(mpo, i, mL, mR, L, R, x, y, work, P.VB_MIXED)
+        torch.cuda.synchronize()
+        ys.append(y.cpu().numpy())
+        tables.append(P.vb_autotune())
+    P.vb_autotune(1, reset=True)
+    print("autotuner table:", tables[0])
+    assert len(tables[0]) >= 1 and any("ms=-1" not in t for t in tables[0])
+    assert all("group=8" in t for t in tables[1])
+    assert np.array_equal(ys[0], ys[1])
