@@ -49,9 +49,15 @@ WORKLOAD = ("internal-conversion-like: 2 states + 24 modes (d 10-30, seed 1002),
 # GB300 FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 / bf16 tensor-core ratio
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# is now (profiles/); a kernel changed since its capture has no entry (null)
-TRAFFIC: dict = {}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernels as
+# they are now, at the workload's largest pair (profiles/heff2_mixed_ic24_launches.md);
+# a kernel changed since its capture has no entry (null)
+TRAFFIC: dict = {
+    "tc_gemm_tf32_kernel": 0.5 * (616.6e6 + 717.3e6),  # mean of the L and R leg launches
+    "sparse_legs": 1300.5e6,
+}
+TRAFFIC_CASE = ("DRAM bytes per launch at the largest pair (15, 16), mL = mR = 64, from ncu; "
+                "equal to the algorithmic bytes there (no re-reads)")
 
 
 def _peaks():
@@ -417,7 +423,7 @@ def run_ours(args):
         tc = prof["heff_tc_legs"]
         tc_ach = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else 0.0
         roof = {"bound": "tensor", "achieved": tc_ach, "peak": pk, "unit": "TFLOP/s", "frac": tc_ach / pk,
-                "traffic": TRAFFIC.get("tc_gemm_tf32_kernel"),
+                "traffic": TRAFFIC.get("tc_gemm_tf32_kernel"), "traffic_case": TRAFFIC_CASE,
                 "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio (tf32 pipe), of measured",
                 "useful_ceiling_split_tf32": pk / 3.0, "frac_of_useful_ceiling": tc_ach / (pk / 3.0),
                 "kernel": "tc_gemm_tf32_kernel (tcgen05 kind::tf32, split-TF32 x3): the dense L and R legs of "
@@ -429,6 +435,7 @@ def run_ours(args):
         roof_legs = {
             "sparse_mpo_legs": {"bound": "hbm", "achieved": w_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                 "frac": w_gbs / peaks["hbm_gbs"], "traffic": TRAFFIC.get("sparse_legs"),
+                                "traffic_case": TRAFFIC_CASE,
                                 "kernel": "sparse MPO legs (FP32, CUDA cores); algorithmic bytes = one read of "
                                           "each leg's input and one write of its output",
                                 "ms_per_step": wl["ms"] / args.steps, "launches_per_step": wl["calls"] / args.steps},
