@@ -259,6 +259,11 @@ vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cf *w, long 
                           int n_part, cudaStream_t st, unsigned int *cnt);
 vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
                                 double *out, double *partial, cudaStream_t st, unsigned int *cnt);
+// the same update without the norm, writing the FP32 copy of the new w into w32
+vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
+                           cf *w32, cudaStream_t st);
+// y = FP32 copy of x
+vb_status vec_to_c32(const cd *x, cf *y, long long n, cudaStream_t st);
 // ------------------------------------------------------------ subspace iteration
 struct SubspaceWork {
   cf *G, *W, *T;  // r x r Gram matrix, r x r transform, r x n scratch rows

@@ -326,13 +326,14 @@ __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V,
   if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
-// w[i] += sign * sum_j c[j] V32_j[i] (correction in FP32, w in FP64), then
-// |w| in FP64 by the last block (cnt: one zeroed counter)
+// w[i] += sign * sum_j c[j] V32_j[i] (correction in FP32, w in FP64); with
+// w32 != nullptr the FP32 copy of the new w is written too; with partial !=
+// nullptr |w| in FP64 by the last block (cnt: one zeroed counter)
 __global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__restrict__ V, long long ldv, int nv,
                                                                 const cd *__restrict__ c, double sign,
                                                                 cd *__restrict__ w, long long n,
                                                                 double *__restrict__ partial, unsigned int *cnt,
-                                                                double *nrm_out) {
+                                                                double *nrm_out, cf *__restrict__ w32) {
   __shared__ cf cs[128];
   __shared__ double sh[8];
   __shared__ unsigned int s_ticket;
@@ -358,14 +359,17 @@ __global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__rest
     const cd o = w[i];
     const cd r = mkc(o.x + (double)ax, o.y + (double)ay);
     w[i] = r;
+    if (w32) w32[i] = mkc((float)r.x, (float)r.y);
     nn = fma(r.x, r.x, fma(r.y, r.y, nn));
     if (two) {
       const cd o2 = w[i2];
       const cd r2 = mkc(o2.x + (double)bx, o2.y + (double)by);
       w[i2] = r2;
+      if (w32) w32[i2] = mkc((float)r2.x, (float)r2.y);
       nn = fma(r2.x, r2.x, fma(r2.y, r2.y, nn));
     }
   }
+  if (!partial) return;
   nn = warp_sum(nn);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
   __syncthreads();
@@ -695,7 +699,29 @@ vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c,
   if (nv > 128 || !cnt) return fail(VB_EINVAL, "multi_axpy32: more than 128 vectors or no counter");
   if (nv <= 0 || n == 0) return vec_norm2(w, n, out, partial, reduce_parts(n), st);
   const int blocks = (int)std::min<long long>(512, std::max<long long>(1, (n + 511) / 512));
-  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out);
+  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out, nullptr);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
+                           cf *w32, cudaStream_t st) {
+  if (nv > 128) return fail(VB_EINVAL, "multi_axpy32: more than 128 vectors");
+  if (nv <= 0 || n == 0) return VB_OK;
+  const int blocks = (int)std::min<long long>(152LL * 8, std::max<long long>(1, (n + 511) / 512));
+  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr, nullptr, nullptr, w32);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
+__global__ void to_c32_kernel(const cd *__restrict__ x, cf *__restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = mkc((float)x[i].x, (float)x[i].y);
+}
+
+vb_status vec_to_c32(const cd *x, cf *y, long long n, cudaStream_t st) {
+  if (n == 0) return VB_OK;
+  to_c32_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, y, n);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

@@ -532,21 +532,27 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
     prof_begin(PH_KRYLOV, st);
     double kbytes = 0.0;
     if (mixed) {
-      // first pass against v_{k-1}, v_k only (the three-term recurrence, FP64),
-      // then one full pass: the full pass then removes components that are
-      // already small (of the size of the FP32 error of the H_eff product),
-      // so it loses no orthogonality to cancellation and runs on the FP32
-      // copies of the vectors (FP32 products, FP64 sums and update)
+      // Gram-Schmidt on the FP32 copies of the vectors (FP32 products, FP64
+      // sums, FP32 corrections added to the FP64 w): w = H v_k comes from the
+      // FP32 tensor-core product and is only FP32-accurate itself, so FP32
+      // arithmetic here adds no error beyond it. A first pass against v_{k-1},
+      // v_k (the three-term recurrence: alpha_k, beta_k), then one full pass,
+      // which only removes components of the size of that FP32 error and so
+      // loses no orthogonality to cancellation.
       const int j0 = k > 0 ? k - 1 : 0;
       const int n1 = k + 1 - j0;
-      VB_TRY(vec_multi_dot(V + j0 * ldv, ldv, n1, w, N, s->d_c + j0, s->d_partc, np, st, s->d_cnt));
-      VB_TRY(vec_multi_axpy(V + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, st, s->w32));
-      VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
+      // bandwidth-bound: more, smaller partial blocks than the FP64 dots use
+      const int np32 = (int)std::min<long long>(512, std::max<long long>(1, (N + 1023) / 1024));
+      VB_TRY(vec_to_c32(w, s->w32, N, st));
+      VB_TRY(vec_multi_dot32(V32 + j0 * ldv, ldv, n1, s->w32, N, s->d_c + j0, s->d_partc, np32, st, s->d_cnt));
+      VB_TRY(vec_multi_axpy32(V32 + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, s->w32, st));
+      VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np32, st, s->d_cnt));
       VB_TRY(vec_multi_axpy32_norm(V32, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st,
                                    s->d_cnt + 32));
-      // algorithmic bytes: FP64 pass (read v's and w twice, write w and its
-      // FP32 copy), FP32 pass (read the copies twice, w32 once, w read and written)
-      kbytes = (double)N * (16.0 * (2 * n1 + 3) + 8.0 + 8.0 * (2 * (k + 1) + 1) + 32.0);
+      // algorithmic bytes: the FP32 copy of w (read 16, write 8), first pass
+      // (copies of v_{k-1}, v_k read twice, w32 read, w read and written, w32
+      // written), full pass (copies read twice, w32 once, w read and written)
+      kbytes = (double)N * (24.0 + 8.0 * (2 * n1 + 1) + 40.0 + 8.0 * (2 * (k + 1) + 1) + 32.0);
     } else {
       VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st, s->d_cnt));
       VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));

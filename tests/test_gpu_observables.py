@@ -140,3 +140,30 @@ def test_spectrum_of_gpu_autocorrelation(P):
     assert np.max(np.abs(got - same)) < 1e-12 * np.max(np.abs(same))
     ref = _trapezoid_closed_form(ws, es, n_t, dt, tau, E)
     assert np.max(np.abs(got - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_batch_configuration_instances_match_the_oracle(P):
+    # the batched coupling scan (64 uneven two-state models, couplings scaled
+    # 0.5..2x, per-instance bond caps): the four 8-mode instances run together
+    # through tdvp2_sweep_batched (one stream each, one shared call with the
+    # largest cap, each instance capped at its own m_cap) and match the oracle
+    # with each instance's own cap
+    batch = vm.batch_models(seed=1004, n=64)
+    pick = [i for i, (m, _) in enumerate(batch) if len(m["omega"]) == 8][:4]
+    assert len(pick) == 4
+    streams = [torch.cuda.Stream() for _ in pick]
+    states, refs = [], []
+    for i, s in zip(pick, streams):
+        m, mm = batch[i]
+        idx = vm.product_state_indices(m)
+        states.append(P.Mps(P.Mpo(m), idx, m_cap=mm, stream=s))
+        refs.append(otdvp.Tdvp2(otdvp.product_mps(vm.local_dims(m), idx), ompo.build_mpo(m),
+                                otdvp.TdvpOptions(m_max=mm)))
+    for _ in range(6):
+        stats = P.sweep_batched(states, 0.5, m_max=max(batch[i][1] for i in pick))
+        assert all(st.noconv == 0 for st in stats)
+        for r in refs:
+            r.step(0.5)
+    for q, r in zip(states, refs):
+        assert np.max(np.abs(q.populations() - otdvp.populations(r.mps))) < 1e-8
+        assert q.bond_dims() == r.mps.bond_dims()
