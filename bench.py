@@ -770,8 +770,10 @@ def run_gradient_case(args):
     family of the plain configuration extended to 24 modes (d = 8, seed
     1005), bond cap 64, 100 steps of 0.5 fs, from the product state
     (tdvp2_population_gradient: forward sweeps, costate sweeps backwards,
-    step checkpointing every 10 steps). --grad-m and --grad-params change the
-    bond cap and the number of couplings (for convergence studies). With
+    step checkpointing every 10 steps). --grad-m, --grad-params and
+    --grad-floor change the bond cap, the number of couplings and the
+    zero-weight floor of the truncation (0: every bond grows to its cap, so
+    the bond dimensions no longer depend on the couplings). With
     --fd-params k, central finite differences (step --fd-h, default 1e-5 eV)
     of the same-form propagation for couplings --fd-start .. --fd-start+k-1,
     their relative difference to the adjoint gradient, and whether the +h and
@@ -790,13 +792,15 @@ def run_gradient_case(args):
     steps, dt, m_max = 100, 0.5, args.grad_m
     st = torch.cuda.current_stream()
     out = {"case": "gradient", "model": "model_small_2state(seed=1005, n_modes=24, levels=8)", "m_max": m_max,
-           "dt_fs": dt, "steps": steps, "t_fs": steps * dt, "dtype": args.dtype, "params": "kappa_I = g^I_upper,upper"}
+           "dt_fs": dt, "steps": steps, "t_fs": steps * dt, "dtype": args.dtype, "params": "kappa_I = g^I_upper,upper",
+           "zero_floor": args.grad_floor}
     grad = None
     if not args.fd_only:
         mps = P.Mps(P.Mpo(m), idx, m_cap=m_max, dtype=dtype, stream=st)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pops, grad = mps.population_gradient(dt, steps, params[:n_par], up, m_max, checkpoint_every=10)
+        pops, grad = mps.population_gradient(dt, steps, params[:n_par], up, m_max, zero_floor=args.grad_floor,
+                                             checkpoint_every=10)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         bonds = mps.bond_dims()
@@ -818,7 +822,7 @@ def run_gradient_case(args):
                 q = P.Mps(P.Mpo(mm), idx, m_cap=m_max, dtype=dtype, stream=st)
                 seq, dw = [], 0.0
                 for _ in range(steps):
-                    s_ = q.sweep(dt, m_max=m_max)
+                    s_ = q.sweep(dt, m_max=m_max, zero_floor=args.grad_floor)
                     seq.append(tuple(q.bond_dims()))
                     dw += s_.discarded_weight
                 vals.append(q.populations()[up])
@@ -868,6 +872,7 @@ def main():
     ap.add_argument("--fd-only", action="store_true")
     ap.add_argument("--grad-m", type=int, default=64)
     ap.add_argument("--grad-params", type=int, default=24)
+    ap.add_argument("--grad-floor", type=float, default=1e-14)
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)

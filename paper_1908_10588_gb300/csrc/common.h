@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -264,6 +265,21 @@ vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, doub
                            cf *w32, cudaStream_t st);
 // y = FP32 copy of x
 vb_status vec_to_c32(const cd *x, cf *y, long long n, cudaStream_t st);
+// inner products of FP32 copies with the FP64 w rounded to FP32 on load
+vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cd *w, long long n, cd *out, cd *partial,
+                          int n_part, cudaStream_t st, unsigned int *cnt);
+// w += sign * sum_{j<n1} c1_j V1_j (n1 <= 2, FP32 correction) fused with
+// out_j = <V_j, w32> for j < nv on the updated w; partial holds partial_elems
+// complex entries, cnt one zeroed counter. axpy_dot32_blocks gives the block
+// count it would use, 0 where the sizes do not fit (then use the two passes).
+constexpr long long AXPY_DOT_CHUNK = 4096;       // elements per block aimed at
+constexpr long long AXPY_DOT_MAX_CHUNK = 12288;  // shared-memory bound (96 KB)
+constexpr long long AXPY_DOT_MAX_BLOCKS = 2048;
+constexpr long long PARTC_ELEMS = 2048LL * 64;   // complex partial sums per handle
+int axpy_dot32_blocks(long long n, int nv, long long partial_elems);
+vb_status vec_axpy_dot32(const cf *V1, int n1, const cd *c1, double sign, cd *w, long long n, const cf *V,
+                         long long ldv, int nv, cd *out, cd *partial, long long partial_elems, cudaStream_t st,
+                         unsigned int *cnt);
 // ------------------------------------------------------------ subspace iteration
 struct SubspaceWork {
   cf *G, *W, *T;  // r x r Gram matrix, r x r transform, r x n scratch rows

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(RT) multi_dot_part(const cd *__restrict__ V, l
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = wid; j < jn; j += RT / 32) {
     double sx = 0.0, sy = 0.0;
+#pragma unroll 4
     for (int b = lane; b < (int)gridDim.x; b += 32) {
       const double2 p = __ldcg(reinterpret_cast<const double2 *>(partial + (long long)b * nv + j0 + j));
       sx += p.x;
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(256) multi_axpy_kernel(const cd *__restrict__ 
       if (s_ticket == gridDim.x - 1 && threadIdx.x < 32) {
         __threadfence();
         double s = 0.0;
+#pragma unroll 4
         for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(partial + b);
         s = warp_sum(s);
         if (threadIdx.x == 0) {
@@ -243,22 +245,45 @@ __global__ void scale_inv_kernel(cd *x, long long n, const double *nrm, double *
   }
 }
 
-// ---- the full Gram-Schmidt pass of the mixed form on FP32 copies of the
-// Krylov vectors. The first pass (against v_{k-1} and v_k, FP64) has removed
-// the large components; what the full pass removes is of the size of the
-// FP32 error of the H_eff product (~1e-7 |w|), so its coefficients need only
-// a few correct digits: products and per-thread sums in FP32, the block and
-// final sums in FP64, and the correction sum_j c_j v_j (tiny) formed in FP32
-// and added to the FP64 vector. Half the bytes of the FP64 pass, no FP64
-// arithmetic beyond the sums and the norm.
-template <int JB>
-__device__ __forceinline__ void dot32_group(const cf *__restrict__ Vg, long long ldv, const cf *__restrict__ w,
-                                            long long i0, long long i1, double *sh, double *out2) {
+// ---- the Gram-Schmidt passes of the mixed form on FP32 copies of the
+// Krylov vectors. w = H v_k comes from the FP32 tensor-core product and is
+// itself only FP32-accurate, so its inner products need no more: products and
+// per-thread sums in FP32, the block and final sums in FP64, and the
+// correction sum_j c_j v_j formed in FP32 and added to the FP64 vector. Half
+// the bytes of the FP64 passes, no FP64 arithmetic beyond the sums and the
+// norm. w is read either as its FP32 copy or as the FP64 vector rounded on
+// load (as_cf), from global or shared memory (index i - woff).
+__device__ __forceinline__ cf as_cf(const cf &v) { return v; }
+__device__ __forceinline__ cf as_cf(const cd &v) { return mkc((float)v.x, (float)v.y); }
+
+template <int JB, typename WT>
+__device__ __forceinline__ void dot32_group(const cf *__restrict__ Vg, long long ldv, const WT *__restrict__ w,
+                                            long long woff, long long i0, long long i1, double *sh,
+                                            double *out2) {
   float sx[JB], sy[JB];
 #pragma unroll
   for (int j = 0; j < JB; ++j) sx[j] = sy[j] = 0.f;
-  for (long long i = i0 + threadIdx.x; i < i1; i += RT) {
-    const cf b = w[i];
+  // two elements per iteration with all their loads issued before the
+  // products (more bytes in flight); the accumulation order is unchanged
+  long long i = i0 + threadIdx.x;
+  for (; i + RT < i1; i += 2 * RT) {
+    const cf b0 = as_cf(w[i - woff]), b1 = as_cf(w[i + RT - woff]);
+    cf a0[JB], a1[JB];
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+      a0[j] = Vg[j * ldv + i];
+      a1[j] = Vg[j * ldv + i + RT];
+    }
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+      sx[j] = fmaf(a0[j].x, b0.x, fmaf(a0[j].y, b0.y, sx[j]));
+      sy[j] = fmaf(a0[j].x, b0.y, fmaf(-a0[j].y, b0.x, sy[j]));
+      sx[j] = fmaf(a1[j].x, b1.x, fmaf(a1[j].y, b1.y, sx[j]));
+      sy[j] = fmaf(a1[j].x, b1.y, fmaf(-a1[j].y, b1.x, sy[j]));
+    }
+  }
+  if (i < i1) {
+    const cf b = as_cf(w[i - woff]);
 #pragma unroll
     for (int j = 0; j < JB; ++j) {
       const cf a = Vg[j * ldv + i];
@@ -283,8 +308,24 @@ __device__ __forceinline__ void dot32_group(const cf *__restrict__ Vg, long long
   }
 }
 
+template <typename WT>
+__device__ __forceinline__ void dot32_any(int jn, const cf *Vg, long long ldv, const WT *w, long long woff,
+                                          long long i0, long long i1, double *sh, double *out2) {
+  switch (jn) {
+    case 8: dot32_group<8>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    case 7: dot32_group<7>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    case 6: dot32_group<6>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    case 5: dot32_group<5>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    case 4: dot32_group<4>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    case 3: dot32_group<3>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    case 2: dot32_group<2>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+    default: dot32_group<1>(Vg, ldv, w, woff, i0, i1, sh, out2); break;
+  }
+}
+
+template <typename WT>
 __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V, long long ldv, int nv,
-                                                       const cf *__restrict__ w, long long n,
+                                                       const WT *__restrict__ w, long long n,
                                                        cd *__restrict__ partial, unsigned int *cnt, cd *out) {
   __shared__ double sh[(RT / 32) * 2 * DOT_JB];
   __shared__ unsigned int s_ticket;
@@ -294,16 +335,7 @@ __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V,
   const long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
   const cf *Vg = V + j0 * ldv;
   double *out2 = reinterpret_cast<double *>(partial + (long long)blockIdx.x * nv + j0);
-  switch (jn) {
-    case 8: dot32_group<8>(Vg, ldv, w, i0, i1, sh, out2); break;
-    case 7: dot32_group<7>(Vg, ldv, w, i0, i1, sh, out2); break;
-    case 6: dot32_group<6>(Vg, ldv, w, i0, i1, sh, out2); break;
-    case 5: dot32_group<5>(Vg, ldv, w, i0, i1, sh, out2); break;
-    case 4: dot32_group<4>(Vg, ldv, w, i0, i1, sh, out2); break;
-    case 3: dot32_group<3>(Vg, ldv, w, i0, i1, sh, out2); break;
-    case 2: dot32_group<2>(Vg, ldv, w, i0, i1, sh, out2); break;
-    default: dot32_group<1>(Vg, ldv, w, i0, i1, sh, out2); break;
-  }
+  dot32_any(jn, Vg, ldv, w, 0, i0, i1, sh, out2);
   // the last block of the group sums the partials in block order
   __threadfence();
   __syncthreads();
@@ -314,6 +346,7 @@ __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V,
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = wid; j < jn; j += RT / 32) {
     double sx = 0.0, sy = 0.0;
+#pragma unroll 4
     for (int b = lane; b < (int)gridDim.x; b += 32) {
       const double2 p = __ldcg(reinterpret_cast<const double2 *>(partial + (long long)b * nv + j0 + j));
       sx += p.x;
@@ -324,6 +357,80 @@ __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V,
     if (lane == 0) out[j0 + j] = mkc(sx, sy);
   }
   if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
+}
+
+// The first pass's update fused with the full pass's inner products (one
+// read of the data instead of two): each block takes one chunk of w,
+// w <- w + sign * sum_{j<n1} c1_j V1_j (FP32 correction, FP64 w, as in
+// multi_axpy32_norm_kernel), keeps the FP32 copy of the new w in shared
+// memory, then forms partial[b * nv + j] = <V_j, w32> over its chunk for all
+// nv vectors in groups of DOT_JB (as multi_dot32_part); the last block sums
+// the partials in block order. Dynamic shared memory: chunk FP32 elements.
+__global__ void __launch_bounds__(RT, 4) axpy_dot32_kernel(const cf *__restrict__ V1, int n1,
+                                                        const cd *__restrict__ c1, double sign,
+                                                        cd *__restrict__ w, long long n, const cf *__restrict__ V,
+                                                        long long ldv, int nv, cd *__restrict__ partial,
+                                                        unsigned int *cnt, cd *out) {
+  extern __shared__ __align__(16) unsigned char adsm[];
+  cf *ws = reinterpret_cast<cf *>(adsm);
+  __shared__ double sh[(RT / 32) * 2 * DOT_JB];
+  __shared__ cf cs[2];
+  __shared__ unsigned int s_ticket;
+  if (threadIdx.x < n1)
+    cs[threadIdx.x] = mkc((float)(sign * c1[threadIdx.x].x), (float)(sign * c1[threadIdx.x].y));
+  __syncthreads();
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  for (long long i = i0 + threadIdx.x; i < i1; i += 2 * RT) {
+    const long long i2 = i + RT;
+    const bool two = i2 < i1;
+    const cd o = w[i];
+    const cd o2 = two ? w[i2] : mkc(0.0, 0.0);
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+    for (int j = 0; j < n1; ++j) {
+      const cf cj = cs[j];
+      const cf v = V1[j * ldv + i];
+      const cf u = two ? V1[j * ldv + i2] : mkc(0.f, 0.f);
+      ax = fmaf(cj.x, v.x, fmaf(-cj.y, v.y, ax));
+      ay = fmaf(cj.x, v.y, fmaf(cj.y, v.x, ay));
+      bx = fmaf(cj.x, u.x, fmaf(-cj.y, u.y, bx));
+      by = fmaf(cj.x, u.y, fmaf(cj.y, u.x, by));
+    }
+    const cd r = mkc(o.x + (double)ax, o.y + (double)ay);
+    w[i] = r;
+    ws[i - i0] = mkc((float)r.x, (float)r.y);
+    if (two) {
+      const cd r2 = mkc(o2.x + (double)bx, o2.y + (double)by);
+      w[i2] = r2;
+      ws[i2 - i0] = mkc((float)r2.x, (float)r2.y);
+    }
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < nv; j0 += DOT_JB) {
+    double *out2 = reinterpret_cast<double *>(partial + (long long)blockIdx.x * nv + j0);
+    dot32_any(min(DOT_JB, nv - j0), V + j0 * ldv, ldv, ws, i0, i0, i1, sh, out2);
+    __syncthreads();  // sh is reused by the next group
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(cnt, 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = wid; j < nv; j += RT / 32) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double2 p = __ldcg(reinterpret_cast<const double2 *>(partial + (long long)b * nv + j));
+      sx += p.x;
+      sy += p.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) out[j] = mkc(sx, sy);
+  }
+  if (threadIdx.x == 0) cnt[0] = 0u;
 }
 
 // w[i] += sign * sum_j c[j] V32_j[i] (correction in FP32, w in FP64); with
@@ -385,6 +492,7 @@ __global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__rest
   if (s_ticket == gridDim.x - 1 && threadIdx.x < 32) {
     __threadfence();
     double t = 0.0;
+#pragma unroll 4
     for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(partial + b);
     t = warp_sum(t);
     if (threadIdx.x == 0) {
@@ -684,12 +792,57 @@ vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double
   return VB_OK;
 }
 
+template <typename WT>
+static vb_status multi_dot32_launch(const cf *V, long long ldv, int nv, const WT *w, long long n, cd *out,
+                                    cd *partial, int n_part, cudaStream_t st, unsigned int *cnt) {
+  if (nv <= 0) return VB_OK;
+  if (nv > 128 || n_part < 1 || (long long)n_part * nv > 512LL * 128 || !cnt)
+    return fail(VB_EINVAL, "multi_dot32: too many vectors or no counters");
+  multi_dot32_part<WT><<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial, cnt,
+                                                                                out);
+  VB_CHECK_LAUNCH();
+  return VB_OK;
+}
+
 vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cf *w, long long n, cd *out, cd *partial,
                           int n_part, cudaStream_t st, unsigned int *cnt) {
-  if (nv <= 0) return VB_OK;
-  if (nv > 128 || (long long)n_part * nv > 512LL * 128 || !cnt)
-    return fail(VB_EINVAL, "multi_dot32: too many vectors or no counters");
-  multi_dot32_part<<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial, cnt, out);
+  return multi_dot32_launch(V, ldv, nv, w, n, out, partial, n_part, st, cnt);
+}
+
+vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cd *w, long long n, cd *out, cd *partial,
+                          int n_part, cudaStream_t st, unsigned int *cnt) {
+  return multi_dot32_launch(V, ldv, nv, w, n, out, partial, n_part, st, cnt);
+}
+
+int axpy_dot32_blocks(long long n, int nv, long long partial_elems) {
+  if (n <= 0 || nv <= 0 || nv > 128) return 0;
+  // AXPY_DOT_CHUNK elements per block on large vectors; on smaller ones at
+  // least four blocks per SM while a block still gets 1024 elements
+  const long long nb = std::min<long long>(
+      AXPY_DOT_MAX_BLOCKS, std::max<long long>((n + AXPY_DOT_CHUNK - 1) / AXPY_DOT_CHUNK,
+                                               std::min<long long>((n + 1023) / 1024, 4 * 152)));
+  if ((n + nb - 1) / nb > AXPY_DOT_MAX_CHUNK || nb * nv > partial_elems) return 0;
+  return (int)nb;
+}
+
+vb_status vec_axpy_dot32(const cf *V1, int n1, const cd *c1, double sign, cd *w, long long n, const cf *V,
+                         long long ldv, int nv, cd *out, cd *partial, long long partial_elems, cudaStream_t st,
+                         unsigned int *cnt) {
+  const int nb = axpy_dot32_blocks(n, nv, partial_elems);
+  if (!nb || n1 < 1 || n1 > 2 || !cnt) return fail(VB_EINVAL, "axpy_dot32: sizes out of range");
+  // the attribute is per device; setting it twice from two threads is harmless
+  static std::atomic<bool> attr_set[64];
+  int dev = 0;
+  VB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "axpy_dot32: device ordinal out of range");
+  if (!attr_set[dev].load()) {
+    VB_TRY_CUDA(cudaFuncSetAttribute(axpy_dot32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(AXPY_DOT_MAX_CHUNK * sizeof(cf))));
+    attr_set[dev].store(true);
+  }
+  const long long chunk = (n + nb - 1) / nb;
+  axpy_dot32_kernel<<<nb, RT, (size_t)chunk * sizeof(cf), st>>>(V1, n1, c1, sign, w, n, V, ldv, nv, partial, cnt,
+                                                                out);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

@@ -542,17 +542,24 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       const int j0 = k > 0 ? k - 1 : 0;
       const int n1 = k + 1 - j0;
       // bandwidth-bound: more, smaller partial blocks than the FP64 dots use
-      const int np32 = (int)std::min<long long>(512, std::max<long long>(1, (N + 1023) / 1024));
-      VB_TRY(vec_to_c32(w, s->w32, N, st));
-      VB_TRY(vec_multi_dot32(V32 + j0 * ldv, ldv, n1, s->w32, N, s->d_c + j0, s->d_partc, np32, st, s->d_cnt));
-      VB_TRY(vec_multi_axpy32(V32 + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, s->w32, st));
-      VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np32, st, s->d_cnt));
+      const int np32 = (int)std::min<long long>(608, std::max<long long>(1, (N + 1023) / 1024));
+      // first pass: inner products with w rounded to FP32 on load
+      VB_TRY(vec_multi_dot32(V32 + j0 * ldv, ldv, n1, w, N, s->d_c + j0, s->d_partc, np32, st, s->d_cnt));
+      if (axpy_dot32_blocks(N, k + 1, PARTC_ELEMS)) {
+        // its update fused with the full pass's inner products
+        VB_TRY(vec_axpy_dot32(V32 + j0 * ldv, n1, s->d_c + j0, -1.0, w, N, V32, ldv, k + 1, s->d_c2, s->d_partc,
+                              PARTC_ELEMS, st, s->d_cnt));
+      } else {
+        VB_TRY(vec_multi_axpy32(V32 + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, s->w32, st));
+        VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np32, st, s->d_cnt));
+      }
       VB_TRY(vec_multi_axpy32_norm(V32, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st,
                                    s->d_cnt + 32));
-      // algorithmic bytes: the FP32 copy of w (read 16, write 8), first pass
-      // (copies of v_{k-1}, v_k read twice, w32 read, w read and written, w32
-      // written), full pass (copies read twice, w32 once, w read and written)
-      kbytes = (double)N * (24.0 + 8.0 * (2 * n1 + 1) + 40.0 + 8.0 * (2 * (k + 1) + 1) + 32.0);
+      // algorithmic bytes: first-pass inner products (w read, copies of
+      // v_{k-1}, v_k read), fused update + inner products (w read and
+      // written, the two copies and all k+1 copies read), full-pass update
+      // (copies read, w read and written)
+      kbytes = (double)N * (16.0 + 8.0 * n1 + 32.0 + 8.0 * n1 + 8.0 * (k + 1) + 8.0 * (k + 1) + 32.0);
     } else {
       VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st, s->d_cnt));
       VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
@@ -1112,7 +1119,7 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
     A2((void **)&s->d_c, 128 * sizeof(cd));
     A2((void **)&s->d_c2, 128 * sizeof(cd));
     A2((void **)&s->d_u, 128 * sizeof(cd));
-    A2((void **)&s->d_partc, (size_t)512 * 128 * sizeof(cd));
+    A2((void **)&s->d_partc, (size_t)PARTC_ELEMS * sizeof(cd));
     A2((void **)&s->d_tcerr, 256);
     A2((void **)&s->d_cnt, 64 * sizeof(unsigned int));
     if (e != VB_OK) return fail_free(e);
