@@ -493,6 +493,8 @@ def run_ours(args):
                                                                 ("heff2", "heff1", "krylov", "split", "env", "merge"))), 4)
                         for k in ("heff2", "heff1", "krylov", "split", "env", "merge")},
         "heff_tflops": achieved,
+        "ritz_jacobi_sweeps_per_call": (prof["ritz_jacobi"]["flops"] / prof["ritz_jacobi"]["calls"]
+                                        if prof.get("ritz_jacobi", {}).get("calls") else None),
         "krylov_iters_max": max(s.krylov_iters_max for s in stats),
         "krylov_iters_per_step": sum(s.krylov_iters_total for s in stats) / len(stats),
         "heff_flops_per_step": heff_flops / args.steps,

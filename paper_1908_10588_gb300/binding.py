@@ -68,7 +68,8 @@ class vb_profile(C.Structure):
 PHASES = ["heff2", "heff1", "krylov", "split", "env", "merge", "split_rho", "split_eigval", "split_eigvec",
           "split_out", "split_subspace_products", "split_subspace_orth", "eigvec_invit", "eigvec_gram_schmidt",
           "eigvec_backtransform", "split_rayleigh_ritz", "split_ritz_fp32", "split_ritz_fp64",
-          "split_orth_cholesky", "split_orth_products", "heff_tc_legs", "heff_sparse_legs", "heff_prep"]
+          "split_orth_cholesky", "split_orth_products", "heff_tc_legs", "heff_sparse_legs", "heff_prep",
+          "ritz_jacobi"]  # ritz_jacobi: its "flops" entry counts Jacobi sweeps
 
 
 class vb_order_opts(C.Structure):

@@ -43,12 +43,14 @@ void count_launch();
 enum { PH_HEFF2 = 0, PH_HEFF1 = 1, PH_KRYLOV = 2, PH_SPLIT = 3, PH_ENV = 4, PH_MERGE = 5, PH_RHO = 6, PH_EIGVAL = 7,
        PH_EIGVEC = 8, PH_SPLITOUT = 9, PH_SUBPROD = 10, PH_SUBORTH = 11, PH_INVIT = 12,
        PH_CGS = 13, PH_BACKT = 14, PH_RR = 15, PH_RR32 = 16, PH_RR64 = 17, PH_CHOL = 18,
-       PH_ORTHGEMM = 19, PH_TC = 20, PH_WLEG = 21, PH_PREP = 22, PH_COUNT = 24 };
+       PH_ORTHGEMM = 19, PH_TC = 20, PH_WLEG = 21, PH_PREP = 22, PH_JACOBI = 23, PH_COUNT = 24 };
 bool prof_on();
 void prof_begin(int phase, cudaStream_t st);
 // flops / bytes: algorithmic work of the call, summed per phase
 void prof_end(int phase, cudaStream_t st, double flops, double bytes = 0.0);
 void prof_collect();  // after a stream synchronisation: fold finished events into the totals
+// add a count to a phase's flops slot (PH_JACOBI: Jacobi sweeps, not flops)
+void prof_note(int phase, double v);
 
 inline vb_status fail(vb_status s, const std::string &msg) {
   set_error(msg);

@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_rows_kernel(const cplx<R> *
 // barriers. A rotation U = diag(1, e^{-i phi}) R(theta) zeroes |A_pq| (phase
 // phi of A_pq; theta from the real Jacobi rule tan 2 theta = 2|A_pq|/(A_pp - A_qq),
 // smaller root). Sweeps stop when no off-diagonal element exceeds
-// 1e-7 sqrt(A_pp A_qq) + 1e-12 tr A. Writes the k largest eigenvalues
+// 1e-7 max(sqrt(A_pp A_qq), |A_pp - A_qq|) + 1e-12 tr A (nor after 20
+// sweeps; the sweep count goes to info[0]). Writes the k largest eigenvalues
 // (descending) and their eigenvectors as rows W[t][0..n).
 constexpr int JAC_THREADS = 1024;
 constexpr int JAC_MAX_N = 112;
@@ -202,7 +203,12 @@ __global__ void __launch_bounds__(JAC_THREADS) ritz_jacobi_kernel(const cf *__re
           const float a = A[p * np + p].x, b = A[q * np + q].x;
           const cf c = A[p * np + q];
           const float ac = sqrtf(c.x * c.x + c.y * c.y);
-          if (ac > 1e-7f * sqrtf(fabsf(a * b)) + floor_abs) {
+          // rotate while the coupling is above FP32 resolution both relative
+          // to the pair's scale and as a rotation angle (|c| / |a - b|): on
+          // a graded matrix the rounding noise of the large entries (~eps
+          // max(a, b)) stays above 1e-7 sqrt(ab) and would keep every sweep
+          // busy with rotations by angles below FP32 precision
+          if (ac > 1e-7f * fmaxf(sqrtf(fabsf(a * b)), fabsf(b - a)) + floor_abs) {
             const float tau = (b - a) / (2.f * ac);
             const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c_ = 1.f / sqrtf(1.f + tt * tt);

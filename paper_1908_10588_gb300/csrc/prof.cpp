@@ -74,6 +74,10 @@ void prof_end(int phase, cudaStream_t st, double flops, double bytes) {
   g_prof.open_start[phase] = nullptr;
 }
 
+void prof_note(int phase, double v) {
+  if (g_prof.every && phase >= 0 && phase < PH_COUNT) g_prof.pflops[phase] += v;
+}
+
 void prof_collect() {
   if (g_prof.pending.empty()) return;
   std::vector<Pending> keep;

@@ -561,9 +561,11 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       // (copies read, w read and written)
       kbytes = (double)N * (16.0 + 8.0 * n1 + 32.0 + 8.0 * n1 + 8.0 * (k + 1) + 8.0 * (k + 1) + 32.0);
     } else {
-      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np, st, s->d_cnt));
+      // FP64-pipe-bound: one partial block per 512 elements up to four per SM
+      const int np64 = (int)std::min<long long>(608, std::max<long long>(1, (N + 511) / 512));
+      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c, s->d_partc, np64, st, s->d_cnt));
       VB_TRY(vec_multi_axpy(V, ldv, k + 1, s->d_c, -1.0, w, N, st));
-      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np, st, s->d_cnt));
+      VB_TRY(vec_multi_dot(V, ldv, k + 1, w, N, s->d_c2, s->d_partc, np64, st, s->d_cnt));
       VB_TRY(vec_multi_axpy_norm(V, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st, s->d_cnt + 32));
     }
 
@@ -904,8 +906,11 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
     h.ws = s->skws32; h.ws_elems = s->skws32_elems;
     VB_TRY(gemm<float>(h, st));
   }
-  if (r <= 112) {
+  const bool jacobi = r <= 112;
+  if (jacobi) {
+    prof_begin(PH_JACOBI, st);
     VB_TRY(ritz_eig_small(s->subG, r, kws, s->ev32, s->subW, s->subflag, st));
+    prof_end(PH_JACOBI, st, 0.0);
   } else {
     VB_TRY(eig_values<float>(r, s->subG, kws, s->ev32, s->eigw32, st));
     VB_TRY(eig_vectors<float>(r, s->subG, kws, kws, s->ev32, s->subW, s->eigw32, st));
@@ -943,7 +948,11 @@ vb_status split_mixed(vb_mps *s, bool left, int mL, int d1, int d2, int mR, int 
   double nrm = 0.0;
   VB_TRY_CUDA(cudaMemcpyAsync(w.data(), s->d_evals, kws * sizeof(double), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaMemcpyAsync(&nrm, s->d_trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  int jac_sweeps = 0;  // sweeps of the Jacobi eigensolver, for the profiler
+  if (jacobi && prof_on())
+    VB_TRY_CUDA(cudaMemcpyAsync(&jac_sweeps, s->subflag, sizeof(int), cudaMemcpyDeviceToHost, st));
   VB_TRY_CUDA(cudaStreamSynchronize(st));
+  if (jacobi) prof_note(PH_JACOBI, (double)jac_sweeps);
   if (r > 112) VB_TRY(EigWork::check(r, kws, 4, s->eigw32, st));
   prof_end(PH_EIGVAL, st, 0.0);
   for (double v : w)
