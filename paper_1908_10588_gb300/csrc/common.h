@@ -255,25 +255,38 @@ vb_status vec_multi_dot(const cd *V, long long ldv, int nv, const cd *w, long lo
 // w32 (nullable): also write the FP32 copy of the result
 vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w,
                          long long n, cudaStream_t st, cf *w32 = nullptr);
-// the full Gram-Schmidt pass of the mixed form on FP32 copies of the Krylov
-// vectors (FP32 products, FP64 sums; cnt: zeroed group counters as for
-// vec_multi_dot, required) and its update of the FP64 w followed by |w|
+// Gram-Schmidt of the mixed form on FP32 copies of the Krylov vectors (FP32
+// products, FP64 sums; cnt: zeroed counters, required). vs (nullable): the
+// copies are stored unnormalised and vs[j] is the factor that normalises
+// copy j; the inner products returned are those with the normalised vectors
+// and the coefficients given are applied to them.
+struct LanczosRecord {  // written by the last block of the full-pass update (all nullable)
+  double *vs_next;      // 1/|w| (0 for w = 0): factor of the new vector's stored copies
+  double *beta_k;       // |w|
+  double *alpha_k;      // Re(ck + c2k)
+  const cd *ck, *c2k;
+};
 vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cf *w, long long n, cd *out, cd *partial,
-                          int n_part, cudaStream_t st, unsigned int *cnt);
+                          int n_part, cudaStream_t st, unsigned int *cnt, const double *vs = nullptr);
+// the update of the FP64 w followed by |w| (into out); w32 (nullable) gets
+// the FP32 copy of the new w
 vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
-                                double *out, double *partial, cudaStream_t st, unsigned int *cnt);
+                                double *out, double *partial, cudaStream_t st, unsigned int *cnt,
+                                const double *vs = nullptr, cf *w32 = nullptr,
+                                const LanczosRecord &rec = LanczosRecord{});
 // the same update without the norm, writing the FP32 copy of the new w into w32
 vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
-                           cf *w32, cudaStream_t st);
+                           cf *w32, cudaStream_t st, const double *vs = nullptr);
 // y = FP32 copy of x
 vb_status vec_to_c32(const cd *x, cf *y, long long n, cudaStream_t st);
 // inner products of FP32 copies with the FP64 w rounded to FP32 on load
 vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cd *w, long long n, cd *out, cd *partial,
-                          int n_part, cudaStream_t st, unsigned int *cnt);
-// w += sign * sum_{j<n1} c1_j V1_j (n1 <= 2, FP32 correction) fused with
-// out_j = <V_j, w32> for j < nv on the updated w; partial holds partial_elems
-// complex entries, cnt one zeroed counter. axpy_dot32_blocks gives the block
-// count it would use, 0 where the sizes do not fit (then use the two passes).
+                          int n_part, cudaStream_t st, unsigned int *cnt, const double *vs = nullptr);
+// w += sign * sum_{j<n1} c1_j V1_j (n1 <= 2, FP32 correction; vs1: factors of
+// the V1 copies) fused with out_j = <V_j, w32> for j < nv on the updated w
+// (vs: factors of the V copies); partial holds partial_elems complex entries,
+// cnt one zeroed counter. axpy_dot32_blocks gives the block count it would
+// use, 0 where the sizes do not fit (then use the two passes).
 constexpr long long AXPY_DOT_CHUNK = 4096;       // elements per block aimed at
 constexpr long long AXPY_DOT_MAX_CHUNK = 12288;  // shared-memory bound (96 KB)
 constexpr long long AXPY_DOT_MAX_BLOCKS = 2048;
@@ -281,7 +294,7 @@ constexpr long long PARTC_ELEMS = 2048LL * 64;   // complex partial sums per han
 int axpy_dot32_blocks(long long n, int nv, long long partial_elems);
 vb_status vec_axpy_dot32(const cf *V1, int n1, const cd *c1, double sign, cd *w, long long n, const cf *V,
                          long long ldv, int nv, cd *out, cd *partial, long long partial_elems, cudaStream_t st,
-                         unsigned int *cnt);
+                         unsigned int *cnt, const double *vs1 = nullptr, const double *vs = nullptr);
 // ------------------------------------------------------------ subspace iteration
 struct SubspaceWork {
   cf *G, *W, *T;  // r x r Gram matrix, r x r transform, r x n scratch rows
@@ -327,9 +340,9 @@ vb_status vec_scale_inv(cd *x, long long n, const double *nrm, cudaStream_t st, 
                         cf *shadow = nullptr);
 // y = s * x with s = *num / *den (device scalars; den may be null -> 1)
 vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st);
-// combine: y = (*nrm) * sum_j u[j] V[j]
+// combine: y = (*nrm) * sum_j u[j] vs[j] V[j] (vs nullable: 1)
 vb_status vec_combine(const cd *V, long long ldv, int nv, const cd *u, const double *nrm, cd *y,
-                      long long n, cudaStream_t st);
+                      long long n, cudaStream_t st, const double *vs = nullptr);
 int reduce_parts(long long n);
 
 // ------------------------------------------------------------ eigen

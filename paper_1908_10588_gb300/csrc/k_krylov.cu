@@ -326,7 +326,8 @@ __device__ __forceinline__ void dot32_any(int jn, const cf *Vg, long long ldv, c
 template <typename WT>
 __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V, long long ldv, int nv,
                                                        const WT *__restrict__ w, long long n,
-                                                       cd *__restrict__ partial, unsigned int *cnt, cd *out) {
+                                                       cd *__restrict__ partial, unsigned int *cnt, cd *out,
+                                                       const double *__restrict__ vs) {
   __shared__ double sh[(RT / 32) * 2 * DOT_JB];
   __shared__ unsigned int s_ticket;
   const int j0 = blockIdx.y * DOT_JB;
@@ -354,7 +355,10 @@ __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V,
     }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
-    if (lane == 0) out[j0 + j] = mkc(sx, sy);
+    if (lane == 0) {
+      const double f = vs ? vs[j0 + j] : 1.0;
+      out[j0 + j] = mkc(sx * f, sy * f);
+    }
   }
   if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
@@ -370,14 +374,17 @@ __global__ void __launch_bounds__(RT, 4) axpy_dot32_kernel(const cf *__restrict_
                                                         const cd *__restrict__ c1, double sign,
                                                         cd *__restrict__ w, long long n, const cf *__restrict__ V,
                                                         long long ldv, int nv, cd *__restrict__ partial,
-                                                        unsigned int *cnt, cd *out) {
+                                                        unsigned int *cnt, cd *out, const double *__restrict__ vs1,
+                                                        const double *__restrict__ vs) {
   extern __shared__ __align__(16) unsigned char adsm[];
   cf *ws = reinterpret_cast<cf *>(adsm);
   __shared__ double sh[(RT / 32) * 2 * DOT_JB];
   __shared__ cf cs[2];
   __shared__ unsigned int s_ticket;
-  if (threadIdx.x < n1)
-    cs[threadIdx.x] = mkc((float)(sign * c1[threadIdx.x].x), (float)(sign * c1[threadIdx.x].y));
+  if (threadIdx.x < n1) {
+    const double f = sign * (vs1 ? vs1[threadIdx.x] : 1.0);
+    cs[threadIdx.x] = mkc((float)(f * c1[threadIdx.x].x), (float)(f * c1[threadIdx.x].y));
+  }
   __syncthreads();
   const long long chunk = (n + gridDim.x - 1) / gridDim.x;
   const long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -428,7 +435,10 @@ __global__ void __launch_bounds__(RT, 4) axpy_dot32_kernel(const cf *__restrict_
     }
     sx = warp_sum(sx);
     sy = warp_sum(sy);
-    if (lane == 0) out[j] = mkc(sx, sy);
+    if (lane == 0) {
+      const double f = vs ? vs[j] : 1.0;
+      out[j] = mkc(sx * f, sy * f);
+    }
   }
   if (threadIdx.x == 0) cnt[0] = 0u;
 }
@@ -440,11 +450,15 @@ __global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__rest
                                                                 const cd *__restrict__ c, double sign,
                                                                 cd *__restrict__ w, long long n,
                                                                 double *__restrict__ partial, unsigned int *cnt,
-                                                                double *nrm_out, cf *__restrict__ w32) {
+                                                                double *nrm_out, cf *__restrict__ w32,
+                                                                const double *__restrict__ vs, LanczosRecord rec) {
   __shared__ cf cs[128];
   __shared__ double sh[8];
   __shared__ unsigned int s_ticket;
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = mkc((float)(sign * c[j].x), (float)(sign * c[j].y));
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const double f = sign * (vs ? vs[j] : 1.0);
+    cs[j] = mkc((float)(f * c[j].x), (float)(f * c[j].y));
+  }
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   double nn = 0.0;
@@ -496,7 +510,11 @@ __global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__rest
     for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(partial + b);
     t = warp_sum(t);
     if (threadIdx.x == 0) {
-      nrm_out[0] = sqrt(t);
+      const double nr = sqrt(t);
+      nrm_out[0] = nr;
+      if (rec.vs_next) rec.vs_next[0] = nr > 0.0 ? 1.0 / nr : 0.0;
+      if (rec.beta_k) rec.beta_k[0] = nr;
+      if (rec.alpha_k) rec.alpha_k[0] = rec.ck[0].x + rec.c2k[0].x;
       cnt[0] = 0u;
     }
   }
@@ -510,10 +528,10 @@ __global__ void copy_kernel(const cd *x, cd *y, long long n) {
 
 __global__ void combine_kernel(const cd *__restrict__ V, long long ldv, int nv,
                                const cd *__restrict__ u, const double *nrm, cd *__restrict__ y,
-                               long long n) {
+                               long long n, const double *__restrict__ vs) {
   __shared__ cd cs[128];
   double s = nrm[0];
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = cscale(u[j], s);
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) cs[j] = cscale(u[j], vs ? s * vs[j] : s);
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -794,24 +812,25 @@ vb_status vec_multi_axpy(const cd *V, long long ldv, int nv, const cd *c, double
 
 template <typename WT>
 static vb_status multi_dot32_launch(const cf *V, long long ldv, int nv, const WT *w, long long n, cd *out,
-                                    cd *partial, int n_part, cudaStream_t st, unsigned int *cnt) {
+                                    cd *partial, int n_part, cudaStream_t st, unsigned int *cnt,
+                                    const double *vs) {
   if (nv <= 0) return VB_OK;
   if (nv > 128 || n_part < 1 || (long long)n_part * nv > 512LL * 128 || !cnt)
     return fail(VB_EINVAL, "multi_dot32: too many vectors or no counters");
   multi_dot32_part<WT><<<dim3(n_part, (nv + DOT_JB - 1) / DOT_JB), RT, 0, st>>>(V, ldv, nv, w, n, partial, cnt,
-                                                                                out);
+                                                                                out, vs);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
 
 vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cf *w, long long n, cd *out, cd *partial,
-                          int n_part, cudaStream_t st, unsigned int *cnt) {
-  return multi_dot32_launch(V, ldv, nv, w, n, out, partial, n_part, st, cnt);
+                          int n_part, cudaStream_t st, unsigned int *cnt, const double *vs) {
+  return multi_dot32_launch(V, ldv, nv, w, n, out, partial, n_part, st, cnt, vs);
 }
 
 vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cd *w, long long n, cd *out, cd *partial,
-                          int n_part, cudaStream_t st, unsigned int *cnt) {
-  return multi_dot32_launch(V, ldv, nv, w, n, out, partial, n_part, st, cnt);
+                          int n_part, cudaStream_t st, unsigned int *cnt, const double *vs) {
+  return multi_dot32_launch(V, ldv, nv, w, n, out, partial, n_part, st, cnt, vs);
 }
 
 int axpy_dot32_blocks(long long n, int nv, long long partial_elems) {
@@ -827,7 +846,7 @@ int axpy_dot32_blocks(long long n, int nv, long long partial_elems) {
 
 vb_status vec_axpy_dot32(const cf *V1, int n1, const cd *c1, double sign, cd *w, long long n, const cf *V,
                          long long ldv, int nv, cd *out, cd *partial, long long partial_elems, cudaStream_t st,
-                         unsigned int *cnt) {
+                         unsigned int *cnt, const double *vs1, const double *vs) {
   const int nb = axpy_dot32_blocks(n, nv, partial_elems);
   if (!nb || n1 < 1 || n1 > 2 || !cnt) return fail(VB_EINVAL, "axpy_dot32: sizes out of range");
   // the attribute is per device; setting it twice from two threads is harmless
@@ -842,27 +861,29 @@ vb_status vec_axpy_dot32(const cf *V1, int n1, const cd *c1, double sign, cd *w,
   }
   const long long chunk = (n + nb - 1) / nb;
   axpy_dot32_kernel<<<nb, RT, (size_t)chunk * sizeof(cf), st>>>(V1, n1, c1, sign, w, n, V, ldv, nv, partial, cnt,
-                                                                out);
+                                                                out, vs1, vs);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
 
 vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
-                                double *out, double *partial, cudaStream_t st, unsigned int *cnt) {
-  if (nv > 128 || !cnt) return fail(VB_EINVAL, "multi_axpy32: more than 128 vectors or no counter");
-  if (nv <= 0 || n == 0) return vec_norm2(w, n, out, partial, reduce_parts(n), st);
+                                double *out, double *partial, cudaStream_t st, unsigned int *cnt,
+                                const double *vs, cf *w32, const LanczosRecord &rec) {
+  if (nv > 128 || nv <= 0 || n <= 0 || !cnt)
+    return fail(VB_EINVAL, "multi_axpy32: 1..128 vectors, a nonempty w and a counter needed");
   const int blocks = (int)std::min<long long>(512, std::max<long long>(1, (n + 511) / 512));
-  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out, nullptr);
+  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, partial, cnt, out, w32, vs, rec);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
 
 vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
-                           cf *w32, cudaStream_t st) {
+                           cf *w32, cudaStream_t st, const double *vs) {
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy32: more than 128 vectors");
   if (nv <= 0 || n == 0) return VB_OK;
   const int blocks = (int)std::min<long long>(152LL * 8, std::max<long long>(1, (n + 511) / 512));
-  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr, nullptr, nullptr, w32);
+  multi_axpy32_norm_kernel<<<blocks, 256, 0, st>>>(V, ldv, nv, c, sign, w, n, nullptr, nullptr, nullptr, w32, vs,
+                                                   LanczosRecord{});
   VB_CHECK_LAUNCH();
   return VB_OK;
 }
@@ -918,9 +939,9 @@ vb_status vec_copy_scaled(const cd *x, cd *y, long long n, cudaStream_t st) {
 }
 
 vb_status vec_combine(const cd *V, long long ldv, int nv, const cd *u, const double *nrm, cd *y,
-                      long long n, cudaStream_t st) {
+                      long long n, cudaStream_t st, const double *vs) {
   if (nv > 128) return fail(VB_EINVAL, "combine: more than 128 vectors");
-  combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, ldv, nv, u, nrm, y, n);
+  combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(V, ldv, nv, u, nrm, y, n, vs);
   VB_CHECK_LAUNCH();
   return VB_OK;
 }

@@ -99,20 +99,22 @@ __global__ void prep_right_env(const cd *__restrict__ R, int N, long long K, lon
 }
 
 // BX[n][k] = [Re x[k][n] (k < K), Im x[k-K][n] (K <= k < 2K), 0...]: a tiled
-// transpose of x (K x Ncols complex double) into K-major fp32 rows
+// transpose of x (K x Ncols complex double) into K-major fp32 rows; x is
+// multiplied by *xs on load where xs is given (a vector stored unnormalised)
 __global__ void prep_vector_T(const cd *__restrict__ x, int K, long long Ncols, long long ld, float *__restrict__ BX,
-                              float *__restrict__ BXlo) {
+                              float *__restrict__ BXlo, const double *__restrict__ xs) {
   __shared__ float tr[32][33], ti[32][33];
   const long long n0 = (long long)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const double f = xs ? xs[0] : 1.0;
   for (int r = ty; r < 32; r += 8) {
     const int k = k0 + r;
     const long long n = n0 + tx;
     cd z = mkc(0.0, 0.0);
     if (k < K && n < Ncols) z = x[(long long)k * Ncols + n];
-    tr[r][tx] = (float)z.x;
-    ti[r][tx] = (float)z.y;
+    tr[r][tx] = (float)(z.x * f);
+    ti[r][tx] = (float)(z.y * f);
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
@@ -381,7 +383,7 @@ int *heff_mixed_err_flag(const vb_mpo *mpo, int site, int two_site, int mL, int 
 
 vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
                            const cd *R, const cd *x, cd *y, void *work, size_t work_bytes, int *err,
-                           cudaStream_t st) {
+                           cudaStream_t st, const double *x_scale) {
   TcLayout lay(mpo, site, two_site, mL, mR);
   if (work_bytes < lay.total) return fail(VB_EINVAL, "heff_mixed_apply: workspace too small");
   char *w = static_cast<char *>(work);
@@ -402,7 +404,7 @@ vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, in
   VB_CHECK_LAUNCH();
   {
     dim3 g((unsigned)((lay.NL + 31) / 32), (unsigned)((lay.KL + 31) / 32));
-    prep_vector_T<<<g, 256, 0, st>>>(x, (int)lay.KL, lay.NL, lay.ldL, BX, BXlo);
+    prep_vector_T<<<g, 256, 0, st>>>(x, (int)lay.KL, lay.NL, lay.ldL, BX, BXlo, x_scale);
     VB_CHECK_LAUNCH();
     if (lay.ldL > 2 * lay.KL) {
       zero_cols<<<grid_for(lay.NL * (lay.ldL - 2 * lay.KL)), 256, 0, st>>>(BX, lay.NL, lay.ldL, 2 * lay.KL);

@@ -30,10 +30,11 @@ constexpr int MIXED_SPLIT_MIN_N = 192;
 constexpr int SUBSPACE_MAXIT = 30;
 constexpr double SUBSPACE_RTOL = 3e-7;
 
-// H_eff products in split-TF32 on the tensor cores (k_mixed.cu)
+// H_eff products in split-TF32 on the tensor cores (k_mixed.cu); x_scale
+// (nullable, device): x is multiplied by *x_scale on load
 vb_status heff_mixed_apply(const vb_mpo *mpo, int site, int two_site, int mL, int mR, const cd *L,
                            const cd *R, const cd *x, cd *y, void *work, size_t work_bytes, int *err,
-                           cudaStream_t st);
+                           cudaStream_t st, const double *x_scale);
 size_t heff_mixed_work_bytes(const vb_mpo *mpo, int site, int two_site, int mL, int mR);
 int *heff_mixed_err_flag(const vb_mpo *mpo, int site, int two_site, int mL, int mR, void *work);
 
@@ -246,6 +247,7 @@ struct vb_mps {
   long long theta_cap = 0, inter_cap = 0, nrho_cap = 0;
   int kw_cap = 0;
   // device scalars
+  double *d_vs = nullptr;  // mixed Lanczos: factors that normalise the stored basis vectors
   double *d_nrm = nullptr, *d_alpha = nullptr, *d_beta = nullptr, *d_bnext = nullptr,
          *d_evals = nullptr, *d_trace = nullptr, *d_part = nullptr, *d_pop = nullptr;
   cd *d_c = nullptr, *d_c2 = nullptr, *d_u = nullptr, *d_partc = nullptr;
@@ -481,16 +483,21 @@ vb_status take_wait_flag(vb_mps *s, const char *who) {
   return fail(VB_ETIMEOUT, std::string(who) + ": a tensor-core kernel's wait ran out (results invalid)");
 }
 
-vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y) {
+// x_scale (nullable, device; mixed two- and one-site products only): x is
+// stored unnormalised and multiplied by *x_scale on load
+vb_status apply_heff(vb_mps *s, const HeffOp &op, const cd *x, cd *y, const double *x_scale = nullptr) {
   if (op.two_site < 0)  // zero-site (bond) Hamiltonian: FP64 in both forms
-    return heff0_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->inter_cap, s->q_ws, s->q_ws_elems,
-                      s->st);
+    return x_scale ? fail(VB_EINVAL, "apply_heff: no input scale for the zero-site product")
+                   : heff0_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->inter_cap, s->q_ws,
+                                s->q_ws_elems, s->st);
   const int ph = op.two_site ? PH_HEFF2 : PH_HEFF1;
   prof_begin(ph, s->st);
   vb_status r;
   if (s->dtype == VB_MIXED)
     r = heff_mixed_apply(s->mpo, op.site, op.two_site, op.mL, op.mR, op.L, op.R, x, y, s->mixw,
-                         s->mixw_bytes, s->d_tcerr, s->st);
+                         s->mixw_bytes, s->d_tcerr, s->st, x_scale);
+  else if (x_scale)
+    r = fail(VB_EINVAL, "apply_heff: input scale only in the mixed form");
   else if (op.two_site)
     r = heff2_fp64(s->mpo, op.site, op.mL, op.mR, op.L, op.R, x, y, s->T1, s->T2, s->inter_cap, s->st);
   else
@@ -517,6 +524,12 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
   const double tau = dt_fs / HBAR_EV_FS;
   const bool mixed = s->dtype == VB_MIXED;
   cf *V32 = mixed ? s->V32 : nullptr;
+  // mixed two- and one-site products: v_{k+1} is kept as the unnormalised w
+  // (FP64 and FP32 copy) and vs[k+1] = 1/|w|; the H_eff product, the
+  // Gram-Schmidt kernels and the final combination apply the factor, so no
+  // pass rescales the vector (vs[0] = 1: v_0 is normalised explicitly)
+  const bool defer = mixed && op.two_site >= 0;
+  const double *vs = defer ? s->d_vs : nullptr;
   prof_begin(PH_KRYLOV, st);
   VB_TRY(vec_norm2(x, N, s->d_nrm, s->d_part, np, st));
   VB_TRY(vec_copy_scaled(x, V, N, st));
@@ -528,7 +541,7 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
   *converged = 0;
   for (int k = 0; k < kmax; ++k) {
     cd *w = V + (k + 1) * ldv;
-    VB_TRY(apply_heff(s, op, V + k * ldv, w));
+    VB_TRY(apply_heff(s, op, V + k * ldv, w, defer ? s->d_vs + k : nullptr));
     prof_begin(PH_KRYLOV, st);
     double kbytes = 0.0;
     if (mixed) {
@@ -543,23 +556,29 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
       const int n1 = k + 1 - j0;
       // bandwidth-bound: more, smaller partial blocks than the FP64 dots use
       const int np32 = (int)std::min<long long>(608, std::max<long long>(1, (N + 1023) / 1024));
+      const double *vs1 = vs ? vs + j0 : nullptr;
       // first pass: inner products with w rounded to FP32 on load
-      VB_TRY(vec_multi_dot32(V32 + j0 * ldv, ldv, n1, w, N, s->d_c + j0, s->d_partc, np32, st, s->d_cnt));
+      VB_TRY(vec_multi_dot32(V32 + j0 * ldv, ldv, n1, w, N, s->d_c + j0, s->d_partc, np32, st, s->d_cnt, vs1));
       if (axpy_dot32_blocks(N, k + 1, PARTC_ELEMS)) {
         // its update fused with the full pass's inner products
         VB_TRY(vec_axpy_dot32(V32 + j0 * ldv, n1, s->d_c + j0, -1.0, w, N, V32, ldv, k + 1, s->d_c2, s->d_partc,
-                              PARTC_ELEMS, st, s->d_cnt));
+                              PARTC_ELEMS, st, s->d_cnt, vs1, vs));
       } else {
-        VB_TRY(vec_multi_axpy32(V32 + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, s->w32, st));
-        VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np32, st, s->d_cnt));
+        VB_TRY(vec_multi_axpy32(V32 + j0 * ldv, ldv, n1, s->d_c + j0, -1.0, w, N, s->w32, st, vs1));
+        VB_TRY(vec_multi_dot32(V32, ldv, k + 1, s->w32, N, s->d_c2, s->d_partc, np32, st, s->d_cnt, vs));
       }
+      // full-pass update and |w|; deferred: also the FP32 copy of w as the
+      // stored copy of v_{k+1}, its factor 1/|w|, beta and alpha of step k
+      LanczosRecord rec{};
+      if (defer) rec = LanczosRecord{s->d_vs + k + 1, s->d_beta + k, s->d_alpha + k, s->d_c + k, s->d_c2 + k};
       VB_TRY(vec_multi_axpy32_norm(V32, ldv, k + 1, s->d_c2, -1.0, w, N, s->d_bnext, s->d_part, st,
-                                   s->d_cnt + 32));
+                                   s->d_cnt + 32, vs, defer ? V32 + (k + 1) * ldv : nullptr, rec));
       // algorithmic bytes: first-pass inner products (w read, copies of
       // v_{k-1}, v_k read), fused update + inner products (w read and
       // written, the two copies and all k+1 copies read), full-pass update
-      // (copies read, w read and written)
-      kbytes = (double)N * (16.0 + 8.0 * n1 + 32.0 + 8.0 * n1 + 8.0 * (k + 1) + 8.0 * (k + 1) + 32.0);
+      // (copies read, w read and written, deferred: the FP32 copy written)
+      kbytes = (double)N * (16.0 + 8.0 * n1 + 32.0 + 8.0 * n1 + 8.0 * (k + 1) + 8.0 * (k + 1) + 32.0 +
+                            (defer ? 8.0 : 0.0));
     } else {
       // FP64-pipe-bound: one partial block per 512 elements up to four per SM
       const int np64 = (int)std::min<long long>(608, std::max<long long>(1, (N + 511) / 512));
@@ -586,16 +605,18 @@ vb_status krylov_expm(vb_mps *s, const HeffOp &op, cd *x, long long N, double dt
         break;
       }
     }
-    prof_begin(PH_KRYLOV, st);
-    // v_{k+1} = w / beta_{k+1}; also records beta_{k+1} and alpha_k
-    VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k, s->d_c + k, s->d_c2 + k, s->d_alpha + k,
-                         mixed ? V32 + (k + 1) * ldv : nullptr));
-    prof_end(PH_KRYLOV, st, 2.0 * Nd);
+    if (!defer) {
+      prof_begin(PH_KRYLOV, st);
+      // v_{k+1} = w / beta_{k+1}; also records beta_{k+1} and alpha_k
+      VB_TRY(vec_scale_inv(w, N, s->d_bnext, st, s->d_beta + k, s->d_c + k, s->d_c2 + k, s->d_alpha + k,
+                           mixed ? V32 + (k + 1) * ldv : nullptr));
+      prof_end(PH_KRYLOV, st, 2.0 * Nd);
+    }
   }
   *iters = kdim;
   if (*converged) s->khint[hk] = kdim;
   prof_begin(PH_KRYLOV, st);
-  VB_TRY(vec_combine(V, ldv, kdim, s->d_u, s->d_nrm, x, N, st));
+  VB_TRY(vec_combine(V, ldv, kdim, s->d_u, s->d_nrm, x, N, st, vs));
   prof_end(PH_KRYLOV, st, 8.0 * Nd * kdim);
   return VB_OK;
 }
@@ -1131,9 +1152,12 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
     A2((void **)&s->d_partc, (size_t)PARTC_ELEMS * sizeof(cd));
     A2((void **)&s->d_tcerr, 256);
     A2((void **)&s->d_cnt, 64 * sizeof(unsigned int));
+    A2((void **)&s->d_vs, 128 * sizeof(double));
     if (e != VB_OK) return fail_free(e);
+    static const double one = 1.0;  // vs[0]: v_0 is stored normalised
     if (cudaMemsetAsync(s->d_tcerr, 0, sizeof(int), s->st) != cudaSuccess ||
-        cudaMemsetAsync(s->d_cnt, 0, 64 * sizeof(unsigned int), s->st) != cudaSuccess) {
+        cudaMemsetAsync(s->d_cnt, 0, 64 * sizeof(unsigned int), s->st) != cudaSuccess ||
+        cudaMemcpyAsync(s->d_vs, &one, sizeof(double), cudaMemcpyHostToDevice, s->st) != cudaSuccess) {
       cudaGetLastError();
       return fail_free(fail(VB_ECUDA, "mps: memset failed"));
     }
@@ -1799,7 +1823,7 @@ vb_status vb_heff2_apply(const vb_mpo *mpo, int i, int mL, int mR, const double 
     int *err = heff_mixed_err_flag(mpo, i, 1, mL, mR, work);
     VB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     VB_TRY(heff_mixed_apply(mpo, i, 1, mL, mR, (const cd *)L, (const cd *)R, (const cd *)theta, (cd *)y, work,
-                            vb_heff_work_elems(mpo, i, mL, mR, 1) * sizeof(cd), err, st));
+                            vb_heff_work_elems(mpo, i, mL, mR, 1) * sizeof(cd), err, st, nullptr));
     if (i == 0 && mpo->e_zpe != 0.0) {  // site 0's FP32 operator leaves out the zero-point constant
       const long long el = (long long)mL * mpo->dims[0] * mpo->dims[1] * mR;
       add_scaled_kernel<<<grid1(el), 256, 0, st>>>((cd *)y, (const cd *)theta, mpo->e_zpe, el);
@@ -1828,7 +1852,7 @@ vb_status vb_heff1_apply(const vb_mpo *mpo, int j, int mL, int mR, const double 
     int *err = heff_mixed_err_flag(mpo, j, 0, mL, mR, work);
     VB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     VB_TRY(heff_mixed_apply(mpo, j, 0, mL, mR, (const cd *)L, (const cd *)R, (const cd *)C, (cd *)y, work,
-                            vb_heff_work_elems(mpo, j, mL, mR, 0) * sizeof(cd), err, st));
+                            vb_heff_work_elems(mpo, j, mL, mR, 0) * sizeof(cd), err, st, nullptr));
     if (j == 0 && mpo->e_zpe != 0.0) {  // site 0's FP32 operator leaves out the zero-point constant
       const long long el = (long long)mL * mpo->dims[0] * mR;
       add_scaled_kernel<<<grid1(el), 256, 0, st>>>((cd *)y, (const cd *)C, mpo->e_zpe, el);
