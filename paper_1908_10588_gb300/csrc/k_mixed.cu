@@ -107,14 +107,16 @@ __global__ void prep_vector_T(const cd *__restrict__ x, int K, long long Ncols, 
   const long long n0 = (long long)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  const double f = xs ? xs[0] : 1.0;
+  // the factor is applied in FP32 (GB300's FP64 pipe is narrow); the
+  // operand is FP32-accurate either way
+  const float f = xs ? (float)xs[0] : 1.f;
   for (int r = ty; r < 32; r += 8) {
     const int k = k0 + r;
     const long long n = n0 + tx;
     cd z = mkc(0.0, 0.0);
     if (k < K && n < Ncols) z = x[(long long)k * Ncols + n];
-    tr[r][tx] = (float)(z.x * f);
-    ti[r][tx] = (float)(z.y * f);
+    tr[r][tx] = (float)z.x * f;
+    ti[r][tx] = (float)z.y * f;
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {

@@ -225,8 +225,13 @@ __global__ void __launch_bounds__(JAC_THREADS) ritz_jacobi_kernel(const cf *__re
       // A <- U^H A U, block by block; V <- V U
       for (int e2 = tid; e2 < h * h; e2 += nt) {
         const int bi = e2 / h, bj = e2 % h;
+        const float si = sn[bi], sj = sn[bj];
+        // a pair that does not rotate has U = I (c = 1, s = 0, phase 1): a
+        // block between two such pairs is left exactly as it is
+        if (si == 0.f && sj == 0.f && ph[bi].x == 1.f && ph[bi].y == 0.f && ph[bj].x == 1.f && ph[bj].y == 0.f)
+          continue;
         const int pi = pp[bi], qi = qq[bi], pj = pp[bj], qj = qq[bj];
-        const float ci = cs[bi], si = sn[bi], cj = cs[bj], sj = sn[bj];
+        const float ci = cs[bi], cj = cs[bj];
         const cf ei = ph[bi], ej = ph[bj];
         const cf b00 = A[pi * np + pj], b01 = A[pi * np + qj], b10 = A[qi * np + pj], b11 = A[qi * np + qj];
         // left: rows (pi, qi) by U_i^H = [[c, -s conj(e)], [s, c conj(e)]]
@@ -257,8 +262,10 @@ __global__ void __launch_bounds__(JAC_THREADS) ritz_jacobi_kernel(const cf *__re
       }
       for (int e2 = tid; e2 < np * h; e2 += nt) {
         const int x = e2 / h, bj = e2 % h;
+        const float sj = sn[bj];
+        if (sj == 0.f && ph[bj].x == 1.f && ph[bj].y == 0.f) continue;  // U = I
         const int pj = pp[bj], qj = qq[bj];
-        const float cj = cs[bj], sj = sn[bj];
+        const float cj = cs[bj];
         const cf ej = ph[bj];
         const cf v0 = V[x * np + pj], v1 = V[x * np + qj];
         const cf w1 = mkc(ej.x * v1.x - ej.y * v1.y, ej.x * v1.y + ej.y * v1.x);
