@@ -323,6 +323,8 @@ __device__ __forceinline__ void dot32_any(int jn, const cf *Vg, long long ldv, c
   }
 }
 
+// out[j] = vs[j] <V_j, w> (vs nullable: 1) for the group of blockIdx.y, the
+// partial sums over each block's chunk of w summed by the group's last block
 template <typename WT>
 __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V, long long ldv, int nv,
                                                        const WT *__restrict__ w, long long n,
@@ -369,7 +371,9 @@ __global__ void __launch_bounds__(RT) multi_dot32_part(const cf *__restrict__ V,
 // multi_axpy32_norm_kernel), keeps the FP32 copy of the new w in shared
 // memory, then forms partial[b * nv + j] = <V_j, w32> over its chunk for all
 // nv vectors in groups of DOT_JB (as multi_dot32_part); the last block sums
-// the partials in block order. Dynamic shared memory: chunk FP32 elements.
+// the partials in block order. vs1 / vs (nullable): factors of the stored
+// copies V1 / V (coefficients and inner products are those of the normalised
+// vectors). Dynamic shared memory: chunk FP32 elements.
 __global__ void __launch_bounds__(RT, 4) axpy_dot32_kernel(const cf *__restrict__ V1, int n1,
                                                         const cd *__restrict__ c1, double sign,
                                                         cd *__restrict__ w, long long n, const cf *__restrict__ V,
@@ -443,9 +447,10 @@ __global__ void __launch_bounds__(RT, 4) axpy_dot32_kernel(const cf *__restrict_
   if (threadIdx.x == 0) cnt[0] = 0u;
 }
 
-// w[i] += sign * sum_j c[j] V32_j[i] (correction in FP32, w in FP64); with
-// w32 != nullptr the FP32 copy of the new w is written too; with partial !=
-// nullptr |w| in FP64 by the last block (cnt: one zeroed counter)
+// w[i] += sign * sum_j c[j] vs[j] V32_j[i] (correction in FP32, w in FP64;
+// vs nullable: 1); with w32 != nullptr the FP32 copy of the new w is written
+// too; with partial != nullptr |w| in FP64 by the last block (cnt: one zeroed
+// counter), which also writes the Lanczos record (1/|w|, |w|, alpha_k)
 __global__ void __launch_bounds__(256) multi_axpy32_norm_kernel(const cf *__restrict__ V, long long ldv, int nv,
                                                                 const cd *__restrict__ c, double sign,
                                                                 cd *__restrict__ w, long long n,
