@@ -76,6 +76,20 @@ def _dist():
     return ws, rank, local
 
 
+def _aggregate_replicas(ms: float, steps: int, ws: int, device="cuda"):
+    """Whole-job timing of N independent replicas (a trajectory does not
+    shard: each rank propagates its own): the timed region's duration is the
+    maximum over ranks, and the rate counts every rank's steps.
+    Returns (max ms, sweeps/s summed over ranks)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * steps / (ms / 1e3)
+
+
 def _clock_sampler_start():
     fd, path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
     os.close(fd)
@@ -294,12 +308,7 @@ def run_ours(args):
     launches = P.vb_kernel_launches() - launches0
     P.vb_profile_enable(False)
     prof = P.vb_profile_read(reset=True)
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1e3)
+    ms, value = _aggregate_replicas(ev0.elapsed_time(ev1), args.steps, ws, "cuda")
     pops = mps.populations()
     bonds = mps.bond_dims()
 
