@@ -277,8 +277,6 @@ vb_status vec_multi_axpy32_norm(const cf *V, long long ldv, int nv, const cd *c,
 // the same update without the norm, writing the FP32 copy of the new w into w32
 vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
                            cf *w32, cudaStream_t st, const double *vs = nullptr);
-// y = FP32 copy of x
-vb_status vec_to_c32(const cd *x, cf *y, long long n, cudaStream_t st);
 // inner products of FP32 copies with the FP64 w rounded to FP32 on load
 vb_status vec_multi_dot32(const cf *V, long long ldv, int nv, const cd *w, long long n, cd *out, cd *partial,
                           int n_part, cudaStream_t st, unsigned int *cnt, const double *vs = nullptr);

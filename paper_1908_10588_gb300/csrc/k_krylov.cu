@@ -893,18 +893,6 @@ vb_status vec_multi_axpy32(const cf *V, long long ldv, int nv, const cd *c, doub
   return VB_OK;
 }
 
-__global__ void to_c32_kernel(const cd *__restrict__ x, cf *__restrict__ y, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = mkc((float)x[i].x, (float)x[i].y);
-}
-
-vb_status vec_to_c32(const cd *x, cf *y, long long n, cudaStream_t st) {
-  if (n == 0) return VB_OK;
-  to_c32_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, y, n);
-  VB_CHECK_LAUNCH();
-  return VB_OK;
-}
-
 vb_status vec_multi_axpy_norm(const cd *V, long long ldv, int nv, const cd *c, double sign, cd *w, long long n,
                               double *out, double *partial, cudaStream_t st, unsigned int *cnt) {
   if (nv > 128) return fail(VB_EINVAL, "multi_axpy: more than 128 vectors");
