@@ -667,7 +667,8 @@ def run_sf_case(args):
     right-canonical state, every bond at min(128, full)): --steps timed steps
     of the mixed form after one warm-up, one FP64-form step; (b) from the
     product state |LE> x |0...0>: --sf-steps steps of both forms, the largest
-    population difference between them along the way."""
+    population difference between them along the way. --sf-mixed-only: (a)
+    for the mixed form alone."""
     import torch
     from paper_1908_10588_gb300 import build as pbuild
     pbuild.build()
@@ -681,7 +682,8 @@ def run_sf_case(args):
     ts = vm.random_right_canonical_mps(STATE_SEED, dims, mmax)
     out = {"case": "singlet_fission", "model": "model_singlet_fission(seed=1003, n_bath=100, levels=10)",
            "n_sites": len(dims), "m_max": mmax, "eps": 1e-8, "dt_fs": 1.0}
-    for name, dtype, nsteps in (("mixed", P.VB_MIXED, args.steps), ("fp64", P.VB_FP64, 1)):
+    forms = (("mixed", P.VB_MIXED, args.steps),) + (() if args.sf_mixed_only else (("fp64", P.VB_FP64, 1),))
+    for name, dtype, nsteps in forms:
         mps = P.Mps(mpo, m_cap=mmax, dtype=dtype, stream=st, tensors=ts)
         if name == "mixed":
             mps.sweep(1.0, **kw)
@@ -708,6 +710,9 @@ def run_sf_case(args):
             tc = pr["heff_tc_legs"]
             out[f"steady_{name}"]["tc_legs_tflops"] = tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
         mps.close()
+    if args.sf_mixed_only:
+        print(json.dumps(out), flush=True)
+        return 0
     idx = vm.product_state_indices(m)
     runs = {}
     for name, dtype in (("mixed", P.VB_MIXED), ("fp64", P.VB_FP64)):
@@ -877,6 +882,7 @@ def main():
     ap.add_argument("--batch-case", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--sf-steps", type=int, default=20)
+    ap.add_argument("--sf-mixed-only", action="store_true")
     ap.add_argument("--fd-params", type=int, default=0)
     ap.add_argument("--fd-start", type=int, default=0)
     ap.add_argument("--fd-h", type=float, default=1e-5)
