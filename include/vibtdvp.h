@@ -80,8 +80,11 @@ typedef struct {
 
 typedef struct {
   int m_cap;          /* largest bond dimension the handle reserves memory for */
-  int dtype;          /* VB_FP64, or VB_MIXED: H_eff products on the tensor cores in TF32 with
-                         FP32 accumulation, everything else in FP64 */
+  int dtype;          /* VB_FP64, or VB_MIXED: H_eff products on the tensor cores in split TF32
+                         with FP32 accumulation, FP32 environments, FP32 directions of the split
+                         with FP64 weights, Lanczos Gram-Schmidt on FP32 copies of the FP64
+                         vectors; the Lanczos vectors, coefficients, small exponential and the
+                         new tensors stay FP64 */
   int pad_full;       /* mps_create: pad the product state to full bonds (<= m_cap) */
   int krylov_cap;     /* largest Krylov dimension reserved (default 40) */
   void *cuda_stream;  /* cudaStream_t */
@@ -428,10 +431,12 @@ unsigned long long vb_kernel_launches(void);
  * inverse iteration, Gram-Schmidt and back-transformation parts of every
  * eigenvector stage; inside the mixed-form H_eff products 20 = the tcgen05
  * legs (L and R contractions, incl. their split-K reductions), 21 = the
- * sparse MPO legs, 22 = the operand preparation). flops[p] / bytes[p] are
- * the algorithmic work of every call of phase p (20: the useful complex
- * flops of the two dense legs; 21: one read of each leg's input and one write
- * of its output, FP32; 0 where not counted). heff_flops[c] counts the algorithmic
+ * sparse MPO legs, 22 = the operand preparation; 23 = the one-CTA Jacobi
+ * eigensolver of the Rayleigh-Ritz step, inside 16). flops[p] / bytes[p] are
+ * the algorithmic work of every call of phase p (2, mixed form: bytes of
+ * the Gram-Schmidt kernels; 20: the useful complex flops of the two dense
+ * legs; 21: one read of each leg's input and one write of its output, FP32;
+ * 23: flops[23] counts Jacobi sweeps instead; 0 where not counted). heff_flops[c] counts the algorithmic
  * floating-point operations of the H_eff products of class c (a complex
  * multiply-add is 8, real-times-complex 4, an identity-block add 2);
  * krylov_flops counts the FP64 operations of the Krylov vector work (phase
