@@ -276,6 +276,7 @@ struct vb_mps {
   long long skws_elems = 0;
   // mixed form: environment updates in complex FP32
   cf *envA32 = nullptr, *envE32 = nullptr, *envO32 = nullptr, *envT1 = nullptr, *envT2 = nullptr;
+  cf *mrgB32 = nullptr;  // mixed merge: FP32 copy of the right site tensor (the left one goes to envA32)
   long long env_site_cap = 0, env_blk_cap = 0;
   std::vector<void *> owned;
   int center = 0;
@@ -1038,6 +1039,28 @@ vb_status env_update(vb_mps *s, bool left, int p, int mL, int mR, const cd *E, c
 vb_status merge(vb_mps *s, int i) {
   const int mL = s->bond[i], mM = s->bond[i + 1], mR = s->bond[i + 2];
   const int d1 = s->dims[i], d2 = s->dims[i + 1];
+  if (s->dtype == VB_MIXED) {
+    // complex FP32 (FP32 products, K = mM terms per element): theta is the
+    // start of an exponential whose products are FP32-accurate themselves
+    const long long na = (long long)mL * d1 * mM, nb = (long long)mM * d2 * mR, nt = (long long)mL * d1 * d2 * mR;
+    if (na > s->env_site_cap || nb > s->env_site_cap || nt > s->theta_cap)
+      return fail(VB_EINVAL, "merge: tensors exceed their FP32 buffers");
+    c64_to_c32<<<grid1(na), 256, 0, s->st>>>(s->A[i], s->envA32, na);
+    VB_CHECK_LAUNCH();
+    c64_to_c32<<<grid1(nb), 256, 0, s->st>>>(s->A[i + 1], s->mrgB32, nb);
+    VB_CHECK_LAUNCH();
+    GemmArgsF g{};
+    g.M = mL * d1; g.N = d2 * mR; g.K = mM; g.batch = 1;
+    g.opA = OP_N; g.opB = OP_N;
+    g.A = s->envA32; g.lda = mM; g.B = s->mrgB32; g.ldb = g.N; g.C = s->M32; g.ldc = g.N;
+    g.alpha = mkc(1.f, 0.f); g.beta = mkc(0.f, 0.f);
+    g.a_size = na; g.b_size = nb; g.c_size = s->theta_cap;
+    g.ws = s->skws32; g.ws_elems = s->skws32_elems;
+    VB_TRY(gemm<float>(g, s->st));
+    c32_to_c64<<<grid1(nt), 256, 0, s->st>>>(s->M32, s->theta, nt);
+    VB_CHECK_LAUNCH();
+    return VB_OK;
+  }
   GemmArgs g{};
   g.M = mL * d1; g.N = d2 * mR; g.K = mM; g.batch = 1;
   g.opA = OP_N; g.opB = OP_N;
@@ -1198,6 +1221,7 @@ vb_status mps_setup(const vb_mpo *mpo, const vb_mps_opts *opts, vb_mps **out) {
           s->env_site_cap = std::max<long long>(s->env_site_cap, (long long)s->bcap[p] * s->dims[p] * s->bcap[p + 1]);
       }
       A2((void **)&s->envA32, (size_t)s->env_site_cap * sizeof(cf));
+      A2((void **)&s->mrgB32, (size_t)s->env_site_cap * sizeof(cf));
       A2((void **)&s->envE32, (size_t)s->env_blk_cap * sizeof(cf));
       A2((void **)&s->envO32, (size_t)s->env_blk_cap * sizeof(cf));
       A2((void **)&s->envT1, (size_t)s->inter_cap * sizeof(cf));
