@@ -81,10 +81,10 @@ typedef struct {
 typedef struct {
   int m_cap;          /* largest bond dimension the handle reserves memory for */
   int dtype;          /* VB_FP64, or VB_MIXED: H_eff products on the tensor cores in split TF32
-                         with FP32 accumulation, FP32 environments, FP32 directions of the split
-                         with FP64 weights, Lanczos Gram-Schmidt on FP32 copies of the FP64
-                         vectors; the Lanczos vectors, coefficients, small exponential and the
-                         new tensors stay FP64 */
+                         with FP32 accumulation, FP32 environments and merge, FP32 directions of
+                         the split with FP64 weights, Lanczos Gram-Schmidt on FP32 copies of the
+                         FP64 vectors; the Lanczos vectors, coefficients, small exponential and
+                         the stored tensors stay FP64 */
   int pad_full;       /* mps_create: pad the product state to full bonds (<= m_cap) */
   int krylov_cap;     /* largest Krylov dimension reserved (default 40) */
   void *cuda_stream;  /* cudaStream_t */
