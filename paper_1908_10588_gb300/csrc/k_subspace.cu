@@ -376,13 +376,14 @@ static vb_status orth_pass(const cf *A, cf *T, int r, int n, const SubspaceWork 
 vb_status subspace_orth(cf *Q, int r, int n, const SubspaceWork &w, unsigned long long seed, cudaStream_t st) {
   if (r < 1 || r > SUBSPACE_MAX_R || n < r)
     return fail(VB_EINVAL, "subspace_orth: needs 1 <= r <= min(n, " + std::to_string(SUBSPACE_MAX_R) + ")");
-  static int smem_set[64] = {0};
+  static std::atomic<bool> smem_set[64];  // per device; setting it twice is harmless
   int dev = 0;
   VB_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+  if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "subspace_orth: device ordinal out of range");
+  if (!smem_set[dev].load()) {
     VB_TRY_CUDA(cudaFuncSetAttribute(chol_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)subspace_chol_smem(SUBSPACE_MAX_R)));
-    smem_set[dev] = 1;
+    smem_set[dev].store(true);
   }
   VB_TRY(orth_pass(Q, w.T, r, n, w, seed, st));
   VB_TRY(orth_pass(w.T, Q, r, n, w, seed ^ 0x5bd1e995ull, st));
@@ -401,14 +402,14 @@ size_t chol64_smem(int r) { return (size_t)r * r * sizeof(cd) + 2 * (size_t)r * 
 
 vb_status chol_w64(const cd *G, int r, cd *W, int *flag, cudaStream_t st) {
   if (r < 1 || r > CHOL64_MAX_R) return fail(VB_EINVAL, "chol_w64: needs 1 <= r <= 112");
-  static int smem_set[64] = {0};
+  static std::atomic<bool> smem_set[64];  // per device; setting it twice is harmless
   int dev = 0;
   VB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "chol_w64: device ordinal out of range");
-  if (!smem_set[dev]) {
+  if (!smem_set[dev].load()) {
     VB_TRY_CUDA(cudaFuncSetAttribute(chol_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)chol64_smem(CHOL64_MAX_R)));
-    smem_set[dev] = 1;
+    smem_set[dev].store(true);
   }
   chol_rows_kernel<double><<<1, CHOL_THREADS, chol64_smem(r), st>>>(G, r, 1e-28, W, flag);
   VB_CHECK_LAUNCH();
@@ -428,14 +429,14 @@ size_t ritz_jacobi_smem(int n) {
 
 vb_status ritz_eig_small(const cf *S, int n, int k, float *evals, cf *W, int *info, cudaStream_t st) {
   if (n < 2 || n > JAC_MAX_N || k < 1 || k > n) return fail(VB_EINVAL, "ritz_eig_small: needs 2 <= n <= 112");
-  static int smem_set[64] = {0};
+  static std::atomic<bool> smem_set[64];  // per device; setting it twice is harmless
   int dev = 0;
   VB_TRY_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(VB_EINVAL, "ritz_eig_small: device ordinal out of range");
-  if (!smem_set[dev]) {
+  if (!smem_set[dev].load()) {
     VB_TRY_CUDA(cudaFuncSetAttribute(ritz_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)ritz_jacobi_smem(JAC_MAX_N)));
-    smem_set[dev] = 1;
+    smem_set[dev].store(true);
   }
   ritz_jacobi_kernel<<<1, JAC_THREADS, ritz_jacobi_smem(n), st>>>(S, n, k, evals, W, info);
   VB_CHECK_LAUNCH();

@@ -828,11 +828,11 @@ vb_status tc_gemm_tf32(const float *A, long long lda, const float *B, long long 
   Epi e = ks > 1 ? Epi{0, ws, N, nullptr, 0, (long long)M * N} : Epi{mode, D, ldd, Y, nh, 0};
   if (ks == 1 && Alo && Blo && nkb <= BRES_MAX_KB && mode == 0) {
     // short K: the B block of an N tile stays resident for a group of M tiles
-    static bool bres_set[64] = {false};
-    if (!bres_set[dev]) {
+    static std::atomic<bool> bres_set[64];  // per device; setting it twice is harmless
+    if (!bres_set[dev].load()) {
       VB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_bres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BRES_SMEM));
-      bres_set[dev] = true;
+      bres_set[dev].store(true);
     }
     // plain fp32 output with 16-byte aligned rows: stored by TMA in 32 x 32 blocks
     CUtensorMap td = ta;
